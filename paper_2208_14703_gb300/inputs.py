@@ -1,0 +1,220 @@
+"""Seeded synthetic inputs for the implicit M1 step.
+
+This module generates the input states, opacities and inflow profiles that the
+CUDA path, the tests, the benchmark and the CPU oracle all consume.  It holds
+none of the solver's arithmetic: it only draws random numbers and lays out
+initial conditions.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) evaluated on a counter, so a
+field is a pure function of (seed, index); normals use the Box-Muller
+transform.  Opacity fields follow the recipe of the workloads:
+log10(sigma) = 1 + 3 g clipped to [-2, 4], g a unit-variance Gaussian random
+field (white noise smoothed by a periodic Gaussian filter of correlation length
+8 cells), so sigma spans 1e-2 .. 1e4 and optically thin and thick regions mix.
+
+Every case is a dict with keys
+  desc:   dim, nx, ny, lx, ly, bc (west, east, south, north), c, a_r, c_v
+  dt:     physical time step (CFL * h / c)
+  state:  float64 (4, ny, nx) planes E, Fx, Fy, T
+  sa, ss: float64 (ny, nx) absorption / scattering opacities
+  inflow: float64 (4, 3, max(nx, ny)) prescribed wall states or None
+  lmax, tol: the level count and relative residual target of the workload
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n outputs of splitmix64 started at state `seed` (counter form)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits."""
+    return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """Standard normals by Box-Muller on two counter streams."""
+    u1 = uniform(seed * 2 + 1, n)
+    u2 = uniform(seed * 2 + 2, n)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def gaussian_field(nx: int, ny: int, seed: int, corr: float = 8.0) -> np.ndarray:
+    """Unit-variance, zero-mean Gaussian random field (periodic smoothing by FFT)."""
+    w = normal(seed, nx * ny).reshape(ny, nx)
+    kx = np.fft.fftfreq(nx)
+    ky = np.fft.fftfreq(ny) if ny > 1 else np.zeros(1)
+    filt = np.exp(-0.5 * (2 * np.pi * corr) ** 2 * (kx[None, :] ** 2 + ky[:, None] ** 2))
+    g = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
+    g -= g.mean()
+    s = g.std()
+    return g / s if s > 0 else g
+
+
+def lognormal_opacity(nx: int, ny: int, seed: int, corr: float = 8.0, lo: float = -2.0,
+                      hi: float = 4.0) -> np.ndarray:
+    g = gaussian_field(nx, ny, seed, corr)
+    return 10.0 ** np.clip(1.0 + 3.0 * g, lo, hi)
+
+
+def _desc(dim, nx, ny, lx, ly, bc, c=1.0, a_r=1.0, c_v=1.0):
+    return dict(dim=dim, nx=nx, ny=ny if dim == 2 else 1, lx=lx, ly=ly, bc=list(bc), c=c,
+                a_r=a_r, c_v=c_v)
+
+
+def _state(nx, ny, E, Fx=None, Fy=None, T=None):
+    s = np.zeros((4, ny, nx))
+    s[0] = E
+    if Fx is not None:
+        s[1] = Fx
+    if Fy is not None:
+        s[2] = Fy
+    s[3] = 1.0 if T is None else T
+    return s
+
+
+def gaussian_1d(n: int = 256, cfl: float = 50.0, lmax: int = 4, tol: float = 1e-10) -> dict:
+    """1D: n cells on [0, 1], c = a_r = C_v = 1, sigma_a = sigma_s = 1, T_g = 1,
+    E = 1e-2 + exp(-(x - 0.5)^2 / 0.005), F = 0, periodic, dt = cfl * h / c."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    E = 1e-2 + np.exp(-(x - 0.5) ** 2 / 0.005)
+    return dict(desc=_desc(1, n, 1, 1.0, 1.0, ["periodic"] * 4), dt=cfl * h,
+                state=_state(n, 1, E[None, :]), sa=np.ones((1, n)), ss=np.ones((1, n)),
+                inflow=None, lmax=lmax, tol=tol)
+
+
+def hot_square_2d(n: int = 1024, cfl: float = 100.0, lmax: int = 8, tol: float = 1e-8,
+                  seed_a: int = 1, seed_s: int = 2) -> dict:
+    """2D plain-FP64 workload: n x n cells on [0,1]^2, lognormal sigma_a, sigma_s,
+    T_g = 1 with a centred hot square of side 1/8 at T_g = 4, E = a_r T_g^4,
+    F = 0, reflecting walls, dt = cfl * h / c."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x)
+    T = np.where((np.abs(X - 0.5) < 1 / 16) & (np.abs(Y - 0.5) < 1 / 16), 4.0, 1.0)
+    return dict(desc=_desc(2, n, n, 1.0, 1.0, ["reflect"] * 4), dt=cfl * h,
+                state=_state(n, n, T ** 4, T=T), sa=lognormal_opacity(n, n, seed_a),
+                ss=lognormal_opacity(n, n, seed_s), inflow=None, lmax=lmax, tol=tol)
+
+
+def beam_channel_2d(n: int = 4096, cfl: float = 100.0, lmax: int = 10, tol: float = 1e-8,
+                    seed_a: int = 3, seed_s: int = 4) -> dict:
+    """2D beam: an f = 1 beam (E = 1, F = (c, 0)) enters through the west wall
+    into a thin channel y in [0.45, 0.55] (sigma_a = sigma_s = 1e-2) cut through
+    the lognormal medium; the rest of the west wall holds the background state
+    (E = 1, F = 0); other walls reflect.  Background T_g = 1, E = 1, F = 0."""
+    h = 1.0 / n
+    y = (np.arange(n) + 0.5) * h
+    chan = (y >= 0.45) & (y <= 0.55)
+    sa = lognormal_opacity(n, n, seed_a)
+    ss = lognormal_opacity(n, n, seed_s)
+    sa[chan, :] = 1e-2
+    ss[chan, :] = 1e-2
+    inflow = np.zeros((4, 3, n))
+    inflow[0, 0, :] = 1.0
+    inflow[0, 1, :] = np.where(chan, 1.0, 0.0)
+    return dict(desc=_desc(2, n, n, 1.0, 1.0, ["inflow", "reflect", "reflect", "reflect"]),
+                dt=cfl * h, state=_state(n, n, np.ones((n, n))), sa=sa, ss=ss, inflow=inflow,
+                lmax=lmax, tol=tol)
+
+
+def riemann_2d(n: int = 64, cfl: float = 2.0, lmax: int = 3, tol: float = 1e-10,
+               sigma: float = 0.0) -> dict:
+    """Section 5.2 Riemann problem in nondimensional form: [0,1]^2, four quadrants
+    with F = (1 - 1e-8) c E F_hat, F_hat = (1,0) bottom-left, (0,-1) bottom-right,
+    (0,1) top-left, (-1,0) top-right; uniform E = 1; periodic."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x)
+    fx = np.where((X < 0.5) & (Y < 0.5), 1.0, 0.0) + np.where((X >= 0.5) & (Y >= 0.5), -1.0, 0.0)
+    fy = np.where((X >= 0.5) & (Y < 0.5), -1.0, 0.0) + np.where((X < 0.5) & (Y >= 0.5), 1.0, 0.0)
+    k = 1.0 - 1e-8
+    s = _state(n, n, np.ones((n, n)), k * fx, k * fy)
+    return dict(desc=_desc(2, n, n, 1.0, 1.0, ["periodic"] * 4), dt=cfl * h, state=s,
+                sa=np.full((n, n), sigma), ss=np.full((n, n), sigma), inflow=None, lmax=lmax,
+                tol=tol)
+
+
+def random_admissible_2d(nx: int, ny: int, seed: int, fmax: float = 0.999, cfl: float = 10.0,
+                         bc=("periodic",) * 4, lmax: int = 2, tol: float = 1e-10,
+                         dim: int = 2) -> dict:
+    """Random admissible states: E log-uniform in [1e-2, 1e2], reduced flux f
+    uniform in [0, fmax] with a uniform direction, T log-uniform in [0.5, 2],
+    lognormal opacities.  A stress input for single kernels."""
+    if dim == 1:
+        ny = 1
+    n = nx * ny
+    E = 10.0 ** (4.0 * uniform(seed * 7 + 1, n) - 2.0)
+    f = fmax * uniform(seed * 7 + 2, n)
+    th = 2 * np.pi * uniform(seed * 7 + 3, n) if dim == 2 else np.where(
+        uniform(seed * 7 + 3, n) < 0.5, 0.0, np.pi)
+    T = 2.0 ** (2.0 * uniform(seed * 7 + 4, n) - 1.0)
+    Fx, Fy = f * E * np.cos(th), f * E * np.sin(th)
+    if dim == 1:
+        Fy = np.zeros(n)
+    s = np.stack([E, Fx, Fy, T]).reshape(4, ny, nx)
+    h = 1.0 / nx
+    sa = lognormal_opacity(nx, ny, seed * 7 + 5)
+    ss = lognormal_opacity(nx, ny, seed * 7 + 6)
+    inflow = None
+    if "inflow" in bc:
+        L = max(nx, ny)
+        inflow = np.zeros((4, 3, L))
+        inflow[:, 0, :] = 1.0
+        inflow[:, 1, :] = 0.5
+    return dict(desc=_desc(dim, nx, ny, 1.0, ny * h if dim == 2 else 1.0, list(bc)), dt=cfl * h,
+                state=s, sa=sa, ss=ss, inflow=inflow, lmax=lmax, tol=tol)
+
+
+def batched_instances(count: int = 512, seed: int = 5,
+                      sizes=(64, 96, 128, 192, 256, 512, 1024), cfl: float = 100.0,
+                      lmax: int = 5, tol: float = 1e-8) -> list:
+    """Independent 2D instances: size drawn uniformly from `sizes` (square),
+    per-instance lognormal opacities, E = 1 + A exp(-|x - x0|^2 / w) with
+    A ~ U[1, 100], x0 ~ U[0.25, 0.75]^2, w ~ U[0.002, 0.02]; T = 1, F = 0,
+    reflecting walls."""
+    u = uniform(seed, 6 * count).reshape(count, 6)
+    out = []
+    for k in range(count):
+        n = int(sizes[min(int(u[k, 0] * len(sizes)), len(sizes) - 1)])
+        A = 1.0 + 99.0 * u[k, 1]
+        x0, y0 = 0.25 + 0.5 * u[k, 2], 0.25 + 0.5 * u[k, 3]
+        w = 0.002 + 0.018 * u[k, 4]
+        h = 1.0 / n
+        x = (np.arange(n) + 0.5) * h
+        X, Y = np.meshgrid(x, x)
+        E = 1.0 + A * np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / w)
+        out.append(dict(desc=_desc(2, n, n, 1.0, 1.0, ["reflect"] * 4), dt=cfl * h,
+                        state=_state(n, n, E), sa=lognormal_opacity(n, n, 1000 + 2 * k),
+                        ss=lognormal_opacity(n, n, 1001 + 2 * k), inflow=None, lmax=lmax,
+                        tol=tol))
+    return out
+
+
+def crop(case: dict, n: int) -> dict:
+    """The lower-left n x n corner of a 2D case (same generator, smaller grid)."""
+    c = dict(case)
+    d = dict(case["desc"])
+    h = d["lx"] / d["nx"]
+    d.update(nx=n, ny=n, lx=n * h, ly=n * h)
+    c["desc"] = d
+    c["state"] = np.ascontiguousarray(case["state"][:, :n, :n])
+    c["sa"] = np.ascontiguousarray(case["sa"][:n, :n])
+    c["ss"] = np.ascontiguousarray(case["ss"][:n, :n])
+    if case.get("inflow") is not None:
+        c["inflow"] = np.ascontiguousarray(case["inflow"][:, :, :n])
+    return c
