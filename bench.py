@@ -1,0 +1,317 @@
+"""Benchmark of the implicit M1 multigrid step on GB300.
+
+Workload (one "step" = one implicit time step v^n -> v^{n+1}, Algorithm 4, of
+the 2D plain-FP64 case): 1024 x 1024 cells on [0,1]^2, seeded lognormal
+sigma_a, sigma_s spanning 1e-2 .. 1e4, T_g = 1 with a hot square T_g = 4,
+E = a_r T^4, F = 0, reflecting walls, dt = 100 h / c, L_max = 8, V-cycles until
+||r|| <= 1e-8 ||r_0||.  Every timed step solves the same v^n (the state is reset
+on the device before each step, inside the timed region).
+
+metric: fine-level smoother cell-updates per second over the whole step
+        (fine cells x fine Jacobi sweeps / step time), summed over ranks.
+roofline: the dominant kernel (the fine Jacobi sweep, FP64), timed with CUDA
+        events on the grid's stream.
+e2e:    the same metric through the C ABI with host buffers: set_state from
+        pinned host arrays, the step, get_state back to host, per step.
+cpu_baseline / --impl reference: the FP64 CPU oracle on a bounded sample of the
+        same workload (a fixed number of V-cycles), on this host's cores.
+
+Multi-GPU: instances are independent, so N ranks run N replicas of the step
+(weak scaling, no collective on the data path); value = all ranks' cell-updates
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M1 smoother cell-updates/s"
+UNIT = "cell-updates/s"
+WORKLOAD = "m1-implicit-step-2d-fp64-1024x1024-lmax8-tol1e-8"
+N = 1024
+FP64_FMA_PER_SM_PER_CLK = 2          # GB300: 1.25 TFLOP/s nominal FP64 at 2.07 GHz, 152 SMs
+SMS = 152
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_fallback": True}
+
+
+def sweep_counts():
+    """Algorithmic work of one fine FP64 Jacobi sweep per cell (2D), counted on
+    the minimal arithmetic of the update: bytes moved and FP64 operations with
+    division and square root weighted by their cost in FMA issue slots."""
+    bytes_per_cell = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8        # read u, b, sigma; write u'
+    return bytes_per_cell
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_sample(case, cycles):
+    """The FP64 oracle, as it stands, on `cycles` V-cycles of the workload
+    (1 host core).  Returns (cell-updates/s, seconds, fine sweeps)."""
+    from oracle import oracle as O
+    g = O.Grid.from_case(case)
+    p = O.SolveParams(lmax=case["lmax"], tol=0.0, max_cycles=cycles)
+    t = time.perf_counter()
+    _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"], p)
+    dt = time.perf_counter() - t
+    cells = case["desc"]["nx"] * case["desc"]["ny"]
+    return cells * st["fine_sweeps"] / dt, dt, st["fine_sweeps"]
+
+
+def run_reference(args, case):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    cyc = 2
+    for _ in range(args.warmup):
+        cpu_sample(case, cyc)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s, _ = cpu_sample(case, cyc)
+        vals.append(v)
+        secs.append(s)
+    value = float(np.mean(vals))
+    sample = f"{cyc} V-cycles of the workload per step (fine sweeps x 1024^2 cells / time)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_2208_14703_gb300 import inputs
+    case = inputs.hot_square_2d(N)
+    if args.impl == "reference":
+        run_reference(args, case)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    from paper_2208_14703_gb300 import build
+    build.build()
+    from paper_2208_14703_gb300 import m1
+
+    stream = torch.cuda.current_stream()
+    grid = m1.grid_from_case(case, stream=stream.cuda_stream)
+    dev = torch.device("cuda", local)
+    s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).to(dev) for k in range(4)]
+    params = m1.m1_default_params(tol=case["tol"])
+    dt = case["dt"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    cells = N * N
+
+    def one_step():
+        grid.set_state(*s0, on_device=True)
+        return grid.implicit_step(dt, params)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    stats = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps (not timed)
+        ev[k][0].record(stream)
+        stats.append(one_step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_total = sum(ms_steps)
+
+    # dominant kernel: the fine FP64 Jacobi sweep, timed with CUDA events on the
+    # grid's stream (state reset first; L2 flushed before each timed launch)
+    nsw = 20
+    ks = []
+    grid.set_state(*s0, on_device=True)
+    for k in range(nsw):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        grid.jacobi(dt, 2)
+        b.record(stream)
+        ks.append((a, b))
+    torch.cuda.synchronize()
+    # each m1_jacobi call = rhs build + two sweeps (an even count ends in the
+    # state buffer, no copy); subtract the rhs kernel timed alone (zero sweeps)
+    z = []
+    for k in range(nsw):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        grid.jacobi(dt, 0)
+        b.record(stream)
+        z.append((a, b))
+    torch.cuda.synchronize()
+    sweep_ms = 0.5 * (np.median([a.elapsed_time(b) for a, b in ks])
+                      - np.median([a.elapsed_time(b) for a, b in z]))
+    sampler_out = sampler.stop()
+
+    sweeps = [s.sweeps for s in stats]
+    cycles = [s.cycles for s in stats]
+    units = cells * sum(sweeps)
+    tmax = torch.tensor([ms_total], device=dev)
+    utot = torch.tensor([float(units)], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(utot, op=torch.distributed.ReduceOp.SUM)
+    value = utot.item() / (tmax.item() * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    pin = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).pin_memory() for k in range(4)]
+    outp = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in range(4)]
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    e2e_units = 0
+    for _ in range(e2e_steps):
+        grid.set_state(*[p.numpy() for p in pin])
+        st = grid.implicit_step(dt, params)
+        grid.get_state([o.numpy() for o in outp])
+        e2e_units += cells * st.sweeps
+    te = time.perf_counter() - te
+    e2e_val = e2e_units / te
+    if world > 1:
+        t = torch.tensor([e2e_val * world], device=dev)
+        e2e_val = t.item()
+
+    pk = peaks()
+    bpc = sweep_counts()
+    achieved = bpc * cells / (sweep_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "kernel": "k_sweep<double> (fine Jacobi sweep)", "kernel_ms": sweep_ms,
+            "peak_source": "measured" if not pk.get("_fallback") else "fallback"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        v, secs, fs = cpu_sample(case, 4)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"4 V-cycles of the same 1024^2 workload ({fs} fine sweeps, {secs:.1f} s)"}
+
+    launches = sum(s.launches for s in stats) + 2 * args.steps
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax.item() / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "lmax": case["lmax"],
+                       "tol": case["tol"], "cfl": 100, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "reset": "v^n restored on the device before every step (timed)"},
+            "cycles_per_step": cycles, "fine_sweeps_per_step": sweeps,
+            "steps_cells_per_s": cells * args.steps / (tmax.item() * 1e-3) * world,
+            "wall_s": wall,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
+                    "d2h_bytes_per_step": 4 * 8 * cells},
+            "gpu_launches": launches, "clocks": sampler_out,
+        }))
+    grid.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * m1.h -- C ABI of libm1: one implicit time step of the gray M1 moment model
+ * for radiative transfer, solved on one GB300 GPU by the nonlinear FAS
+ * geometric multigrid of Bloch, Tremblin, Gonzalez & Audit, "Towards a
+ * multigrid method for the M1 model for radiative transfer" (arXiv:2208.14703).
+ *
+ * The unknowns per cell are the radiative energy E, the radiative flux
+ * F = (Fx, Fy) and the gas temperature T (Section 2.1, Eq. (3)); the scheme is
+ * the backward-Euler Rusanov (HLL with speeds +-c) finite volume scheme of
+ * Section 2.2, Eq. (6), on a uniform Cartesian grid, plus backward-Euler
+ * absorption (sigma_a) / scattering (sigma_s) sources coupling E to T.  The
+ * paper itself sets every opacity to zero; with sigma_a = sigma_s = 0 the
+ * operator is exactly its Eq. (6).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are row-major [ny][nx] (index j*nx + i), FP64, one array per field.
+ *    In 1D (dim = 1) ny must be 1 and Fy may be NULL.
+ *  - `on_device` = 0: host pointers (any host memory; pinned is faster);
+ *    `on_device` = 1: CUDA device pointers on the grid's device, read or
+ *    written in stream order on the grid's stream.
+ *  - Input arrays are copied; the caller keeps ownership of every pointer it
+ *    passes.  The grid owns all device memory it allocates and frees it in
+ *    m1_destroy_grid.  The library never frees caller memory.
+ *  - Every call returns an m1_status; nothing is thrown across the ABI.
+ *  - A grid is used by one host thread at a time (calls on one grid are not
+ *    thread safe); different grids are independent.
+ */
+#ifndef M1_H
+#define M1_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m1_grid* m1_grid_t;
+
+typedef enum {
+    M1_OK = 0,
+    M1_PENDING = 1,
+    M1_ERR_INVALID_ARG = -1,          /* bad size, pointer, level count or parameter */
+    M1_ERR_NONADMISSIBLE_INPUT = -2,  /* E <= 0, T <= 0, |F| > c E, sigma < 0 or non-finite */
+    M1_ERR_OOM = -3,                  /* device allocation failed */
+    M1_ERR_NOT_CONVERGED = -4,        /* max_cycles reached; the last iterate is kept */
+    M1_ERR_CUDA = -5,                 /* a CUDA call failed (see m1_last_error) */
+    M1_ERR_TIMEOUT = -6,
+    M1_ERR_REJECTED = -7
+} m1_status;
+
+/* Boundary conditions per wall (west, east, south, north).  The paper only asks
+ * for "appropriate boundary conditions" (Section 4.2); each is one ghost cell:
+ *   PERIODIC wrap; REFLECT mirror cell with the wall-normal flux negated;
+ *   NEUMANN copy of the boundary cell; INFLOW prescribed (E, Fx, Fy) set by
+ *   m1_set_inflow (T copied from the boundary cell). */
+typedef enum { M1_BC_PERIODIC = 0, M1_BC_REFLECT = 1, M1_BC_NEUMANN = 2, M1_BC_INFLOW = 3 } m1_bc;
+
+typedef enum { M1_FP64 = 0, M1_MIXED = 1 } m1_precision;
+
+/* Grid description.  lx, ly: domain lengths (cells hx = lx/nx, hy = ly/ny);
+ * lmax: number of multigrid levels counting the fine grid (Section 5, "L_max";
+ * lmax = 1 is plain Jacobi); nx (and ny in 2D) must be divisible by 2^(lmax-1).
+ * c, a_r, c_v: speed of light, radiation constant, gas heat capacity. */
+typedef struct {
+    int dim, nx, ny;
+    double lx, ly;
+    int bc[4];
+    int lmax;
+    double c, a_r, c_v;
+    int precision;   /* m1_precision */
+} m1_grid_desc;
+
+/* Solver parameters of Algorithm 4 (Appendix A).  Section 5 fixes nu0 = 3 (fine
+ * pre/post smoothing sweeps), nu_l = 1 (Jacobi sweeps per pseudo-time step on
+ * coarse levels), m_pseudo = 3 (pseudo-time steps), dtau0 = 1e-3.  The paper
+ * leaves the rest open; defaults (m1_default_params): m_coarse = 3, grow 1.1,
+ * shrink 0.5 (Algorithm 4), eps_i = 1e-2, eps_d = 1e-4, tol = 1e-8 (relative to
+ * the initial residual), dtau clamped to [1e-12, 1e6], theta_ex = 0.5 (fraction
+ * of the admissible explicit pseudo-time step), theta_c = 0.5 (damping of an
+ * inadmissible prolongated cell), max_cycles = 20000. */
+typedef struct {
+    int nu0, nu_l, m_pseudo, m_coarse;
+    double dtau0, grow, shrink, eps_i, eps_d, tol, dtau_min, dtau_max, theta_ex, theta_c;
+    int max_cycles;
+} m1_solve_params;
+
+/* Statistics of one implicit step.  res0/res: ||r|| before the first and after
+ * the last V-cycle, ||r||^2 = sum over cells h^d (rE^2 + |rF|^2/c^2 + rT^2);
+ * sweeps: fine-level Jacobi sweeps; ms: device time of the step. */
+typedef struct {
+    int cycles;
+    double res0, res, dtau_final;
+    long long sweeps;
+    double ms;
+    int status;
+    unsigned int newton_fail, damped;
+    long long launches;   /* kernels this call launched (cycles queued past convergence included) */
+} m1_step_stats;
+
+/* Fills *p with the defaults listed above. */
+m1_status m1_default_params(m1_solve_params* p);
+
+/* Allocates the level hierarchy of `desc` on the current CUDA device.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a stream owned by the grid.
+ * Errors: INVALID_ARG (sizes, lmax, dim), OOM, CUDA. */
+m1_status m1_create_grid(const m1_grid_desc* desc, void* cuda_stream, m1_grid_t* out);
+m1_status m1_destroy_grid(m1_grid_t g);
+
+/* Sets the state v^n (E, Fx, Fy, T per cell) and the opacities sigma_a,
+ * sigma_s (constant during a step; restricted by full weighting to the coarse
+ * levels).  Checks admissibility (Eq. (7): E > 0, |F| <= c E; and T > 0,
+ * sigma >= 0, all finite): NONADMISSIBLE_INPUT leaves the grid unchanged.
+ * sig_a / sig_s may be NULL to keep the previous opacities. */
+m1_status m1_set_state(m1_grid_t g, const double* E, const double* Fx, const double* Fy,
+                       const double* T, const double* sig_a, const double* sig_s, int on_device);
+
+/* Prescribed ghost state of an inflow wall (side 0..3 = W, E, S, N): host
+ * arrays of length ny (W/E) or nx (S/N).  The coarse levels see its
+ * full-weighting restriction along the wall. */
+m1_status m1_set_inflow(m1_grid_t g, int side, const double* E, const double* Fx, const double* Fy);
+
+/* Copies the current state out (v^{n+1} after a step). Fy may be NULL. */
+m1_status m1_get_state(m1_grid_t g, double* E, double* Fx, double* Fy, double* T, int on_device);
+
+/* One implicit time step of length dt (Algorithm 4): b = (E^n, F^n, C_v T^n),
+ * V-cycles until ||r|| <= tol ||r_0|| (or ||r_0|| <= 1e-14 ||b||), the state
+ * becomes v^{n+1}.  params may be NULL for the defaults; stats may be NULL.
+ * Returns NOT_CONVERGED after max_cycles with the last (admissible) iterate
+ * kept as the state.  Blocks until the step is done. */
+m1_status m1_implicit_step(m1_grid_t g, double dt, const m1_solve_params* params,
+                           m1_step_stats* stats);
+
+/* Algorithm 1 alone (the Jacobi method of Section 3, timed in the paper's
+ * Table 1): b = (E, F, C_v T) of the current state, then `sweeps` nonlinear
+ * Jacobi sweeps of A(v) = b starting from the current state, which becomes the
+ * result.  Asynchronous: the sweeps are queued on the grid's stream and the call
+ * returns; synchronise that stream before reading the state from another stream. */
+m1_status m1_jacobi(m1_grid_t g, double dt, int sweeps);
+
+/* ||b - A(v)|| (the norm above) of the current state v for a step of length dt,
+ * with b the right-hand side of the last implicit step taken on this grid with
+ * the same dt, or b = (E, F, C_v T) of the current state if there was none. */
+m1_status m1_residual_norm(m1_grid_t g, double dt, double* out);
+
+/* Residual history of the last step: hist[k] = ||r_k||, k = 0..cycles (up to
+ * len entries); dtau[k] = implicit pseudo-time step used in cycle k+1. */
+m1_status m1_step_history(m1_grid_t g, double* hist, double* dtau, int len);
+
+/* ---- single-kernel entry points (one kernel on caller data, for checks) ----
+ * Stateless: each call allocates its own device buffers for `desc` (lmax is
+ * ignored; precision selects FP64 or FP32 arithmetic), runs one kernel on the
+ * current device and copies the result to host memory.  Host arrays are planar
+ * [4][ny*nx] (E, Fx, Fy, T) for states and [2][ny*nx] (sigma_a, sigma_s) for
+ * opacities; inflow is [4 walls][3 fields][max(nx, ny)] or NULL.
+ *
+ * m1_op_level modes:
+ *   M1_OP_APPLY     out = A(state)                         (Eq. (12) + sources)
+ *   M1_OP_RESIDUAL  out = rhs - A(state), *norm = ||out||  (Eq. (13))
+ *   M1_OP_FAS_RHS   out = A(state) + rhs                   (Eq. (24))
+ *   M1_OP_JACOBI    out = one Jacobi sweep of A(u) = rhs from u = state
+ *                                                          (Algorithm 1)
+ *   M1_OP_PSEUDO    out = one pseudo-time step with source f = rhs: explicit
+ *                   limited half then one Jacobi sweep of u + dtau A(u) = u~
+ *                   (Eq. (30), Algorithm 3), theta_ex = theta */
+enum { M1_OP_APPLY = 0, M1_OP_RESIDUAL = 1, M1_OP_FAS_RHS = 2, M1_OP_JACOBI = 3, M1_OP_PSEUDO = 4 };
+m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt, const double* sig,
+                      const double* state, const double* rhs, int mode, double dtau, double theta,
+                      double* out, double* norm);
+
+/* Full weighting (Section 4.2, Eq. (21)/(22)) of a fine state (STATE ghosts) and
+ * a fine residual (DIFF ghosts: zero at inflow walls) to the coarse grid
+ * (nx/2 x ny/2; ny stays 1 in 1D).  Outputs are planar [4][coarse cells]. */
+m1_status m1_op_restrict(const m1_grid_desc* fine, const double* inflow, const double* state,
+                         const double* resid, double* coarse_state, double* coarse_resid);
+
+/* Prolongation of the coarse correction uc - vc onto the fine iterate uf with
+ * the damping of inadmissible cells (Eq. (18), Eq. (34), theta_c = theta);
+ * *damped = number of damped cells. */
+m1_status m1_op_prolong_correct(const m1_grid_desc* fine, const double* uc, const double* vc,
+                                const double* uf, double theta, double* out, int* damped);
+
+/* Text of the last CUDA error seen by this thread's calls (static storage). */
+const char* m1_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M1_H */

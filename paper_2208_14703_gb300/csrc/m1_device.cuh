@@ -1,0 +1,276 @@
+// Device-side data structures and per-cell arithmetic of the implicit M1
+// multigrid step (Bloch, Tremblin, Gonzalez & Audit, arXiv:2208.14703).
+//
+// Layout.  A level stores its states as arrays of Cell4 {E, Fx, Fy, T}
+// (array-of-structures: one 32-byte vector load per cell in FP64, 16 bytes in
+// FP32), row-major with index j*nx + i, and the opacities as Sig2 {sa, ss}.
+// In 1D ny = 1 and Fy stays zero.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace m1 {
+
+enum Bc { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NEUMANN = 2, BC_INFLOW = 3 };
+enum Kind { KIND_STATE = 0, KIND_DIFF = 1 };
+enum Wall { WALL_W = 0, WALL_E = 1, WALL_S = 2, WALL_N = 3 };
+
+// Relative slack of the admissibility test that decides whether a prolongated
+// cell is damped (Algorithm 4): cells on the f = 1 boundary up to rounding are
+// not damped.  Same value in FP32 would be below its precision; the FP32 path
+// uses a slack scaled to its epsilon.
+template <typename R> struct Slack;
+template <> struct Slack<double> { static constexpr double v = 1e-12; };
+template <> struct Slack<float> { static constexpr float v = 1e-6f; };
+
+template <typename R> struct alignas(4 * sizeof(R)) Cell4 { R E, Fx, Fy, T; };
+template <typename R> struct alignas(2 * sizeof(R)) Sig2 { R sa, ss; };
+
+// Tile shape of the stencil kernels: 256 threads, 32 x 8 cells in 2D, 256 x 1 in 1D.
+constexpr int kThreads = 256;
+constexpr int kTx2 = 32, kTy2 = 8, kTx1 = 256;
+constexpr int kHalo = (kTx2 + 2) * (kTy2 + 2) > (kTx1 + 2) ? (kTx2 + 2) * (kTy2 + 2) : (kTx1 + 2);
+
+// One grid level as the kernels see it.  Constants that depend on the time
+// step (ax, bx, diag, cdt) are rewritten before every implicit step.
+template <typename R>
+struct Level {
+    int dim, nx, ny, n;
+    int bc[4];
+    int tx, ty, tiles_x, tiles;   // tile shape and count
+    int prof_len;                 // stride of the inflow profile table
+    R c, a_r, c_v;
+    R ax, ay, bx, by;             // c dt / h and dt / (2 h) per axis (y: 0 in 1D)
+    R diag;                       // 1 + ax + ay
+    R cdt;                        // c dt
+    double vol;                   // cell volume h^d (norm weight)
+    Cell4<R>* v;                  // restricted iterate v_l
+    Cell4<R>* u[2];               // ping-pong iterate u_l
+    Cell4<R>* f;                  // right-hand side (b at level 0, FAS rhs above)
+    Cell4<R>* r;                  // residual (restricted from below / computed here)
+    Sig2<R>* sig;                 // opacities
+    R* inflow;                    // [wall][E, Fx, Fy][prof_len] prescribed ghosts
+};
+
+// Device-resident control block of one implicit step: the cycle counter, the
+// residual norms, the implicit pseudo-time step and the stop flag.  Every kernel
+// of a captured V-cycle returns at once when `done` is set, so a CUDA graph of
+// the cycle can be relaunched past convergence without changing the result.
+struct Ctl {
+    // parameters (written by the host before the step)
+    double tol, grow, shrink, eps_i, eps_d, dtau0, dtau_min, dtau_max, theta_ex, theta_c;
+    int max_cycles, hist_len;
+    // state
+    double res0, res, res_prev, bnorm, dtau;
+    int kappa, done, status, result_buf;
+    unsigned int newton_fail, damped;
+    double* hist;                 // res_hist[kappa], length hist_len (device)
+    double* dtau_hist;            // dtau used in cycle kappa, length hist_len
+};
+
+enum CtlStatus { CTL_OK = 0, CTL_NOT_CONVERGED = -4 };
+
+// ---------------------------------------------------------------------------
+// Per-cell arithmetic.
+
+// M1 closure (Section 2.1, Eq. (5)) in the algebraically equivalent form
+//   s = sqrt(4 - 3 f^2),  (1 - chi)/2 = (s - 1)/3,  (3 chi - 1)/(2 f^2) = 3/(2 + s),
+//   P = (s - 1)/3 E I + 3/(2 + s) F F^T / (c^2 E),
+// which needs no unit vector n and is smooth at F = 0.  f^2 is clamped to 1.
+template <typename R>
+__device__ __forceinline__ void closure(R E, R Fx, R Fy, R inv_c2, R& Pxx, R& Pxy, R& Pyy)
+{
+    R iE = R(1) / E;
+    R fx = Fx * iE, fy = Fy * iE;
+    R f2 = (fx * fx + fy * fy) * inv_c2;
+    f2 = f2 < R(1) ? f2 : R(1);
+    R s = sqrt(R(4) - R(3) * f2);
+    R iso = (s - R(1)) * (R(1) / R(3));
+    R q = R(3) / (R(2) + s) * inv_c2;
+    Pxx = E * (iso + q * fx * fx);
+    Pxy = E * (q * fx * fy);
+    Pyy = E * (iso + q * fy * fy);
+}
+
+// Largest tau >= 0 with u + tau d admissible (E > 0, T > 0, |F| <= c E): the
+// smallest positive root of |F + tau dF|^2 = c^2 (E + tau dE)^2 and the linear
+// E and T bounds; +inf when none applies.
+template <typename R>
+__device__ __forceinline__ R max_admissible_step(const Cell4<R>& u, const Cell4<R>& d, R c)
+{
+    const R inf = R(INFINITY);
+    R tau = inf;
+    if (d.E < R(0)) tau = fmin(tau, -u.E / d.E);
+    if (d.T < R(0)) tau = fmin(tau, -u.T / d.T);
+    R c2 = c * c;
+    R a = d.Fx * d.Fx + d.Fy * d.Fy - c2 * d.E * d.E;
+    R b = u.Fx * d.Fx + u.Fy * d.Fy - c2 * u.E * d.E;
+    R c0 = u.Fx * u.Fx + u.Fy * u.Fy - c2 * u.E * u.E;
+    c0 = c0 > R(0) ? R(0) : c0;
+    R disc = b * b - a * c0;
+    R t = inf;
+    if (a > R(0)) {
+        R sd = sqrt(disc);
+        t = b <= R(0) ? (-b + sd) / a : -c0 / (b + sd);
+    } else if (a < R(0)) {
+        if (b > R(0) && disc >= R(0)) t = -c0 / (b + sqrt(disc));
+    } else if (b > R(0)) {
+        t = -c0 / (R(2) * b);
+    }
+    return fmin(tau, t);
+}
+
+template <typename R>
+__device__ __forceinline__ bool admissible(const Cell4<R>& s, R c)
+{
+    return s.E > R(0) && s.T > R(0) &&
+           s.Fx * s.Fx + s.Fy * s.Fy <= c * c * s.E * s.E * (R(1) + Slack<R>::v);
+}
+
+// Newton on g(T) = C T + K T^4 - R (increasing, convex for T > 0) started at
+// T0 = min(R/C, (R/K)^(1/4)), which lies at or right of the root.
+// FP32 iterations reach about 1e-7; the FP64 variant then takes two Newton
+// steps in FP64 with the FP32 reciprocal of g' (each step squares the relative
+// error up to the 1e-7 error of that reciprocal), reaching FP64 rounding.
+__device__ __forceinline__ float newton_quartic_f32(float C, float K, float Rr, bool& ok)
+{
+    float T = fminf(Rr / C, sqrtf(sqrtf(Rr / K)));
+    ok = false;
+    for (int it = 0; it < 40; ++it) {
+        float T3 = T * T * T;
+        float g = fmaf(K, T3 * T, C * T) - Rr;
+        float dg = fmaf(4.0f * K, T3, C);
+        float dT = g / dg;
+        T -= dT;
+        if (fabsf(dT) <= 4e-7f * T) { ok = true; break; }
+    }
+    return T;
+}
+
+template <typename R> struct Quartic;
+template <> struct Quartic<float> {
+    __device__ static float solve(float C, float K, float Rr, bool& ok)
+    {
+        return newton_quartic_f32(C, K, Rr, ok);
+    }
+};
+template <> struct Quartic<double> {
+    __device__ static double solve(double C, double K, double Rr, bool& ok)
+    {
+        bool ok32;
+        double T = (double)newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
+        double dT = 0.0;
+        for (int it = 0; it < 3; ++it) {
+            double T3 = T * T * T;
+            double g = fma(K, T3 * T, C * T) - Rr;
+            double dg = fma(4.0 * K, T3, C);
+            dT = g * (double)(1.0f / (float)dg);
+            T -= dT;
+            if (it >= 1 && fabs(dT) <= 1e-15 * T) break;
+        }
+        ok = fabs(dT) <= 1e-12 * T;
+        return T;
+    }
+};
+
+// Local solve D^{-1} of one cell with the backward-Euler sources:
+//   (w0 + w1 diag) E + w1 ka (E - a_r T^4)   = bE
+//   (w0 + w1 (diag + kt)) F                  = bF
+//   (w0 + w1 C_v) T - w1 ka (E - a_r T^4)    = bT
+// (w0, w1) = (0, 1): fine-level Jacobi (Algorithm 1); (1, dtau): implicit
+// pseudo-time step (Eq. (30)).  E is eliminated; the quartic in T is solved by
+// Newton; E follows.  Without absorption the T equation is linear.
+template <typename R>
+__device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, R c_v, R a_r,
+                                                R bE, R bFx, R bFy, R bT, bool& ok)
+{
+    Cell4<R> o;
+    R A = w0 + w1 * diag;
+    R k = w1 * ka;
+    R iF = R(1) / (w0 + w1 * (diag + kt));
+    o.Fx = bFx * iF;
+    o.Fy = bFy * iF;
+    R C = w0 + w1 * c_v;
+    ok = true;
+    if (k == R(0)) {
+        o.T = bT / C;
+        o.E = bE / A;
+        return o;
+    }
+    R iAk = R(1) / (A + k);
+    R K = k * A * a_r * iAk;
+    R Rr = bT + k * bE * iAk;
+    R T = Quartic<R>::solve(C, K, Rr, ok);
+    R T2 = T * T;
+    o.T = T;
+    o.E = (bE + k * a_r * T2 * T2) * iAk;
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Ghost cells: one layer per wall.  periodic: wrap; reflecting: mirror with the
+// wall-normal flux negated; Neumann: copy; inflow: the prescribed (E, Fx, Fy)
+// with T from the mirror cell.  Differences (kind DIFF) hold zero at inflow
+// walls.  A corner resolves the y wall on the cell the x wall points to, then
+// applies the x wall on top (the x wall is the outer rule).
+template <typename R>
+__device__ __forceinline__ Cell4<R> fetch(const Level<R>& L, const Cell4<R>* __restrict__ s,
+                                          int i, int j, int kind)
+{
+    const int jo = j;
+    int xrule = -1, xwall = 0, yrule = -1, ywall = 0;
+    if (i < 0 || i >= L.nx) {
+        xwall = i < 0 ? WALL_W : WALL_E;
+        int bc = L.bc[xwall];
+        if (bc == BC_PERIODIC) {
+            i = i < 0 ? i + L.nx : i - L.nx;
+        } else {
+            i = i < 0 ? -1 - i : 2 * L.nx - 1 - i;
+            xrule = bc;
+        }
+    }
+    if (j < 0 || j >= L.ny) {
+        ywall = j < 0 ? WALL_S : WALL_N;
+        int bc = L.bc[ywall];
+        if (bc == BC_PERIODIC) {
+            j = j < 0 ? j + L.ny : j - L.ny;
+        } else {
+            j = j < 0 ? -1 - j : 2 * L.ny - 1 - j;
+            yrule = bc;
+        }
+    }
+    if (kind == KIND_DIFF && (xrule == BC_INFLOW || yrule == BC_INFLOW)) {
+        Cell4<R> z = { R(0), R(0), R(0), R(0) };
+        return z;
+    }
+    Cell4<R> c = s[(size_t)j * L.nx + i];
+    if (yrule == BC_REFLECT) c.Fy = -c.Fy;
+    if (yrule == BC_INFLOW) {
+        const R* p = L.inflow + (size_t)(ywall * 3) * L.prof_len;
+        c.E = p[i]; c.Fx = p[L.prof_len + i]; c.Fy = p[2 * L.prof_len + i];
+    }
+    if (xrule == BC_REFLECT) c.Fx = -c.Fx;
+    if (xrule == BC_INFLOW) {
+        int jj = jo < 0 ? 0 : (jo >= L.ny ? L.ny - 1 : jo);
+        const R* p = L.inflow + (size_t)(xwall * 3) * L.prof_len;
+        c.E = p[jj]; c.Fx = p[L.prof_len + jj]; c.Fy = p[2 * L.prof_len + jj];
+    }
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ Sig2<R> fetch_sig(const Level<R>& L, const Sig2<R>* __restrict__ s,
+                                             int i, int j)
+{
+    if (i < 0 || i >= L.nx) {
+        if (L.bc[i < 0 ? WALL_W : WALL_E] == BC_PERIODIC) i = i < 0 ? i + L.nx : i - L.nx;
+        else i = i < 0 ? -1 - i : 2 * L.nx - 1 - i;
+    }
+    if (j < 0 || j >= L.ny) {
+        if (L.bc[j < 0 ? WALL_S : WALL_N] == BC_PERIODIC) j = j < 0 ? j + L.ny : j - L.ny;
+        else j = j < 0 ? -1 - j : 2 * L.ny - 1 - j;
+    }
+    return s[(size_t)j * L.nx + i];
+}
+
+}  // namespace m1

@@ -1,0 +1,561 @@
+// Kernels of the implicit M1 multigrid step (arXiv:2208.14703), FP64 and FP32.
+//
+//   k_sweep     one Jacobi sweep (Algorithm 1 / Eq. (10)); PSEUDO = true fuses
+//               the explicit and implicit halves of the pseudo-time step
+//               (Eq. (30), Algorithm 3) into the same sweep
+//   k_apply     A(u) for the residual r = f - A(u) (Eq. (13)) with per-tile norm
+//               partials, or the FAS right-hand side f = A(v) + r (Eq. (24))
+//   k_restrict  full-weighting restriction of the iterate and residual (Eq. (21)/(22))
+//   k_prolong   prolongation of the coarse correction (Eq. (14)/(18)) with the
+//               per-cell damping of Eq. (34)
+//   k_finalize  deterministic norm reduction, cycle counter, stop test and the
+//               adaptive implicit pseudo-time step (Algorithm 4)
+//
+// The stencil kernels stage a tile plus a one-cell halo in shared memory and
+// evaluate each cell's closure once per pass; neighbours read it from there.
+#include "m1_kernels.cuh"
+
+namespace m1 {
+
+template <typename R>
+struct Tile {
+    R E[kHalo], Fx[kHalo], Fy[kHalo], Pxx[kHalo], Pxy[kHalo], Pyy[kHalo];
+};
+
+template <typename R>
+__device__ __forceinline__ void load_level(Level<R>& dst, const Level<R>* src)
+{
+    static_assert(sizeof(Level<R>) % 8 == 0, "level descriptor size");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(Level<R>) / 8); k += blockDim.x) d[k] = s[k];
+}
+
+// Stage the tile [x0, x0+tx) x [y0, y0+ty) of state `s` with its one-cell halo
+// (no corners) and each staged cell's closure.
+template <typename R>
+__device__ __forceinline__ void load_tile(const Level<R>& L, const Cell4<R>* __restrict__ s,
+                                          int x0, int y0, Tile<R>& t)
+{
+    const int hw = L.tx + 2, hh = L.dim == 2 ? L.ty + 2 : 1, oy = L.dim == 2 ? 1 : 0;
+    const R inv_c2 = R(1) / (L.c * L.c);
+    for (int k = threadIdx.x; k < hw * hh; k += blockDim.x) {
+        int hi = k % hw, hj = k / hw;
+        int gi = x0 + hi - 1, gj = y0 + hj - oy;
+        bool edge_x = hi == 0 || hi == hw - 1, edge_y = oy && (hj == 0 || hj == hh - 1);
+        if ((edge_x && edge_y) || gi > L.nx || gj > L.ny) continue;
+        Cell4<R> c = fetch(L, s, gi, gj, KIND_STATE);
+        R pxx, pxy, pyy;
+        closure(c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
+        t.E[k] = c.E; t.Fx[k] = c.Fx; t.Fy[k] = c.Fy;
+        t.Pxx[k] = pxx; t.Pxy[k] = pxy; t.Pyy[k] = pyy;
+    }
+}
+
+// Sum of the neighbour operators L and R of Eq. (9) around staged cell `ck`
+// (2D: the x pair and the y pair of faces).
+template <typename R>
+__device__ __forceinline__ void neighbour_sum(const Level<R>& L, const Tile<R>& t, int ck,
+                                              R& NE, R& NFx, R& NFy)
+{
+    const R c = L.c;
+    const int w = ck - 1, e = ck + 1;
+    NE = L.bx * (c * (t.E[w] + t.E[e]) + (t.Fx[w] - t.Fx[e]));
+    NFx = c * L.bx * ((t.Fx[w] + t.Fx[e]) + c * (t.Pxx[w] - t.Pxx[e]));
+    NFy = c * L.bx * ((t.Fy[w] + t.Fy[e]) + c * (t.Pxy[w] - t.Pxy[e]));
+    if (L.dim == 2) {
+        const int hw = L.tx + 2, sth = ck - hw, nth = ck + hw;
+        NE += L.by * (c * (t.E[sth] + t.E[nth]) + (t.Fy[sth] - t.Fy[nth]));
+        NFx += c * L.by * ((t.Fx[sth] + t.Fx[nth]) + c * (t.Pxy[sth] - t.Pxy[nth]));
+        NFy += c * L.by * ((t.Fy[sth] + t.Fy[nth]) + c * (t.Pyy[sth] - t.Pyy[nth]));
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void tile_origin(const Level<R>& L, int tile, int& x0, int& y0)
+{
+    x0 = (tile % L.tiles_x) * L.tx;
+    y0 = (tile / L.tiles_x) * L.ty;
+}
+
+// ---------------------------------------------------------------------------
+template <typename R, bool PSEUDO>
+__global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__ Lp, int in_buf,
+                                                    int out_buf, Ctl* __restrict__ ctl)
+{
+    if (ctl->done) return;
+    __shared__ Level<R> L;
+    __shared__ Tile<R> t;
+    load_level(L, Lp);
+    __syncthreads();
+    int x0, y0;
+    tile_origin(L, blockIdx.x, x0, y0);
+    const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
+    load_tile(L, src, x0, y0, t);
+    __syncthreads();
+    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+    const int i = x0 + lx, j = y0 + ly;
+    if (i >= L.nx || j >= L.ny) return;
+    const size_t k = (size_t)j * L.nx + i;
+    const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+    R NE, NFx, NFy;
+    neighbour_sum(L, t, ck, NE, NFx, NFy);
+    const Cell4<R> b = L.f[k];
+    const Sig2<R> sg = L.sig[k];
+    const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+    bool ok;
+    Cell4<R> out;
+    if (!PSEUDO) {
+        out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE, b.Fx + NFx,
+                             b.Fy + NFy, b.T, ok);
+    } else {
+        // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*) (tau* = the
+        // largest admissible step along f); implicit half: one Jacobi sweep of
+        // u + dtau A(u) = u~ from the old iterate
+        const R dtau = (R)ctl->dtau;
+        const Cell4<R> u = src[k];
+        R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(u, b, L.c));
+        out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
+                             u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
+                             u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+    }
+    if (!ok) atomicAdd(&ctl->newton_fail, 1u);
+    L.u[out_buf][k] = out;
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__ Lp, int state_buf,
+                                                    double* __restrict__ partials, int write_r,
+                                                    Ctl* __restrict__ ctl)
+{
+    if (ctl && ctl->done) return;
+    __shared__ Level<R> L;
+    __shared__ Tile<R> t;
+    __shared__ double red[kThreads / 32];
+    load_level(L, Lp);
+    __syncthreads();
+    int x0, y0;
+    tile_origin(L, blockIdx.x, x0, y0);
+    const Cell4<R>* __restrict__ src = state_buf < 0 ? L.v : L.u[state_buf];
+    load_tile(L, src, x0, y0, t);
+    __syncthreads();
+    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+    const int i = x0 + lx, j = y0 + ly;
+    double nrm = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const size_t k = (size_t)j * L.nx + i;
+        const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+        R NE, NFx, NFy;
+        neighbour_sum(L, t, ck, NE, NFx, NFy);
+        const Cell4<R> u = src[k];
+        const Sig2<R> sg = L.sig[k];
+        const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+        const R T2 = u.T * u.T;
+        const R src_e = ka * (u.E - L.a_r * T2 * T2);
+        Cell4<R> a;
+        a.E = L.diag * u.E + src_e - NE;
+        a.Fx = (L.diag + kt) * u.Fx - NFx;
+        a.Fy = (L.diag + kt) * u.Fy - NFy;
+        a.T = L.c_v * u.T - src_e;
+        if (MODE == APPLY_RESID) {
+            const Cell4<R> f = L.f[k];
+            Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
+            if (write_r) L.r[k] = r;
+            const double ic2 = 1.0 / ((double)L.c * (double)L.c);
+            nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
+                  (double)r.T * r.T;
+        } else if (MODE == APPLY_FAS) {
+            const Cell4<R> r = L.r[k];
+            Cell4<R> o = { a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
+            L.f[k] = o;
+        } else {
+            L.r[k] = a;
+        }
+    }
+    if (MODE == APPLY_RESID && partials) {
+        double s = block_sum<R>(nrm, red);
+        if (threadIdx.x == 0) partials[blockIdx.x] = s * L.vol;
+    }
+}
+
+// Norm of a whole state (used for ||b||): per-tile partials.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restrict__ Lp,
+                                                         const Cell4<R>* __restrict__ s,
+                                                         double* __restrict__ partials)
+{
+    __shared__ Level<R> L;
+    __shared__ double red[kThreads / 32];
+    load_level(L, Lp);
+    __syncthreads();
+    int x0, y0;
+    tile_origin(L, blockIdx.x, x0, y0);
+    const int i = x0 + threadIdx.x % L.tx, j = y0 + threadIdx.x / L.tx;
+    double nrm = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const Cell4<R> r = s[(size_t)j * L.nx + i];
+        const double ic2 = 1.0 / ((double)L.c * (double)L.c);
+        nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
+              (double)r.T * r.T;
+    }
+    double sum = block_sum<R>(nrm, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum * L.vol;
+}
+
+// ---------------------------------------------------------------------------
+// Full weighting, coarse cell (ic, jc) <- fine cells 2ic-1..2ic+1 (x) and
+// 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restrict__ Lfp,
+                                                       const Level<R>* __restrict__ Lcp,
+                                                       int fine_buf, Ctl* __restrict__ ctl)
+{
+    if (ctl && ctl->done) return;
+    __shared__ Level<R> Lf, Lc;
+    load_level(Lf, Lfp);
+    load_level(Lc, Lcp);
+    __syncthreads();
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= Lc.n) return;
+    const int ic = kc % Lc.nx, jc = kc / Lc.nx;
+    const R w[3] = { R(0.25), R(0.5), R(0.25) };
+    const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
+    Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 };
+    const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+    for (int b = b0; b <= b1; ++b) {
+        const R wy = Lf.dim == 2 ? w[b + 1] : R(1);
+        const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+        for (int a = -1; a <= 1; ++a) {
+            const R wt = wy * w[a + 1];
+            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, KIND_STATE);
+            const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
+            av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
+            ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+        }
+    }
+    Lc.v[kc] = av;
+    Lc.r[kc] = ar;
+}
+
+template <typename R>
+__global__ void k_restrict_sig(const Level<R>* __restrict__ Lfp, const Level<R>* __restrict__ Lcp)
+{
+    __shared__ Level<R> Lf, Lc;
+    load_level(Lf, Lfp);
+    load_level(Lc, Lcp);
+    __syncthreads();
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= Lc.n) return;
+    const int ic = kc % Lc.nx, jc = kc / Lc.nx;
+    const R w[3] = { R(0.25), R(0.5), R(0.25) };
+    Sig2<R> acc = { 0, 0 };
+    const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+    for (int b = b0; b <= b1; ++b) {
+        const R wy = Lf.dim == 2 ? w[b + 1] : R(1);
+        const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+        for (int a = -1; a <= 1; ++a) {
+            const Sig2<R> s = fetch_sig(Lf, Lf.sig, 2 * ic + a, jf);
+            acc.sa += wy * w[a + 1] * s.sa;
+            acc.ss += wy * w[a + 1] * s.ss;
+        }
+    }
+    Lc.sig[kc] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// u_l += P(u_{l+1} - v_{l+1}) per fine cell (fine 2i <- coarse i, fine 2i+1 <-
+// half of coarse i and i+1; tensor product in 2D); a target outside the
+// admissible set is replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ Lcp,
+                                                      const Level<R>* __restrict__ Lfp,
+                                                      int coarse_buf, int fine_buf,
+                                                      Ctl* __restrict__ ctl)
+{
+    if (ctl->done) return;
+    __shared__ Level<R> Lf, Lc;
+    load_level(Lf, Lfp);
+    load_level(Lc, Lcp);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Lf.n) return;
+    const int i = k % Lf.nx, j = k / Lf.nx;
+    const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
+    const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
+    const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
+    const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
+    Cell4<R> pe = { 0, 0, 0, 0 };
+    for (int b = 0; b <= oy; ++b)
+        for (int a = 0; a <= ox; ++a) {
+            const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
+            const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
+            pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
+            pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
+        }
+    Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
+    const Cell4<R> u = uf[k];
+    Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
+    if (!admissible(tg, Lf.c)) {
+        R ts = max_admissible_step(u, pe, Lf.c);
+        R th = (R)ctl->theta_c * fmin(R(1), ts);
+        tg.E = u.E + th * pe.E; tg.Fx = u.Fx + th * pe.Fx;
+        tg.Fy = u.Fy + th * pe.Fy; tg.T = u.T + th * pe.T;
+        atomicAdd(&ctl->damped, 1u);
+    }
+    uf[k] = tg;
+}
+
+// ---------------------------------------------------------------------------
+// b = (E^n, F^n, C_v T^n) of the iterate in buffer `buf` (Algorithm 4).
+template <typename R>
+__global__ void k_make_rhs(const Level<R>* __restrict__ Lp, int buf)
+{
+    __shared__ Level<R> L;
+    load_level(L, Lp);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.n) return;
+    Cell4<R> s = L.u[buf][k];
+    s.T *= L.c_v;
+    L.f[k] = s;
+}
+
+// Deterministic reduction of per-tile partials (fixed order: thread t sums
+// entries t, t+256, ... then a fixed tree), then the control logic.
+__device__ double block_reduce_fixed(const double* __restrict__ p, int n, double* red)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += p[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctl,
+                                                       const double* __restrict__ part, int np,
+                                                       const double* __restrict__ partb, int npb,
+                                                       int mode, int cur)
+{
+    __shared__ double red[kThreads];
+    if (mode == FIN_CYCLE && ctl->done) return;
+    const double s = block_reduce_fixed(part, np, red);
+    double sb = 0.0;
+    if (mode == FIN_INIT) sb = block_reduce_fixed(partb, npb, red);
+    if (threadIdx.x != 0) return;
+    const double res = sqrt(s);
+    if (mode == FIN_INIT) {
+        ctl->res0 = res; ctl->res = res; ctl->res_prev = res;
+        ctl->bnorm = sqrt(sb);
+        ctl->dtau = ctl->dtau0;
+        ctl->kappa = 0;
+        if (ctl->hist_len > 0) ctl->hist[0] = res;
+        ctl->result_buf = cur;
+        if (res <= 1e-14 * ctl->bnorm) { ctl->done = 1; ctl->status = CTL_OK; }
+        else { ctl->done = 0; ctl->status = CTL_NOT_CONVERGED; }
+        return;
+    }
+    const int kappa = ++ctl->kappa;
+    ctl->res = res;
+    if (kappa < ctl->hist_len) { ctl->hist[kappa] = res; ctl->dtau_hist[kappa - 1] = ctl->dtau; }
+    ctl->result_buf = cur;
+    if (res <= ctl->tol * ctl->res0) { ctl->done = 1; ctl->status = CTL_OK; return; }
+    const double delta = fabs(res - ctl->res_prev) / ctl->res0;
+    double dtau = ctl->dtau;
+    if (delta > ctl->eps_i) dtau *= ctl->grow;
+    if (delta < ctl->eps_d) dtau *= ctl->shrink;
+    dtau = dtau < ctl->dtau_min ? ctl->dtau_min : (dtau > ctl->dtau_max ? ctl->dtau_max : dtau);
+    ctl->dtau = dtau;
+    ctl->res_prev = res;
+    if (kappa >= ctl->max_cycles) { ctl->done = 1; ctl->status = CTL_NOT_CONVERGED; }
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversion: planar FP64 E | Fx | Fy | T (caller's arrays) <-> Cell4<R>.
+template <typename R>
+__global__ void k_pack_state(const double* __restrict__ E, const double* __restrict__ Fx,
+                             const double* __restrict__ Fy, const double* __restrict__ T,
+                             double tscale, Cell4<R>* __restrict__ out, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    Cell4<R> c = { (R)E[k], (R)Fx[k], Fy ? (R)Fy[k] : R(0), (R)(T[k] * tscale) };
+    out[k] = c;
+}
+
+template <typename R>
+__global__ void k_unpack_state(const Cell4<R>* __restrict__ in, double* __restrict__ E,
+                               double* __restrict__ Fx, double* __restrict__ Fy,
+                               double* __restrict__ T, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const Cell4<R> c = in[k];
+    E[k] = c.E; Fx[k] = c.Fx;
+    if (Fy) Fy[k] = c.Fy;
+    T[k] = c.T;
+}
+
+template <typename R>
+__global__ void k_pack_sig(const double* __restrict__ sa, const double* __restrict__ ss,
+                           Sig2<R>* __restrict__ out, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    Sig2<R> s = { (R)sa[k], (R)ss[k] };
+    out[k] = s;
+}
+
+// Admissibility and finiteness check of an input state: counts bad cells.
+template <typename R>
+__global__ void k_check_state(const Cell4<R>* __restrict__ s, const Sig2<R>* __restrict__ sig,
+                              int n, R c, unsigned int* __restrict__ bad)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const Cell4<R> u = s[k];
+    bool ok = isfinite(u.E) && isfinite(u.Fx) && isfinite(u.Fy) && isfinite(u.T) && u.E > R(0) &&
+              u.T > R(0) && u.Fx * u.Fx + u.Fy * u.Fy <= c * c * u.E * u.E * (R(1) + Slack<R>::v);
+    if (sig) {
+        const Sig2<R> g = sig[k];
+        ok = ok && isfinite(g.sa) && isfinite(g.ss) && g.sa >= R(0) && g.ss >= R(0);
+    }
+    if (!ok) atomicAdd(bad, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+template <typename R>
+void launch_sweep(const Level<R>* dL, const Level<R>& hL, bool pseudo, int in_buf, int out_buf,
+                  Ctl* ctl, cudaStream_t s)
+{
+    if (pseudo) k_sweep<R, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
+    else k_sweep<R, false><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
+}
+
+template <typename R>
+void launch_apply(const Level<R>* dL, const Level<R>& hL, int mode, int state_buf,
+                  double* partials, int write_r, Ctl* ctl, cudaStream_t s)
+{
+    if (mode == APPLY_RESID)
+        k_apply<R, APPLY_RESID><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+    else if (mode == APPLY_FAS)
+        k_apply<R, APPLY_FAS><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+    else
+        k_apply<R, APPLY_A><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+}
+
+template <typename R>
+void launch_norm_state(const Level<R>* dL, const Level<R>& hL, const Cell4<R>* st,
+                       double* partials, cudaStream_t s)
+{
+    k_norm_state<R><<<hL.tiles, kThreads, 0, s>>>(dL, st, partials);
+}
+
+template <typename R>
+void launch_restrict(const Level<R>* dLf, const Level<R>* dLc, const Level<R>& hLc, int fine_buf,
+                     Ctl* ctl, cudaStream_t s)
+{
+    k_restrict<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
+}
+
+template <typename R>
+void launch_restrict_sig(const Level<R>* dLf, const Level<R>* dLc, const Level<R>& hLc,
+                         cudaStream_t s)
+{
+    k_restrict_sig<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc);
+}
+
+template <typename R>
+void launch_prolong(const Level<R>* dLc, const Level<R>* dLf, const Level<R>& hLf, int coarse_buf,
+                    int fine_buf, Ctl* ctl, cudaStream_t s)
+{
+    k_prolong<R><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
+}
+
+template <typename R>
+void launch_make_rhs(const Level<R>* dL, const Level<R>& hL, int buf, cudaStream_t s)
+{
+    k_make_rhs<R><<<cdiv(hL.n, kThreads), kThreads, 0, s>>>(dL, buf);
+}
+
+void launch_finalize(Ctl* ctl, const double* part, int np, const double* partb, int npb, int mode,
+                     int cur, cudaStream_t s)
+{
+    k_finalize<<<1, kThreads, 0, s>>>(ctl, part, np, partb, npb, mode, cur);
+}
+
+template <typename R>
+void launch_pack_state(const double* E, const double* Fx, const double* Fy, const double* T,
+                       double tscale, Cell4<R>* out, int n, cudaStream_t s)
+{
+    k_pack_state<R><<<cdiv(n, kThreads), kThreads, 0, s>>>(E, Fx, Fy, T, tscale, out, n);
+}
+
+template <typename R>
+void launch_unpack_state(const Cell4<R>* in, double* E, double* Fx, double* Fy, double* T, int n,
+                         cudaStream_t s)
+{
+    k_unpack_state<R><<<cdiv(n, kThreads), kThreads, 0, s>>>(in, E, Fx, Fy, T, n);
+}
+
+template <typename R>
+void launch_pack_sig(const double* sa, const double* ss, Sig2<R>* out, int n, cudaStream_t s)
+{
+    k_pack_sig<R><<<cdiv(n, kThreads), kThreads, 0, s>>>(sa, ss, out, n);
+}
+
+template <typename R>
+void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c, unsigned int* bad,
+                        cudaStream_t s)
+{
+    k_check_state<R><<<cdiv(n, kThreads), kThreads, 0, s>>>(st, sig, n, (R)c, bad);
+}
+
+#define M1_INSTANTIATE(R)                                                                          \
+    template void launch_sweep<R>(const Level<R>*, const Level<R>&, bool, int, int, Ctl*,         \
+                                  cudaStream_t);                                                   \
+    template void launch_apply<R>(const Level<R>*, const Level<R>&, int, int, double*, int, Ctl*, \
+                                  cudaStream_t);                                                   \
+    template void launch_norm_state<R>(const Level<R>*, const Level<R>&, const Cell4<R>*,         \
+                                       double*, cudaStream_t);                                     \
+    template void launch_restrict<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, Ctl*,\
+                                     cudaStream_t);                                                \
+    template void launch_restrict_sig<R>(const Level<R>*, const Level<R>*, const Level<R>&,       \
+                                         cudaStream_t);                                            \
+    template void launch_prolong<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, int,  \
+                                    Ctl*, cudaStream_t);                                           \
+    template void launch_make_rhs<R>(const Level<R>*, const Level<R>&, int, cudaStream_t);        \
+    template void launch_pack_state<R>(const double*, const double*, const double*, const double*,\
+                                       double, Cell4<R>*, int, cudaStream_t);                      \
+    template void launch_unpack_state<R>(const Cell4<R>*, double*, double*, double*, double*, int,\
+                                         cudaStream_t);                                            \
+    template void launch_pack_sig<R>(const double*, const double*, Sig2<R>*, int, cudaStream_t);  \
+    template void launch_check_state<R>(const Cell4<R>*, const Sig2<R>*, int, double,             \
+                                        unsigned int*, cudaStream_t);
+
+M1_INSTANTIATE(double)
+M1_INSTANTIATE(float)
+
+}  // namespace m1

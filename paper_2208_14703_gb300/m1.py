@@ -1,0 +1,259 @@
+"""Python binding of libm1 (include/m1.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all the
+arithmetic of the implicit M1 step runs in the CUDA kernels of libm1.so.  The
+module raises at import time if libm1.so has not been built, so nothing can
+silently run without the CUDA library.
+
+Arrays: numpy float64 (host) or torch CUDA float64 tensors (device).  States
+are passed per field (E, Fx, Fy, T), each of shape (ny, nx) or (nx,) in 1D.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libm1.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libm1.so is not built ({_LIB_PATH}); run "
+                      "`python -m paper_2208_14703_gb300.build` (needs nvcc)")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+OK, PENDING, ERR_INVALID_ARG, ERR_NONADMISSIBLE_INPUT, ERR_OOM, ERR_NOT_CONVERGED, ERR_CUDA, \
+    ERR_TIMEOUT, ERR_REJECTED = 0, 1, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "NONADMISSIBLE_INPUT", -3: "OOM",
+                -4: "NOT_CONVERGED", -5: "CUDA", -6: "TIMEOUT", -7: "REJECTED"}
+BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
+FP64, MIXED = 0, 1
+OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
+
+EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
+           "m1_set_inflow", "m1_get_state", "m1_implicit_step", "m1_residual_norm",
+           "m1_step_history", "m1_jacobi", "m1_op_level", "m1_op_restrict", "m1_op_prolong_correct",
+           "m1_last_error"]
+
+
+class M1Error(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = f"{what}: {STATUS_NAMES.get(status, status)}"
+        err = _lib.m1_last_error().decode()
+        if status == ERR_CUDA and err:
+            msg += f" ({err})"
+        super().__init__(msg)
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("bc", ctypes.c_int * 4),
+                ("lmax", ctypes.c_int), ("c", ctypes.c_double), ("a_r", ctypes.c_double),
+                ("c_v", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("nu0", ctypes.c_int), ("nu_l", ctypes.c_int), ("m_pseudo", ctypes.c_int),
+                ("m_coarse", ctypes.c_int), ("dtau0", ctypes.c_double),
+                ("grow", ctypes.c_double), ("shrink", ctypes.c_double),
+                ("eps_i", ctypes.c_double), ("eps_d", ctypes.c_double),
+                ("tol", ctypes.c_double), ("dtau_min", ctypes.c_double),
+                ("dtau_max", ctypes.c_double), ("theta_ex", ctypes.c_double),
+                ("theta_c", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("dtau_final", ctypes.c_double), ("sweeps", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("status", ctypes.c_int),
+                ("newton_fail", ctypes.c_uint), ("damped", ctypes.c_uint),
+                ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_lib.m1_last_error.restype = ctypes.c_char_p
+_lib.m1_default_params.argtypes = [ctypes.POINTER(SolveParams)]
+_lib.m1_create_grid.argtypes = [ctypes.POINTER(GridDesc), _vp, ctypes.POINTER(_vp)]
+_lib.m1_destroy_grid.argtypes = [_vp]
+_lib.m1_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.m1_set_inflow.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+_lib.m1_get_state.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.m1_implicit_step.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(SolveParams),
+                                  ctypes.POINTER(StepStats)]
+_lib.m1_residual_norm.argtypes = [_vp, ctypes.c_double, _dp]
+_lib.m1_step_history.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_lib.m1_jacobi.argtypes = [_vp, ctypes.c_double, ctypes.c_int]
+_lib.m1_op_level.argtypes = [ctypes.POINTER(GridDesc), _vp, ctypes.c_double, _vp, _vp, _vp,
+                             ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _dp]
+_lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
+_lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
+                                       _vp, ctypes.POINTER(ctypes.c_int)]
+
+
+def _check(status, what, allow=()):
+    if status != OK and status not in allow:
+        raise M1Error(status, what)
+    return status
+
+
+def _ptr(a):
+    """Data pointer of a numpy array (host) or a torch tensor (device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _host(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_desc(dim, nx, ny, lx, ly, bc, lmax, c=1.0, a_r=1.0, c_v=1.0, precision=FP64):
+    d = GridDesc()
+    d.dim, d.nx, d.ny = dim, nx, ny if dim == 2 else 1
+    d.lx, d.ly = lx, ly
+    for k, b in enumerate(bc):
+        d.bc[k] = BC[b] if isinstance(b, str) else int(b)
+    d.lmax, d.c, d.a_r, d.c_v, d.precision = lmax, c, a_r, c_v, precision
+    return d
+
+
+def desc_from_case(case, lmax=None, precision=FP64):
+    s = case["desc"]
+    return make_desc(s["dim"], s["nx"], s["ny"], s["lx"], s["ly"], s["bc"],
+                     case["lmax"] if lmax is None else lmax, s["c"], s["a_r"], s["c_v"], precision)
+
+
+def m1_default_params(**overrides) -> SolveParams:
+    p = SolveParams()
+    _check(_lib.m1_default_params(ctypes.byref(p)), "m1_default_params")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Grid:
+    """Owner of one m1_grid_t (m1_create_grid / m1_destroy_grid)."""
+
+    def __init__(self, desc: GridDesc, stream=None):
+        h = _vp()
+        _check(_lib.m1_create_grid(ctypes.byref(desc), stream, ctypes.byref(h)), "m1_create_grid")
+        self.h = h
+        self.desc = desc
+
+    def close(self):
+        if self.h:
+            _lib.m1_destroy_grid(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.desc.ny, self.desc.nx)
+
+    def set_state(self, E, Fx, Fy, T, sig_a=None, sig_s=None, on_device=False):
+        if not on_device:
+            E, Fx, Fy, T, sig_a, sig_s = map(_host, (E, Fx, Fy, T, sig_a, sig_s))
+        st = _lib.m1_set_state(self.h, _ptr(E), _ptr(Fx), _ptr(Fy), _ptr(T), _ptr(sig_a),
+                               _ptr(sig_s), int(on_device))
+        return _check(st, "m1_set_state")
+
+    def set_inflow(self, side, E, Fx, Fy):
+        E, Fx, Fy = map(_host, (E, Fx, Fy))
+        return _check(_lib.m1_set_inflow(self.h, side, _ptr(E), _ptr(Fx), _ptr(Fy)),
+                      "m1_set_inflow")
+
+    def get_state(self, out=None, on_device=False):
+        """Returns (E, Fx, Fy, T) as host arrays, or fills `out` (4 arrays/tensors)."""
+        if out is None:
+            out = [np.zeros(self.shape) for _ in range(4)]
+        st = _lib.m1_get_state(self.h, *[_ptr(a) for a in out], int(on_device))
+        _check(st, "m1_get_state")
+        return out
+
+    def implicit_step(self, dt, params: SolveParams | None = None, allow_not_converged=False):
+        stats = StepStats()
+        st = _lib.m1_implicit_step(self.h, dt, ctypes.byref(params) if params else None,
+                                   ctypes.byref(stats))
+        _check(st, "m1_implicit_step", allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return stats
+
+    def jacobi(self, dt, sweeps):
+        """Queue `sweeps` Jacobi sweeps (Algorithm 1) on the grid's stream."""
+        return _check(_lib.m1_jacobi(self.h, dt, sweeps), "m1_jacobi")
+
+    def residual_norm(self, dt):
+        out = ctypes.c_double()
+        _check(_lib.m1_residual_norm(self.h, dt, ctypes.byref(out)), "m1_residual_norm")
+        return out.value
+
+    def step_history(self, length):
+        hist = np.zeros(length)
+        dtau = np.zeros(length)
+        _check(_lib.m1_step_history(self.h, _ptr(hist), _ptr(dtau), length), "m1_step_history")
+        return hist, dtau
+
+
+def grid_from_case(case, lmax=None, precision=FP64, stream=None) -> Grid:
+    """A grid holding the state, opacities and inflow of an input case."""
+    g = Grid(desc_from_case(case, lmax, precision), stream)
+    s = case["state"]
+    g.set_state(s[0], s[1], s[2], s[3], case["sa"], case["ss"])
+    if case.get("inflow") is not None:
+        d = case["desc"]
+        for w in range(4):
+            if d["bc"][w] == "inflow":
+                n = d["ny"] if w < 2 else d["nx"]
+                g.set_inflow(w, *[case["inflow"][w, f, :n] for f in range(3)])
+    return g
+
+
+def m1_op_level(desc, dt, sig, state, rhs=None, mode=OP_APPLY, dtau=0.0, theta=0.5, inflow=None):
+    n = desc.nx * desc.ny
+    state = _host(state).reshape(4, n)
+    sig = _host(sig).reshape(2, n)
+    rhs = None if rhs is None else _host(rhs).reshape(4, n)
+    inflow = _host(inflow)
+    out = np.zeros((4, n))
+    nrm = ctypes.c_double()
+    st = _lib.m1_op_level(ctypes.byref(desc), _ptr(inflow), dt, _ptr(sig), _ptr(state), _ptr(rhs),
+                          mode, dtau, theta, _ptr(out), ctypes.byref(nrm))
+    _check(st, "m1_op_level")
+    return out.reshape(4, desc.ny, desc.nx), nrm.value
+
+
+def m1_op_restrict(desc, state, resid, inflow=None):
+    n = desc.nx * desc.ny
+    nc = (desc.nx // 2) * (desc.ny // 2 if desc.dim == 2 else 1)
+    state, resid = _host(state).reshape(4, n), _host(resid).reshape(4, n)
+    cs, cr = np.zeros((4, nc)), np.zeros((4, nc))
+    st = _lib.m1_op_restrict(ctypes.byref(desc), _ptr(_host(inflow)), _ptr(state), _ptr(resid),
+                             _ptr(cs), _ptr(cr))
+    _check(st, "m1_op_restrict")
+    shp = (4, desc.ny // 2 if desc.dim == 2 else 1, desc.nx // 2)
+    return cs.reshape(shp), cr.reshape(shp)
+
+
+def m1_op_prolong_correct(desc, uc, vc, uf, theta=0.5):
+    n = desc.nx * desc.ny
+    uc, vc, uf = _host(uc).reshape(4, -1), _host(vc).reshape(4, -1), _host(uf).reshape(4, n)
+    out = np.zeros((4, n))
+    damped = ctypes.c_int()
+    st = _lib.m1_op_prolong_correct(ctypes.byref(desc), _ptr(uc), _ptr(vc), _ptr(uf), theta,
+                                    _ptr(out), ctypes.byref(damped))
+    _check(st, "m1_op_prolong_correct")
+    return out.reshape(4, desc.ny, desc.nx), damped.value
