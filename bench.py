@@ -40,8 +40,6 @@ METRIC = "M1 smoother cell-updates/s"
 UNIT = "cell-updates/s"
 WORKLOAD = "m1-implicit-step-2d-fp64-1024x1024-lmax8-tol1e-8"
 N = 1024
-FP64_FMA_PER_SM_PER_CLK = 2          # GB300: 1.25 TFLOP/s nominal FP64 at 2.07 GHz, 152 SMs
-SMS = 152
 
 
 def peaks():
@@ -52,12 +50,18 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_fallback": True}
 
 
-def sweep_counts():
-    """Algorithmic work of one fine FP64 Jacobi sweep per cell (2D), counted on
-    the minimal arithmetic of the update: bytes moved and FP64 operations with
-    division and square root weighted by their cost in FMA issue slots."""
-    bytes_per_cell = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8        # read u, b, sigma; write u'
-    return bytes_per_cell
+# Algorithmic work of one fine FP64 Jacobi sweep (2D), per cell-update.
+# Bytes: read the iterate u, the right-hand side b and (sigma_a, sigma_s); write u'.
+SWEEP_BYTES = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8
+# FP64 work in FMA issue slots, counted on the minimal arithmetic of the update
+# (one closure per cell: 3 div/sqrt + 18 ops; neighbour sums: 24 ops; local
+# solve: 2 div + 22 ops + a 3-iteration Newton of 6 ops and 1 div each), with a
+# division or square root weighted by its measured cost on GB300 (FP64 FMA
+# 0.595 T/s vs 58.3 G div/s or sqrt/s: 10.2 slots).  2 flops per slot.
+DIV_SLOTS = 10.2
+SWEEP_SLOTS = (3 * DIV_SLOTS + 18) + 24 + (2 * DIV_SLOTS + 22) + 3 * (6 + DIV_SLOTS)
+SWEEP_FLOPS = 2 * SWEEP_SLOTS
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (recipe table), 152 SMs x 2 DFMA/clk x 2.07 GHz
 
 
 class ClockSampler:
@@ -180,7 +184,9 @@ def main():
     build.build()
     from paper_2208_14703_gb300 import m1
 
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream shared by the grid and the CUDA events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     grid = m1.grid_from_case(case, stream=stream.cuda_stream)
     dev = torch.device("cuda", local)
     s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).to(dev) for k in range(4)]
@@ -274,12 +280,15 @@ def main():
         e2e_val = t.item()
 
     pk = peaks()
-    bpc = sweep_counts()
-    achieved = bpc * cells / (sweep_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None,
-            "kernel": "k_sweep<double> (fine Jacobi sweep)", "kernel_ms": sweep_ms,
-            "peak_source": "measured" if not pk.get("_fallback") else "fallback"}
+    tflops = SWEEP_FLOPS * cells / (sweep_ms * 1e-3) / 1e12
+    gbs = SWEEP_BYTES * cells / (sweep_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
+            "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep_ms,
+            "peak_source": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
+            "flops_per_cell": SWEEP_FLOPS,
+            "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / pk["hbm_gbs"], "bytes_per_cell": SWEEP_BYTES}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -123,7 +123,9 @@ m1_status m1_set_inflow(m1_grid_t g, int side, const double* E, const double* Fx
 m1_status m1_get_state(m1_grid_t g, double* E, double* Fx, double* Fy, double* T, int on_device);
 
 /* One implicit time step of length dt (Algorithm 4): b = (E^n, F^n, C_v T^n),
- * V-cycles until ||r|| <= tol ||r_0|| (or ||r_0|| <= 1e-14 ||b||), the state
+ * V-cycles until ||r|| <= tol ||r_0||, the state becomes v^{n+1}; no cycle at all
+ * when ||r_0|| <= 1e-14 (1 + c dt/hx + c dt/hy) ||b|| (already solved to the
+ * rounding of A, e.g. an equilibrium state E = a_r T^4, F = 0), the state
  * becomes v^{n+1}.  params may be NULL for the defaults; stats may be NULL.
  * Returns NOT_CONVERGED after max_cycles with the last (admissible) iterate
  * kept as the state.  Blocks until the step is done. */

@@ -701,7 +701,8 @@ static int fine_jacobi(level_t* q, double dt, const double* b, double* u, int nu
  *          dtau_min, dtau_max, theta_ex (1/2), theta_c (1/2) }
  * The state v (4 planes) holds v^n on entry, v^{n+1} on return; b = (E^n, F^n,
  * C_v T^n).  Cycle loop [READINGS]:
- *  - r_0 = b - A(v^n); stop at once if ||r_0|| <= 1e-14 ||b||;
+ *  - r_0 = b - A(v^n); stop at once if ||r_0|| <= 1e-14 diag ||b||, with
+ *    diag = 1 + c dt/hx (+ c dt/hy) the transport diagonal (rounding floor);
  *  - cycle kappa = 1, 2, ...: down leg l = 0 .. L-2 (pre-smooth, residual,
  *    restriction of the smoothed iterate u_l and of the residual: standard FAS,
  *    Algorithm 2), coarsest level L-1 (pseudo-time solve; plain Jacobi sweeps
@@ -747,7 +748,9 @@ int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflo
     int kappa = 0, status = 0, newton_fail = 0, damped = 0;
     long long fine_sweeps = 0;
 
-    if (res0 > 1e-14 * bnorm) {
+    /* [READING] a right-hand side already solved to rounding: ||r_0|| below
+     * 1e-14 (1 + c dt/hx + c dt/hy) ||b||, the rounding floor of evaluating A */
+    if (res0 > 1e-14 * transport_diag(&g0, dt) * bnorm) {
         status = -4;
         while (kappa < maxc) {
             /* ---- down leg ---- */

@@ -414,6 +414,7 @@ struct Impl : ImplBase {
         c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
         c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
         c.hist_len = hist_len; c.hist = hist; c.dtau_hist = dtau_hist;
+        c.res0_floor = 1e-14 * (double)h[0].diag;   // rounding floor of evaluating A
         *ctl_h = c;
         M1_CK(cudaEventRecord(ev0, stream));
         M1_CK(cudaMemcpyAsync(ctl, ctl_h, sizeof(Ctl), cudaMemcpyHostToDevice, stream));

@@ -59,6 +59,7 @@ struct Level {
 struct Ctl {
     // parameters (written by the host before the step)
     double tol, grow, shrink, eps_i, eps_d, dtau0, dtau_min, dtau_max, theta_ex, theta_c;
+    double res0_floor;            // stop at once if ||r_0|| <= res0_floor ||b||
     int max_cycles, hist_len;
     // state
     double res0, res, res_prev, bnorm, dtau;

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctl,
         ctl->kappa = 0;
         if (ctl->hist_len > 0) ctl->hist[0] = res;
         ctl->result_buf = cur;
-        if (res <= 1e-14 * ctl->bnorm) { ctl->done = 1; ctl->status = CTL_OK; }
+        if (res <= ctl->res0_floor * ctl->bnorm) { ctl->done = 1; ctl->status = CTL_OK; }
         else { ctl->done = 0; ctl->status = CTL_NOT_CONVERGED; }
         return;
     }
