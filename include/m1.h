@@ -181,6 +181,31 @@ m1_status m1_op_restrict(const m1_grid_desc* fine, const double* inflow, const d
 m1_status m1_op_prolong_correct(const m1_grid_desc* fine, const double* uc, const double* vc,
                                 const double* uf, double theta, double* out, int* damped);
 
+/* Residual norm without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * where they need the norm -- a framework whose own pool owns all device
+ * memory, or a latency-critical loop in which a cudaMalloc (which can
+ * synchronise the whole device) is not allowed.
+ * Computes ||b - A(v)|| (the norm of m1_step_stats) for a step of length dt on
+ * the grid `desc` (lmax and precision ignored; FP64), from caller-owned device
+ * arrays: state [4][ny*nx] planar (E, Fx, Fy, T), rhs [4][ny*nx], sig [2][ny*nx]
+ * (sigma_a, sigma_s), inflow [4 walls][3][max(nx, ny)] (may be NULL when no wall
+ * is INFLOW), and writes the norm to *norm_out, a device pointer.  Queued on
+ * `cuda_stream` (NULL: the legacy default stream); returns without waiting.
+ * It allocates nothing: the per-tile partial sums go to a fixed array of 65536
+ * doubles (512 KiB) in the library's own device memory, which every GPU that
+ * loads the library holds until the process exits.  A grid needing more than
+ * 65536 tiles (32 x 8 cells in 2D, 256 in 1D; so at most 4096 x 4096 cells in
+ * 2D) is rejected with INVALID_ARG and a message in m1_last_error.  Each call
+ * overwrites the entries it reads, so nothing needs clearing, but all calls
+ * share the array: calls whose kernels overlap on the GPU (unordered streams)
+ * race on it.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture. */
+m1_status m1_residual_norm_noalloc(const m1_grid_desc* desc, double dt, const double* state,
+                                   const double* rhs, const double* sig, const double* inflow,
+                                   double* norm_out, void* cuda_stream);
+
 /* Text of the last CUDA error seen by this thread's calls (static storage). */
 const char* m1_last_error(void);
 

@@ -663,6 +663,10 @@ m1_status make_op_impl(const m1_grid_desc* desc, int lmax, const double* inflow,
 
 }  // namespace
 
+namespace m1 {
+void set_error_text(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace m1
+
 struct m1_grid {
     std::unique_ptr<ImplBase> impl;
 };

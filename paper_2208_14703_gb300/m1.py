@@ -33,7 +33,7 @@ OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
            "m1_set_inflow", "m1_get_state", "m1_implicit_step", "m1_residual_norm",
            "m1_step_history", "m1_jacobi", "m1_op_level", "m1_op_restrict", "m1_op_prolong_correct",
-           "m1_last_error"]
+           "m1_residual_norm_noalloc", "m1_last_error"]
 
 
 class M1Error(RuntimeError):
@@ -90,6 +90,8 @@ _lib.m1_step_history.argtypes = [_vp, _vp, _vp, ctypes.c_int]
 _lib.m1_jacobi.argtypes = [_vp, ctypes.c_double, ctypes.c_int]
 _lib.m1_op_level.argtypes = [ctypes.POINTER(GridDesc), _vp, ctypes.c_double, _vp, _vp, _vp,
                              ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _dp]
+_lib.m1_residual_norm_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_double, _vp, _vp,
+                                          _vp, _vp, _vp, _vp]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
