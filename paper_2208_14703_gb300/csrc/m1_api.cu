@@ -53,6 +53,36 @@ void restrict_profile(const double* fine, int nf, double* coarse, int nc)
     }
 }
 
+// Relaunch a captured cycle graph until the device control block reports done.
+// Batch k is queued before the host waits on the flag copied after batch k-1,
+// so the GPU never idles on the poll; cycles queued past convergence return at
+// once (every kernel checks the flag).  At most max_cycles + 2 graphs' worth.
+m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles,
+                         cudaStream_t stream, Ctl* ctl, int* done_h, cudaEvent_t* poll,
+                         long long* launched_out)
+{
+    long long launched = 0;
+    const long long cap_cycles = (long long)max_cycles + 2 * graph_cycles;
+    int batch = 1;
+    for (long long k = 0;; ++k) {
+        const int slot = (int)(k & 1);
+        for (int b = 0; b < batch && launched < cap_cycles; ++b) {
+            M1_CK(cudaGraphLaunch(graph, stream));
+            launched += graph_cycles;
+        }
+        M1_CK(cudaMemcpyAsync(done_h + slot, &ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        M1_CK(cudaEventRecord(poll[slot], stream));
+        if (k > 0) {
+            M1_CK(cudaEventSynchronize(poll[slot ^ 1]));
+            if (done_h[slot ^ 1]) break;
+        }
+        if (launched >= cap_cycles) break;
+        batch = std::min(batch * 2, 8);
+    }
+    *launched_out = launched;
+    return M1_OK;
+}
+
 struct Params {
     int nu0, nu_l, m, mc;
     bool operator==(const Params& o) const
@@ -105,6 +135,7 @@ struct Impl : ImplBase {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t poll[2] = { nullptr, nullptr };
     int last_cycles = 0;
+    bool delta = false;            // correction-form FP32 hierarchy of the mixed path
 
     ~Impl() override
     {
@@ -131,10 +162,11 @@ struct Impl : ImplBase {
         return M1_OK;
     }
 
-    m1_status init(const m1_grid_desc& dsc, cudaStream_t s)
+    m1_status init(const m1_grid_desc& dsc, cudaStream_t s, bool correction_form = false)
     {
         desc = dsc;
         L = dsc.lmax;
+        delta = correction_form;
         if (s) stream = s;
         else { M1_CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking)); own_stream = true; }
         M1_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -163,6 +195,7 @@ struct Impl : ImplBase {
             M1_TRY(dalloc(&q.u[1], q.n));
             M1_TRY(dalloc(&q.f, q.n));
             M1_TRY(dalloc(&q.r, q.n));
+            if (delta) M1_TRY(dalloc(&q.w, q.n));
             M1_TRY(dalloc(&q.sig, q.n));
             M1_TRY(dalloc(&q.inflow, (size_t)12 * q.prof_len));
             M1_CK(cudaMemsetAsync(q.inflow, 0, sizeof(R) * 12 * q.prof_len, stream));
@@ -322,7 +355,7 @@ struct Impl : ImplBase {
     void sweeps_fine(int& cur, int count, cudaStream_t s)
     {
         for (int k = 0; k < count; ++k) {
-            m1::launch_sweep<R>(d, h[0], false, cur, 1 - cur, ctl, s);
+            m1::launch_sweep<R>(d, h[0], false, cur, 1 - cur, ctl, s, delta);
             cur = 1 - cur;
         }
     }
@@ -332,40 +365,44 @@ struct Impl : ImplBase {
     void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
     {
         for (int k = 0; k < m; ++k) {
-            if (k == 0 && from_v) { m1::launch_sweep<R>(d + l, h[l], true, -1, 0, ctl, s); cur = 0; }
-            else { m1::launch_sweep<R>(d + l, h[l], true, cur, 1 - cur, ctl, s); cur = 1 - cur; }
+            if (k == 0 && from_v) { m1::launch_sweep<R>(d + l, h[l], true, -1, 0, ctl, s, delta); cur = 0; }
+            else { m1::launch_sweep<R>(d + l, h[l], true, cur, 1 - cur, ctl, s, delta); cur = 1 - cur; }
         }
     }
 
-    void record_cycle(const Params& p, int& cur0, cudaStream_t s)
+    // One V-cycle of Algorithm 4 on this hierarchy.  tail: end with the fine
+    // residual norm and the stop test (the mixed-precision driver does its own).
+    void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true)
     {
         std::vector<int> cur(L, 0);
         cur[0] = cur0;
         for (int l = 0; l < L - 1; ++l) {
             if (l == 0) {
                 sweeps_fine(cur[0], p.nu0, s);
-                m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], nullptr, 1, ctl, s);
+                m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], nullptr, 1, ctl, s, delta);
             } else {
-                m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s);
+                m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s, delta);
                 pseudo(l, cur[l], p.m, true, s);
-                m1::launch_apply<R>(d + l, h[l], m1::APPLY_RESID, cur[l], nullptr, 1, ctl, s);
+                m1::launch_apply<R>(d + l, h[l], m1::APPLY_RESID, cur[l], nullptr, 1, ctl, s, delta);
             }
-            m1::launch_restrict<R>(d + l, d + l + 1, h[l + 1], cur[l], ctl, s);
+            m1::launch_restrict<R>(d + l, d + l + 1, h[l + 1], cur[l], ctl, s, delta);
         }
         if (L == 1) {
             sweeps_fine(cur[0], p.nu0, s);
         } else {
             const int l = L - 1;
-            m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s);
+            m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s, delta);
             pseudo(l, cur[l], p.mc, true, s);
         }
         for (int l = L - 2; l >= 0; --l) {
-            m1::launch_prolong<R>(d + l + 1, d + l, h[l], cur[l + 1], cur[l], ctl, s);
+            m1::launch_prolong<R>(d + l + 1, d + l, h[l], cur[l + 1], cur[l], ctl, s, delta);
             if (l == 0) sweeps_fine(cur[0], p.nu0, s);
             else pseudo(l, cur[l], p.m, false, s);
         }
-        m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], part, 0, ctl, s);
-        m1::launch_finalize(ctl, part, h[0].tiles, nullptr, 0, m1::FIN_CYCLE, cur[0], s);
+        if (tail) {
+            m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], part, 0, ctl, s);
+            m1::launch_finalize(ctl, part, h[0].tiles, nullptr, 0, m1::FIN_CYCLE, cur[0], s);
+        }
         cur0 = cur[0];
     }
 
@@ -425,28 +462,8 @@ struct Impl : ImplBase {
         m1::launch_finalize(ctl, part, h[0].tiles, partb, h[0].tiles, m1::FIN_INIT, 0, stream);
         M1_CK(cudaGetLastError());
         dt_rhs = dt; rhs_valid = true;
-        // Relaunch the cycle graph until the device reports done.  Batch k is
-        // queued before the host waits on the flag copied after batch k-1, so the
-        // GPU never idles on the poll; cycles queued past convergence return at
-        // once (every kernel checks the flag).
         long long launched = 0;
-        const long long cap_cycles = (long long)sp.max_cycles + 2 * graph_cycles;
-        int batch = 1;
-        for (long long k = 0;; ++k) {
-            const int slot = (int)(k & 1);
-            for (int b = 0; b < batch && launched < cap_cycles; ++b) {
-                M1_CK(cudaGraphLaunch(graph, stream));
-                launched += graph_cycles;
-            }
-            M1_CK(cudaMemcpyAsync(done_h + slot, &ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream));
-            M1_CK(cudaEventRecord(poll[slot], stream));
-            if (k > 0) {
-                M1_CK(cudaEventSynchronize(poll[slot ^ 1]));
-                if (done_h[slot ^ 1]) break;
-            }
-            if (launched >= cap_cycles) break;
-            batch = std::min(batch * 2, 8);
-        }
+        M1_TRY(run_until_done(graph, graph_cycles, sp.max_cycles, stream, ctl, done_h, poll, &launched));
         M1_CK(cudaMemcpyAsync(ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
         M1_CK(cudaStreamSynchronize(stream));
         if (ctl_h->result_buf == 1) {
@@ -620,6 +637,131 @@ struct Impl : ImplBase {
     }
 };
 
+// Mixed precision (row a11): the FP32 hierarchy `lo` runs the V-cycles of
+// Algorithm 4 on the correction problem A32(u) = A32(v32) + r64; the FP64 fine
+// level `hi` holds v^n, b and the opacities, computes the residual r64 and its
+// norm (stop test, dtau control), and accumulates the corrections in FP64.
+// Both share `hi`'s control block and stream.
+struct MixedImpl : ImplBase {
+    Impl<double> hi;
+    Impl<float> lo;
+    cudaGraphExec_t graph = nullptr;
+    Params gparams{};
+
+    ~MixedImpl() override
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+
+    m1_status init(const m1_grid_desc& dsc, cudaStream_t s)
+    {
+        m1_grid_desc d = dsc;
+        d.lmax = 1;
+        d.precision = M1_FP64;
+        M1_TRY(hi.init(d, s));
+        M1_TRY(lo.init(dsc, hi.stream, true));
+        lo.ctl = hi.ctl;
+        return M1_OK;
+    }
+
+    m1_status set_state(const double* E, const double* Fx, const double* Fy, const double* T,
+                        const double* sa, const double* ss, int dev) override
+    {
+        M1_TRY(hi.set_state(E, Fx, Fy, T, sa, ss, dev));
+        return lo.set_state(E, Fx, Fy, T, sa, ss, dev);
+    }
+
+    m1_status set_inflow(int side, const double* E, const double* Fx, const double* Fy) override
+    {
+        M1_TRY(hi.set_inflow(side, E, Fx, Fy));
+        return lo.set_inflow(side, E, Fx, Fy);
+    }
+
+    m1_status get_state(double* E, double* Fx, double* Fy, double* T, int dev) override
+    {
+        return hi.get_state(E, Fx, Fy, T, dev);
+    }
+
+    m1_status residual_norm(double dt, double* out) override { return hi.residual_norm(dt, out); }
+    m1_status history(double* hs, double* dt, int len) override { return hi.history(hs, dt, len); }
+    m1_status jacobi(double, int) override { return M1_ERR_INVALID_ARG; }
+
+    // FP32 V-cycle, FP64 accumulation of its correction, FP64 defect of the new
+    // iterate with the FP32 right-hand side of the next cycle, stop test.
+    void record_mixed_cycle(const Params& p, cudaStream_t s)
+    {
+        int cur0 = 0;
+        lo.record_cycle(p, cur0, s, false);
+        m1::launch_accumulate(hi.d, hi.h[0], lo.d, cur0, hi.ctl, s);
+        m1::launch_defect(hi.d, hi.h[0], lo.d, hi.part, hi.ctl, s);
+        m1::launch_finalize(hi.ctl, hi.part, hi.h[0].tiles, nullptr, 0, m1::FIN_CYCLE, 0, s);
+    }
+
+    m1_status build_graph(const Params& p)
+    {
+        if (graph && gparams == p) return M1_OK;
+        if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        M1_CK(cudaStreamBeginCapture(lo.cap, cudaStreamCaptureModeThreadLocal));
+        record_mixed_cycle(p, lo.cap);
+        cudaError_t e = cudaStreamEndCapture(lo.cap, &g);
+        if (e != cudaSuccess) { set_err(e, "cudaStreamEndCapture"); return M1_ERR_CUDA; }
+        e = cudaGraphInstantiate(&graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { set_err(e, "cudaGraphInstantiate"); graph = nullptr; return M1_ERR_CUDA; }
+        gparams = p;
+        return M1_OK;
+    }
+
+    m1_status step(double dt, const m1_solve_params& sp, m1_step_stats* st) override
+    {
+        if (!(dt > 0) || sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 ||
+            sp.max_cycles < 1 || !(sp.tol >= 0))
+            return M1_ERR_INVALID_ARG;
+        M1_TRY(hi.set_dt(dt));
+        M1_TRY(lo.set_dt(dt));
+        Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
+        M1_TRY(build_graph(p));
+        Ctl c{};
+        c.tol = sp.tol; c.grow = sp.grow; c.shrink = sp.shrink; c.eps_i = sp.eps_i;
+        c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
+        c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
+        c.hist_len = hi.hist_len; c.hist = hi.hist; c.dtau_hist = hi.dtau_hist;
+        c.res0_floor = 1e-14 * (double)hi.h[0].diag;
+        *hi.ctl_h = c;
+        cudaStream_t s = hi.stream;
+        M1_CK(cudaEventRecord(hi.ev0, s));
+        M1_CK(cudaMemcpyAsync(hi.ctl, hi.ctl_h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        m1::launch_make_rhs<double>(hi.d, hi.h[0], 0, s);
+        m1::launch_norm_state<double>(hi.d, hi.h[0], hi.h[0].f, hi.partb, s);
+        m1::launch_defect(hi.d, hi.h[0], lo.d, hi.part, hi.ctl, s);
+        m1::launch_finalize(hi.ctl, hi.part, hi.h[0].tiles, hi.partb, hi.h[0].tiles, m1::FIN_INIT, 0, s);
+        M1_CK(cudaGetLastError());
+        hi.dt_rhs = dt; hi.rhs_valid = true;
+        long long launched = 0;
+        M1_TRY(run_until_done(graph, 1, sp.max_cycles, s, hi.ctl, hi.done_h, hi.poll, &launched));
+        M1_CK(cudaMemcpyAsync(hi.ctl_h, hi.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        M1_CK(cudaEventRecord(hi.ev1, s));
+        M1_CK(cudaEventSynchronize(hi.ev1));
+        hi.last_cycles = hi.ctl_h->kappa;
+        if (st) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, hi.ev0, hi.ev1);
+            st->cycles = hi.ctl_h->kappa;
+            st->res0 = hi.ctl_h->res0;
+            st->res = hi.ctl_h->kappa > 0 ? hi.ctl_h->res : hi.ctl_h->res0;
+            st->dtau_final = hi.ctl_h->dtau;
+            st->sweeps = (long long)hi.ctl_h->kappa * (lo.L == 1 ? p.nu0 : 2 * p.nu0);
+            st->ms = ms;
+            st->status = hi.ctl_h->status;
+            st->newton_fail = hi.ctl_h->newton_fail;
+            st->damped = hi.ctl_h->damped;
+            st->launches = 4 + launched * (lo.kernels_per_cycle(p) + 1);
+        }
+        return hi.ctl_h->status == m1::CTL_OK ? M1_OK : M1_ERR_NOT_CONVERGED;
+    }
+};
+
 m1_status validate(const m1_grid_desc* d)
 {
     if (!d) return M1_ERR_INVALID_ARG;
@@ -690,12 +832,18 @@ m1_status m1_create_grid(const m1_grid_desc* desc, void* cuda_stream, m1_grid_t*
     if (!out) return M1_ERR_INVALID_ARG;
     *out = nullptr;
     M1_TRY(validate(desc));
-    if (desc->precision != M1_FP64) return M1_ERR_INVALID_ARG;   // mixed: separate path
-    std::unique_ptr<Impl<double>> impl(new Impl<double>());
-    m1_status s = impl->init(*desc, static_cast<cudaStream_t>(cuda_stream));
-    if (s != M1_OK) return s;
     m1_grid* g = new m1_grid;
-    g->impl = std::move(impl);
+    m1_status s;
+    if (desc->precision == M1_MIXED) {
+        std::unique_ptr<MixedImpl> impl(new MixedImpl());
+        s = impl->init(*desc, static_cast<cudaStream_t>(cuda_stream));
+        g->impl = std::move(impl);
+    } else {
+        std::unique_ptr<Impl<double>> impl(new Impl<double>());
+        s = impl->init(*desc, static_cast<cudaStream_t>(cuda_stream));
+        g->impl = std::move(impl);
+    }
+    if (s != M1_OK) { delete g; return s; }
     *out = g;
     return M1_OK;
 }

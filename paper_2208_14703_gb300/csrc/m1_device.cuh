@@ -48,6 +48,7 @@ struct Level {
     Cell4<R>* u[2];               // ping-pong iterate u_l
     Cell4<R>* f;                  // right-hand side (b at level 0, FAS rhs above)
     Cell4<R>* r;                  // residual (restricted from below / computed here)
+    Cell4<R>* w;                  // base state of the correction form (mixed path), else null
     Sig2<R>* sig;                 // opacities
     R* inflow;                    // [wall][E, Fx, Fy][prof_len] prescribed ghosts
 };
@@ -205,6 +206,95 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
     R T2 = T * T;
     o.T = T;
     o.E = (bE + k * a_r * T2 * T2) * iAk;
+    return o;
+}
+
+
+// ---------------------------------------------------------------------------
+// Correction form (mixed precision).  The FP32 cycle carries a correction e
+// around a base state w and evaluates differences A(w + e) - A(w) directly,
+// with every term of size O(e), so that FP32 rounding is relative to |e| and
+// not to |w| (a subtraction u32 - w32 would lose the correction to the
+// rounding of the full state).
+
+// P(w + e) - P(w) for the closure of Eq. (5) written as
+// P = E a I + (q / c^2) E phi phi^T, phi = F / E, a = (s - 1)/3, q = 3/(2 + s),
+// s = sqrt(4 - 3 f^2), f^2 = |phi|^2 / c^2, using
+//   d phi = (e_F - phi0 e_E) / E1,  d(f^2) = d phi . (phi0 + phi1) / c^2,
+//   d s = -3 d(f^2) / (s0 + s1),  d q = -3 d s / ((2 + s0)(2 + s1)).
+template <typename R>
+__device__ __forceinline__ void closure_delta(R wE, R wFx, R wFy, R eE, R eFx, R eFy, R inv_c2,
+                                              R& dPxx, R& dPxy, R& dPyy)
+{
+    const R E1 = wE + eE;
+    const R iE0 = R(1) / wE, iE1 = R(1) / E1;
+    const R px0 = wFx * iE0, py0 = wFy * iE0;
+    const R dpx = (eFx - px0 * eE) * iE1, dpy = (eFy - py0 * eE) * iE1;
+    const R px1 = px0 + dpx, py1 = py0 + dpy;
+    const R f20 = (px0 * px0 + py0 * py0) * inv_c2;
+    const R df2 = (dpx * (px0 + px1) + dpy * (py0 + py1)) * inv_c2;
+    const R f21 = f20 + df2;
+    const R c0 = f20 < R(1) ? f20 : R(1), c1 = f21 < R(1) ? f21 : R(1);
+    const R dc = (f20 <= R(1) && f21 <= R(1)) ? df2 : c1 - c0;
+    const R s0 = sqrt(R(4) - R(3) * c0), s1 = sqrt(R(4) - R(3) * c1);
+    const R ds = R(-3) * dc / (s0 + s1);
+    const R a1 = (s1 - R(1)) * (R(1) / R(3)), da = ds * (R(1) / R(3));
+    const R q0 = R(3) / (R(2) + s0);
+    const R dq = R(-3) * ds / ((R(2) + s0) * (R(2) + s1));
+    const R iso = eE * a1 + wE * da;
+    dPxx = iso + inv_c2 * (dq * E1 * px1 * px1 + q0 * (eE * px1 * px1 + wE * dpx * (px0 + px1)));
+    dPyy = iso + inv_c2 * (dq * E1 * py1 * py1 + q0 * (eE * py1 * py1 + wE * dpy * (py0 + py1)));
+    dPxy = inv_c2 * (dq * E1 * px1 * py1 + q0 * (eE * px1 * py1 + wE * (dpx * py1 + px0 * dpy)));
+}
+
+// (T + x)^4 - T^4 = x (4 T^3 + 6 T^2 x + 4 T x^2 + x^3), without cancellation.
+template <typename R>
+__device__ __forceinline__ R quartic_delta(R T, R x)
+{
+    return x * (R(4) * T * T * T + x * (R(6) * T * T + x * (R(4) * T + x)));
+}
+
+// The local solve of `local_solve` for the correction (e_E, e_F, x = e_T) of a
+// base cell with temperature T:
+//   (w0 + w1 diag) e_E + w1 ka (e_E - a_r dT4)  = bE,  dT4 = (T + x)^4 - T^4
+//   (w0 + w1 (diag + kt)) e_F                   = bF
+//   (w0 + w1 C_v) x - w1 ka (e_E - a_r dT4)     = bT
+// Eliminating e_E leaves h(x) = C x + K dT4(x) - R = 0, increasing and convex
+// for T + x > 0; Newton from x = 0 lands right of the root after one step and
+// then decreases monotonically.
+template <typename R>
+__device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, R kt, R c_v,
+                                                      R a_r, R T, R bE, R bFx, R bFy, R bT,
+                                                      bool& ok)
+{
+    Cell4<R> o;
+    const R A = w0 + w1 * diag;
+    const R k = w1 * ka;
+    const R iF = R(1) / (w0 + w1 * (diag + kt));
+    o.Fx = bFx * iF;
+    o.Fy = bFy * iF;
+    const R C = w0 + w1 * c_v;
+    ok = true;
+    if (k == R(0)) {
+        o.T = bT / C;
+        o.E = bE / A;
+        return o;
+    }
+    const R iAk = R(1) / (A + k);
+    const R K = k * A * a_r * iAk;
+    const R Rr = bT + k * bE * iAk;
+    R x = R(0);
+    ok = false;
+    for (int it = 0; it < 40; ++it) {
+        const R Tx = T + x;
+        const R h = C * x + K * quartic_delta(T, x) - Rr;
+        const R dh = C + R(4) * K * Tx * Tx * Tx;
+        const R dx = h / dh;
+        x -= dx;
+        if (fabs(dx) <= R(2e-7) * fabs(x) || dx == R(0)) { ok = true; break; }
+    }
+    o.T = x;
+    o.E = (bE + k * a_r * quartic_delta(T, x)) * iAk;
     return o;
 }
 

@@ -13,6 +13,8 @@
 //
 // The stencil kernels stage a tile plus a one-cell halo in shared memory and
 // evaluate each cell's closure once per pass; neighbours read it from there.
+#include <type_traits>
+
 #include "m1_kernels.cuh"
 
 namespace m1 {
@@ -32,8 +34,11 @@ __device__ __forceinline__ void load_level(Level<R>& dst, const Level<R>* src)
 }
 
 // Stage the tile [x0, x0+tx) x [y0, y0+ty) of state `s` with its one-cell halo
-// (no corners) and each staged cell's closure.
-template <typename R>
+// (no corners) and each staged cell's closure.  DELTA (correction form): `s`
+// is the correction e, the base state is L.w, and the tile holds e and the
+// closure difference P(w + e) - P(w); the neighbour operators are linear in
+// (E, F, P), so the same neighbour sum then gives N(w + e) - N(w).
+template <typename R, bool DELTA = false>
 __device__ __forceinline__ void load_tile(const Level<R>& L, const Cell4<R>* __restrict__ s,
                                           int x0, int y0, Tile<R>& t)
 {
@@ -44,9 +49,16 @@ __device__ __forceinline__ void load_tile(const Level<R>& L, const Cell4<R>* __r
         int gi = x0 + hi - 1, gj = y0 + hj - oy;
         bool edge_x = hi == 0 || hi == hw - 1, edge_y = oy && (hj == 0 || hj == hh - 1);
         if ((edge_x && edge_y) || gi > L.nx || gj > L.ny) continue;
-        Cell4<R> c = fetch(L, s, gi, gj, KIND_STATE);
         R pxx, pxy, pyy;
-        closure(c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
+        Cell4<R> c;
+        if (!DELTA) {
+            c = fetch(L, s, gi, gj, KIND_STATE);
+            closure(c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
+        } else {
+            const Cell4<R> w = fetch(L, L.w, gi, gj, KIND_STATE);
+            c = fetch(L, s, gi, gj, KIND_DIFF);
+            closure_delta(w.E, w.Fx, w.Fy, c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
+        }
         t.E[k] = c.E; t.Fx[k] = c.Fx; t.Fy[k] = c.Fy;
         t.Pxx[k] = pxx; t.Pxy[k] = pxy; t.Pyy[k] = pyy;
     }
@@ -79,7 +91,7 @@ __device__ __forceinline__ void tile_origin(const Level<R>& L, int tile, int& x0
 }
 
 // ---------------------------------------------------------------------------
-template <typename R, bool PSEUDO>
+template <typename R, bool PSEUDO, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__ Lp, int in_buf,
                                                     int out_buf, Ctl* __restrict__ ctl)
 {
@@ -91,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__
     int x0, y0;
     tile_origin(L, blockIdx.x, x0, y0);
     const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-    load_tile(L, src, x0, y0, t);
+    load_tile<R, DELTA>(L, src, x0, y0, t);
     __syncthreads();
     const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
     const int i = x0 + lx, j = y0 + ly;
@@ -106,18 +118,32 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__
     bool ok;
     Cell4<R> out;
     if (!PSEUDO) {
-        out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE, b.Fx + NFx,
-                             b.Fy + NFy, b.T, ok);
+        if (!DELTA)
+            out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE, b.Fx + NFx,
+                                 b.Fy + NFy, b.T, ok);
+        else
+            out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, L.w[k].T,
+                                       b.E + NE, b.Fx + NFx, b.Fy + NFy, b.T, ok);
     } else {
         // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*) (tau* = the
         // largest admissible step along f); implicit half: one Jacobi sweep of
-        // u + dtau A(u) = u~ from the old iterate
+        // u + dtau A(u) = u~ from the old iterate.  DELTA: u = w + e, and the
+        // sweep updates the correction e (u~ - w = e + tau f).
         const R dtau = (R)ctl->dtau;
         const Cell4<R> u = src[k];
-        R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(u, b, L.c));
-        out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
-                             u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
-                             u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+        if (!DELTA) {
+            R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(u, b, L.c));
+            out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
+                                 u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
+                                 u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+        } else {
+            const Cell4<R> w = L.w[k];
+            const Cell4<R> full = { w.E + u.E, w.Fx + u.Fx, w.Fy + u.Fy, w.T + u.T };
+            R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(full, b, L.c));
+            out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, w.T,
+                                       u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
+                                       u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+        }
     }
     if (!ok) atomicAdd(&ctl->newton_fail, 1u);
     L.u[out_buf][k] = out;
@@ -137,7 +163,7 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s;
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__ Lp, int state_buf,
                                                     double* __restrict__ partials, int write_r,
                                                     Ctl* __restrict__ ctl)
@@ -151,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
     int x0, y0;
     tile_origin(L, blockIdx.x, x0, y0);
     const Cell4<R>* __restrict__ src = state_buf < 0 ? L.v : L.u[state_buf];
-    load_tile(L, src, x0, y0, t);
+    load_tile<R, DELTA>(L, src, x0, y0, t);
     __syncthreads();
     const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
     const int i = x0 + lx, j = y0 + ly;
@@ -164,8 +190,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
         const Cell4<R> u = src[k];
         const Sig2<R> sg = L.sig[k];
         const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-        const R T2 = u.T * u.T;
-        const R src_e = ka * (u.E - L.a_r * T2 * T2);
+        R src_e;
+        if (!DELTA) {
+            const R T2 = u.T * u.T;
+            src_e = ka * (u.E - L.a_r * T2 * T2);
+        } else {
+            // A(w + e) - A(w): the source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
+            src_e = ka * (u.E - L.a_r * quartic_delta(L.w[k].T, u.T));
+        }
         Cell4<R> a;
         a.E = L.diag * u.E + src_e - NE;
         a.Fx = (L.diag + kt) * u.Fx - NFx;
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restr
 // ---------------------------------------------------------------------------
 // Full weighting, coarse cell (ic, jc) <- fine cells 2ic-1..2ic+1 (x) and
 // 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis.
-template <typename R>
+template <typename R, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restrict__ Lfp,
                                                        const Level<R>* __restrict__ Lcp,
                                                        int fine_buf, Ctl* __restrict__ ctl)
@@ -234,21 +266,28 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
     const int ic = kc % Lc.nx, jc = kc / Lc.nx;
     const R w[3] = { R(0.25), R(0.5), R(0.25) };
     const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
-    Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 };
+    Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
     const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
     for (int b = b0; b <= b1; ++b) {
         const R wy = Lf.dim == 2 ? w[b + 1] : R(1);
         const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
         for (int a = -1; a <= 1; ++a) {
             const R wt = wy * w[a + 1];
-            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, KIND_STATE);
+            // correction form: the correction has zero inflow ghosts, the base
+            // carries the prescribed state
+            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
             const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
             av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
             ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+            if (DELTA) {
+                const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
+                aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+            }
         }
     }
     Lc.v[kc] = av;
     Lc.r[kc] = ar;
+    if (DELTA) Lc.w[kc] = aw;
 }
 
 template <typename R>
@@ -280,7 +319,7 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ Lfp, const Level<R>*
 // u_l += P(u_{l+1} - v_{l+1}) per fine cell (fine 2i <- coarse i, fine 2i+1 <-
 // half of coarse i and i+1; tensor product in 2D); a target outside the
 // admissible set is replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).
-template <typename R>
+template <typename R, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ Lcp,
                                                       const Level<R>* __restrict__ Lfp,
                                                       int coarse_buf, int fine_buf,
@@ -307,16 +346,20 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
             pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
         }
     Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
-    const Cell4<R> u = uf[k];
+    const Cell4<R> e = uf[k];
+    Cell4<R> u = e;
+    if (DELTA) {   // correction form: the admissible set constrains w + e
+        const Cell4<R> w = Lf.w[k];
+        u.E += w.E; u.Fx += w.Fx; u.Fy += w.Fy; u.T += w.T;
+    }
     Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
+    R th = R(1);
     if (!admissible(tg, Lf.c)) {
-        R ts = max_admissible_step(u, pe, Lf.c);
-        R th = (R)ctl->theta_c * fmin(R(1), ts);
-        tg.E = u.E + th * pe.E; tg.Fx = u.Fx + th * pe.Fx;
-        tg.Fy = u.Fy + th * pe.Fy; tg.T = u.T + th * pe.T;
+        th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
         atomicAdd(&ctl->damped, 1u);
     }
-    uf[k] = tg;
+    const Cell4<R> out = { e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy, e.T + th * pe.T };
+    uf[k] = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -448,16 +491,30 @@ static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 template <typename R>
 void launch_sweep(const Level<R>* dL, const Level<R>& hL, bool pseudo, int in_buf, int out_buf,
-                  Ctl* ctl, cudaStream_t s)
+                  Ctl* ctl, cudaStream_t s, bool delta)
 {
+    if (delta && std::is_same<R, float>::value) {
+        if (pseudo) k_sweep<R, true, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
+        else k_sweep<R, false, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
+        return;
+    }
     if (pseudo) k_sweep<R, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
     else k_sweep<R, false><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
 }
 
 template <typename R>
 void launch_apply(const Level<R>* dL, const Level<R>& hL, int mode, int state_buf,
-                  double* partials, int write_r, Ctl* ctl, cudaStream_t s)
+                  double* partials, int write_r, Ctl* ctl, cudaStream_t s, bool delta)
 {
+    if (delta && std::is_same<R, float>::value) {
+        if (mode == APPLY_RESID)
+            k_apply<R, APPLY_RESID, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        else if (mode == APPLY_FAS)
+            k_apply<R, APPLY_FAS, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        else
+            k_apply<R, APPLY_A, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        return;
+    }
     if (mode == APPLY_RESID)
         k_apply<R, APPLY_RESID><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
     else if (mode == APPLY_FAS)
@@ -475,9 +532,12 @@ void launch_norm_state(const Level<R>* dL, const Level<R>& hL, const Cell4<R>* s
 
 template <typename R>
 void launch_restrict(const Level<R>* dLf, const Level<R>* dLc, const Level<R>& hLc, int fine_buf,
-                     Ctl* ctl, cudaStream_t s)
+                     Ctl* ctl, cudaStream_t s, bool delta)
 {
-    k_restrict<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
+    if (delta && std::is_same<R, float>::value)
+        k_restrict<R, true><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
+    else
+        k_restrict<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
 }
 
 template <typename R>
@@ -489,9 +549,12 @@ void launch_restrict_sig(const Level<R>* dLf, const Level<R>* dLc, const Level<R
 
 template <typename R>
 void launch_prolong(const Level<R>* dLc, const Level<R>* dLf, const Level<R>& hLf, int coarse_buf,
-                    int fine_buf, Ctl* ctl, cudaStream_t s)
+                    int fine_buf, Ctl* ctl, cudaStream_t s, bool delta)
 {
-    k_prolong<R><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
+    if (delta && std::is_same<R, float>::value)
+        k_prolong<R, true><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
+    else
+        k_prolong<R><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
 }
 
 template <typename R>
@@ -535,17 +598,17 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 
 #define M1_INSTANTIATE(R)                                                                          \
     template void launch_sweep<R>(const Level<R>*, const Level<R>&, bool, int, int, Ctl*,         \
-                                  cudaStream_t);                                                   \
+                                  cudaStream_t, bool);                                             \
     template void launch_apply<R>(const Level<R>*, const Level<R>&, int, int, double*, int, Ctl*, \
-                                  cudaStream_t);                                                   \
+                                  cudaStream_t, bool);                                             \
     template void launch_norm_state<R>(const Level<R>*, const Level<R>&, const Cell4<R>*,         \
                                        double*, cudaStream_t);                                     \
     template void launch_restrict<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, Ctl*,\
-                                     cudaStream_t);                                                \
+                                     cudaStream_t, bool);                                          \
     template void launch_restrict_sig<R>(const Level<R>*, const Level<R>*, const Level<R>&,       \
                                          cudaStream_t);                                            \
     template void launch_prolong<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, int,  \
-                                    Ctl*, cudaStream_t);                                           \
+                                    Ctl*, cudaStream_t, bool);                                     \
     template void launch_make_rhs<R>(const Level<R>*, const Level<R>&, int, cudaStream_t);        \
     template void launch_pack_state<R>(const double*, const double*, const double*, const double*,\
                                        double, Cell4<R>*, int, cudaStream_t);                      \
@@ -557,5 +620,98 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 
 M1_INSTANTIATE(double)
 M1_INSTANTIATE(float)
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP32 V-cycles in correction form inside FP64 defect
+// correction.
+//
+// k_defect: per fine cell, r64 = b64 - A64(v64) in FP64 (norm partials for the
+// stop test), and the FP32 fine problem of the next cycle in correction form:
+// base state w = fl32(v64), initial correction e = 0, source g = fl32(r64)
+// (the FP32 cycle solves A32(w + e) - A32(w) = r64 for e).
+__global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __restrict__ L64p,
+                                                     const Level<float>* __restrict__ L32p,
+                                                     double* __restrict__ partials,
+                                                     Ctl* __restrict__ ctl)
+{
+    if (ctl->done) return;
+    __shared__ Level<double> L;
+    __shared__ Level<float> M;
+    __shared__ Tile<double> t;
+    __shared__ double red[kThreads / 32];
+    load_level(L, L64p);
+    load_level(M, L32p);
+    __syncthreads();
+    int x0, y0;
+    tile_origin(L, blockIdx.x, x0, y0);
+    load_tile(L, L.u[0], x0, y0, t);
+    __syncthreads();
+    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+    const int i = x0 + lx, j = y0 + ly;
+    double nrm = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const size_t k = (size_t)j * L.nx + i;
+        const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+        double NE, NFx, NFy;
+        neighbour_sum(L, t, ck, NE, NFx, NFy);
+        const Cell4<double> u = L.u[0][k];
+        const Sig2<double> sg = L.sig[k];
+        const double ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+        const double T2 = u.T * u.T, se = ka * (u.E - L.a_r * T2 * T2);
+        const Cell4<double> b = L.f[k];
+        const double rE = b.E - (L.diag * u.E + se - NE);
+        const double rFx = b.Fx - ((L.diag + kt) * u.Fx - NFx);
+        const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
+        const double rT = b.T - (L.c_v * u.T - se);
+        nrm = rE * rE + (rFx * rFx + rFy * rFy) / (L.c * L.c) + rT * rT;
+        const Cell4<float> w = { (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
+        const Cell4<float> g = { (float)rE, (float)rFx, (float)rFy, (float)rT };
+        const Cell4<float> z = { 0.f, 0.f, 0.f, 0.f };
+        M.w[k] = w;
+        M.f[k] = g;
+        M.u[0][k] = z;
+    }
+    double sum = block_sum<double>(nrm, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum * L.vol;
+}
+
+// k_accumulate: v64 += e in FP64 (e = the FP32 cycle's correction in buffer
+// `buf`); a cell whose update leaves the admissible set takes
+// v64 + theta_c min(1, tau*) e instead (the damping rule of Eq. (34)).
+__global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __restrict__ L64p,
+                                                         const Level<float>* __restrict__ L32p,
+                                                         int buf, Ctl* __restrict__ ctl)
+{
+    if (ctl->done) return;
+    __shared__ Level<double> L;
+    __shared__ Level<float> M;
+    load_level(L, L64p);
+    load_level(M, L32p);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.n) return;
+    const Cell4<float> a = M.u[buf][k];
+    const Cell4<double> e = { (double)a.E, (double)a.Fx, (double)a.Fy, (double)a.T };
+    const Cell4<double> u = L.u[0][k];
+    Cell4<double> t = { u.E + e.E, u.Fx + e.Fx, u.Fy + e.Fy, u.T + e.T };
+    if (!admissible(t, L.c)) {
+        const double th = ctl->theta_c * fmin(1.0, max_admissible_step(u, e, L.c));
+        t.E = u.E + th * e.E; t.Fx = u.Fx + th * e.Fx; t.Fy = u.Fy + th * e.Fy; t.T = u.T + th * e.T;
+        atomicAdd(&ctl->damped, 1u);
+    }
+    L.u[0][k] = t;
+}
+
+void launch_defect(const Level<double>* L64, const Level<double>& h64, const Level<float>* L32,
+                   double* partials, Ctl* ctl, cudaStream_t s)
+{
+    k_defect<<<h64.tiles, kThreads, 0, s>>>(L64, L32, partials, ctl);
+}
+
+void launch_accumulate(const Level<double>* L64, const Level<double>& h64, const Level<float>* L32,
+                       int buf, Ctl* ctl, cudaStream_t s)
+{
+    k_accumulate<<<cdiv(h64.n, kThreads), kThreads, 0, s>>>(L64, L32, buf, ctl);
+}
 
 }  // namespace m1
