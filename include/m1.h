@@ -148,6 +148,30 @@ m1_status m1_residual_norm(m1_grid_t g, double dt, double* out);
  * len entries); dtau[k] = implicit pseudo-time step used in cycle k+1. */
 m1_status m1_step_history(m1_grid_t g, double* hist, double* dtau, int len);
 
+/* ---- batches: many independent instances stepped together ---------------------
+ * A batch holds `count` instances (grids) that share lmax and precision; sizes,
+ * dimension (1D and 2D may mix), walls, constants and time steps are per
+ * instance.  One persistent launch per level and kernel serves all instances
+ * (their tiles are items of a device work list), one CUDA graph holds the
+ * V-cycle, and each instance keeps its own dtau_im, residual norms and stop flag
+ * (Algorithm 4 per instance): an instance's result is the same alone and in a
+ * batch.  Index arguments are 0 .. count-1. */
+typedef struct m1_batch* m1_batch_t;
+m1_status m1_create_batch(const m1_grid_desc* descs, int count, void* cuda_stream, m1_batch_t* out);
+m1_status m1_destroy_batch(m1_batch_t b);
+m1_status m1_batch_set_state(m1_batch_t b, int index, const double* E, const double* Fx,
+                             const double* Fy, const double* T, const double* sig_a,
+                             const double* sig_s, int on_device);
+m1_status m1_batch_set_inflow(m1_batch_t b, int index, int side, const double* E, const double* Fx,
+                              const double* Fy);
+m1_status m1_batch_get_state(m1_batch_t b, int index, double* E, double* Fx, double* Fy, double* T,
+                             int on_device);
+/* One implicit step of every instance; dt[count]; stats[count] (may be NULL).
+ * Returns when every instance has converged (or reached max_cycles:
+ * NOT_CONVERGED if any did). */
+m1_status m1_batch_implicit_step(m1_batch_t b, const double* dt, const m1_solve_params* params,
+                                 m1_step_stats* stats);
+
 /* ---- single-kernel entry points (one kernel on caller data, for checks) ----
  * Stateless: each call allocates its own device buffers for `desc` (lmax is
  * ignored; precision selects FP64 or FP32 arithmetic), runs one kernel on the

@@ -1,6 +1,8 @@
-// Host side of libm1: the level hierarchy, the V-cycle of Algorithm 4 (Appendix
-// A) recorded once into a CUDA graph and relaunched until the device-side stop
-// flag is set, and the C ABI declared in include/m1.h.
+// Host side of libm1: slot-based engines (one engine = instances sharing a level
+// count and a precision; a single grid is an engine with one slot), the V-cycle
+// of Algorithm 4 (Appendix A) recorded once into a CUDA graph whose persistent
+// kernels walk device-resident work lists and relaunched until every instance's
+// device-side stop flag is set, and the C ABI declared in include/m1.h.
 #include <m1.h>
 
 #include <algorithm>
@@ -8,57 +10,28 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
-#include <string>
 #include <vector>
 
-#include "m1_kernels.cuh"
+#include "m1_engine.h"
 
-namespace {
+namespace m1 {
 
 thread_local char g_err[512] = "";
+
+void set_error_text(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
 
 void set_err(cudaError_t e, const char* what)
 {
     std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define M1_CK(call)                                                                                \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess) {                                                                   \
-            set_err(e_, #call);                                                                    \
-            return e_ == cudaErrorMemoryAllocation ? M1_ERR_OOM : M1_ERR_CUDA;                     \
-        }                                                                                          \
-    } while (0)
-
-#define M1_TRY(expr)                                                                               \
-    do {                                                                                           \
-        m1_status s_ = (expr);                                                                     \
-        if (s_ != M1_OK) return s_;                                                                \
-    } while (0)
-
-using m1::Cell4;
-using m1::Ctl;
-using m1::Level;
-using m1::Sig2;
-
-// Full-weighting restriction of an inflow profile along its wall (1/4, 1/2,
-// 1/4; ends copied), giving the coarse level's prescribed ghost states.
-void restrict_profile(const double* fine, int nf, double* coarse, int nc)
-{
-    for (int i = 0; i < nc; ++i) {
-        if (nc == nf) { coarse[i] = fine[i]; continue; }
-        int a = std::max(2 * i - 1, 0), b = 2 * i, c = std::min(2 * i + 1, nf - 1);
-        coarse[i] = 0.25 * fine[a] + 0.5 * fine[b] + 0.25 * fine[c];
-    }
-}
-
-// Relaunch a captured cycle graph until the device control block reports done.
-// Batch k is queued before the host waits on the flag copied after batch k-1,
-// so the GPU never idles on the poll; cycles queued past convergence return at
-// once (every kernel checks the flag).  At most max_cycles + 2 graphs' worth.
+// Relaunch a captured cycle graph until the batch control block reports that
+// every active instance is done.  Batch k is queued before the host waits on the
+// flag copied after batch k-1, so the GPU never idles on the poll; cycles queued
+// past convergence return at once (every kernel checks its instance's flag).
+// At most max_cycles + 2 graphs' worth are launched.
 m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles,
-                         cudaStream_t stream, Ctl* ctl, int* done_h, cudaEvent_t* poll,
+                         cudaStream_t stream, BatchCtl* bctl, int* done_h, cudaEvent_t* poll,
                          long long* launched_out)
 {
     long long launched = 0;
@@ -70,7 +43,8 @@ m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles
             M1_CK(cudaGraphLaunch(graph, stream));
             launched += graph_cycles;
         }
-        M1_CK(cudaMemcpyAsync(done_h + slot, &ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        M1_CK(cudaMemcpyAsync(done_h + slot, &bctl->all_done, sizeof(int), cudaMemcpyDeviceToHost,
+                              stream));
         M1_CK(cudaEventRecord(poll[slot], stream));
         if (k > 0) {
             M1_CK(cudaEventSynchronize(poll[slot ^ 1]));
@@ -83,686 +57,18 @@ m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles
     return M1_OK;
 }
 
-struct Params {
-    int nu0, nu_l, m, mc;
-    bool operator==(const Params& o) const
-    {
-        return nu0 == o.nu0 && nu_l == o.nu_l && m == o.m && mc == o.mc;
+// Full-weighting restriction of an inflow profile along its wall (1/4, 1/2,
+// 1/4; ends copied), giving the coarse level's prescribed ghost states.
+void restrict_profile(const double* fine, int nf, double* coarse, int nc)
+{
+    for (int i = 0; i < nc; ++i) {
+        if (nc == nf) { coarse[i] = fine[i]; continue; }
+        int a = std::max(2 * i - 1, 0), b = 2 * i, c = std::min(2 * i + 1, nf - 1);
+        coarse[i] = 0.25 * fine[a] + 0.5 * fine[b] + 0.25 * fine[c];
     }
-};
+}
 
-struct ImplBase {
-    virtual ~ImplBase() = default;
-    virtual m1_status set_state(const double* E, const double* Fx, const double* Fy,
-                                const double* T, const double* sa, const double* ss, int dev) = 0;
-    virtual m1_status set_inflow(int side, const double* E, const double* Fx, const double* Fy) = 0;
-    virtual m1_status get_state(double* E, double* Fx, double* Fy, double* T, int dev) = 0;
-    virtual m1_status step(double dt, const m1_solve_params& p, m1_step_stats* st) = 0;
-    virtual m1_status residual_norm(double dt, double* out) = 0;
-    virtual m1_status history(double* hist, double* dtau, int len) = 0;
-    virtual m1_status jacobi(double dt, int sweeps) = 0;
-};
-
-template <typename R>
-struct Impl : ImplBase {
-    m1_grid_desc desc{};
-    int L = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t cap = nullptr;
-    std::vector<Level<R>> h;       // host copies of the level descriptors
-    Level<R>* d = nullptr;         // device array of descriptors
-    std::vector<void*> allocs;
-    std::vector<std::vector<double>> prof;   // inflow profiles per level [4*3*prof_len]
-    Ctl* ctl = nullptr;            // device control block
-    Ctl* ctl_h = nullptr;          // pinned host mirror
-    int* done_h = nullptr;         // pinned flags for polling
-    double* hist = nullptr;
-    double* dtau_hist = nullptr;
-    int hist_len = 0;
-    double* part = nullptr;        // per-tile norm partials (fine level)
-    double* partb = nullptr;
-    double* stage = nullptr;       // planar FP64 staging, 6 * n0
-    Sig2<R>* sig_stage = nullptr;
-    unsigned int* bad = nullptr;
-    unsigned int* bad_h = nullptr;
-    double dt_levels = NAN;        // dt the level constants were computed for
-    double dt_rhs = NAN;           // dt of the last step (level-0 f holds its b)
-    bool rhs_valid = false;
-    cudaGraphExec_t graph = nullptr;
-    Params gparams{};
-    int graph_cycles = 1;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t poll[2] = { nullptr, nullptr };
-    int last_cycles = 0;
-    bool delta = false;            // correction-form FP32 hierarchy of the mixed path
-
-    ~Impl() override
-    {
-        if (graph) cudaGraphExecDestroy(graph);
-        if (stream) cudaStreamSynchronize(stream);
-        for (void* p : allocs) cudaFree(p);
-        if (ctl_h) cudaFreeHost(ctl_h);
-        if (done_h) cudaFreeHost(done_h);
-        if (bad_h) cudaFreeHost(bad_h);
-        if (ev0) cudaEventDestroy(ev0);
-        if (ev1) cudaEventDestroy(ev1);
-        for (auto& e : poll) if (e) cudaEventDestroy(e);
-        if (cap) cudaStreamDestroy(cap);
-        if (own_stream && stream) cudaStreamDestroy(stream);
-    }
-
-    template <typename T>
-    m1_status dalloc(T** p, size_t count)
-    {
-        void* q = nullptr;
-        M1_CK(cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
-        allocs.push_back(q);
-        *p = static_cast<T*>(q);
-        return M1_OK;
-    }
-
-    m1_status init(const m1_grid_desc& dsc, cudaStream_t s, bool correction_form = false)
-    {
-        desc = dsc;
-        L = dsc.lmax;
-        delta = correction_form;
-        if (s) stream = s;
-        else { M1_CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking)); own_stream = true; }
-        M1_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        M1_CK(cudaEventCreate(&ev0));
-        M1_CK(cudaEventCreate(&ev1));
-        M1_CK(cudaEventCreateWithFlags(&poll[0], cudaEventDisableTiming));
-        M1_CK(cudaEventCreateWithFlags(&poll[1], cudaEventDisableTiming));
-        h.resize(L);
-        prof.resize(L);
-        int nx = dsc.nx, ny = dsc.dim == 2 ? dsc.ny : 1;
-        double hx = dsc.lx / dsc.nx, hy = dsc.dim == 2 ? dsc.ly / dsc.ny : 1.0;
-        for (int l = 0; l < L; ++l) {
-            Level<R>& q = h[l];
-            std::memset(&q, 0, sizeof(q));
-            q.dim = dsc.dim; q.nx = nx; q.ny = ny; q.n = nx * ny;
-            for (int w = 0; w < 4; ++w) q.bc[w] = dsc.bc[w];
-            q.tx = dsc.dim == 2 ? m1::kTx2 : m1::kTx1;
-            q.ty = dsc.dim == 2 ? m1::kTy2 : 1;
-            q.tiles_x = (nx + q.tx - 1) / q.tx;
-            q.tiles = q.tiles_x * ((ny + q.ty - 1) / q.ty);
-            q.prof_len = std::max(nx, ny);
-            q.c = (R)dsc.c; q.a_r = (R)dsc.a_r; q.c_v = (R)dsc.c_v;
-            q.vol = dsc.dim == 2 ? hx * hy : hx;
-            M1_TRY(dalloc(&q.v, q.n));
-            M1_TRY(dalloc(&q.u[0], q.n));
-            M1_TRY(dalloc(&q.u[1], q.n));
-            M1_TRY(dalloc(&q.f, q.n));
-            M1_TRY(dalloc(&q.r, q.n));
-            if (delta) M1_TRY(dalloc(&q.w, q.n));
-            M1_TRY(dalloc(&q.sig, q.n));
-            M1_TRY(dalloc(&q.inflow, (size_t)12 * q.prof_len));
-            M1_CK(cudaMemsetAsync(q.inflow, 0, sizeof(R) * 12 * q.prof_len, stream));
-            prof[l].assign((size_t)12 * q.prof_len, 0.0);
-            nx /= 2; if (dsc.dim == 2) ny /= 2;
-            hx *= 2; if (dsc.dim == 2) hy *= 2;
-        }
-        M1_TRY(dalloc(&d, L));
-        M1_TRY(dalloc(&ctl, 1));
-        M1_CK(cudaMallocHost(&ctl_h, sizeof(Ctl)));
-        M1_CK(cudaMallocHost(&done_h, 2 * sizeof(int)));
-        M1_CK(cudaMallocHost(&bad_h, sizeof(unsigned int)));
-        std::memset(ctl_h, 0, sizeof(Ctl));
-        hist_len = 20001;
-        M1_TRY(dalloc(&hist, hist_len));
-        M1_TRY(dalloc(&dtau_hist, hist_len));
-        M1_TRY(dalloc(&part, h[0].tiles));
-        M1_TRY(dalloc(&partb, h[0].tiles));
-        M1_TRY(dalloc(&stage, (size_t)6 * h[0].n));
-        M1_TRY(dalloc(&sig_stage, h[0].n));
-        M1_TRY(dalloc(&bad, 1));
-        M1_TRY(upload_levels());
-        M1_CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream));
-        M1_CK(cudaStreamSynchronize(stream));
-        return M1_OK;
-    }
-
-    m1_status upload_levels()
-    {
-        M1_CK(cudaMemcpyAsync(d, h.data(), sizeof(Level<R>) * L, cudaMemcpyHostToDevice, stream));
-        M1_CK(cudaStreamSynchronize(stream));   // h may change right after
-        return M1_OK;
-    }
-
-    m1_status set_dt(double dt)
-    {
-        if (dt == dt_levels) return M1_OK;
-        for (int l = 0; l < L; ++l) {
-            Level<R>& q = h[l];
-            double hx = desc.lx / desc.nx * (double)(1 << l);
-            double hy = desc.dim == 2 ? desc.ly / desc.ny * (double)(1 << l) : 1.0;
-            double ax = desc.c * dt / hx, ay = desc.dim == 2 ? desc.c * dt / hy : 0.0;
-            q.ax = (R)ax; q.ay = (R)ay;
-            q.bx = (R)(dt / (2.0 * hx)); q.by = desc.dim == 2 ? (R)(dt / (2.0 * hy)) : R(0);
-            q.diag = (R)(1.0 + ax + ay);
-            q.cdt = (R)(desc.c * dt);
-        }
-        M1_TRY(upload_levels());
-        dt_levels = dt;
-        return M1_OK;
-    }
-
-    // ---- state in / out ------------------------------------------------------
-    m1_status pack_into(Cell4<R>* dst, const double* E, const double* Fx, const double* Fy,
-                        const double* T, double tscale, int dev)
-    {
-        const int n = h[0].n;
-        if (!dev) {
-            M1_CK(cudaMemcpyAsync(stage, E, n * 8, cudaMemcpyHostToDevice, stream));
-            M1_CK(cudaMemcpyAsync(stage + n, Fx, n * 8, cudaMemcpyHostToDevice, stream));
-            if (Fy) M1_CK(cudaMemcpyAsync(stage + 2 * (size_t)n, Fy, n * 8, cudaMemcpyHostToDevice, stream));
-            M1_CK(cudaMemcpyAsync(stage + 3 * (size_t)n, T, n * 8, cudaMemcpyHostToDevice, stream));
-            E = stage; Fx = stage + n; Fy = Fy ? stage + 2 * (size_t)n : nullptr; T = stage + 3 * (size_t)n;
-        }
-        m1::launch_pack_state<R>(E, Fx, Fy, T, tscale, dst, n, stream);
-        M1_CK(cudaGetLastError());
-        return M1_OK;
-    }
-
-    m1_status unpack_from(const Cell4<R>* src, int n, double* E, double* Fx, double* Fy, double* T,
-                          int dev)
-    {
-        if (dev) {
-            m1::launch_unpack_state<R>(src, E, Fx, Fy, T, n, stream);
-            M1_CK(cudaGetLastError());
-            M1_CK(cudaStreamSynchronize(stream));
-            return M1_OK;
-        }
-        double* s = stage;
-        m1::launch_unpack_state<R>(src, s, s + n, Fy ? s + 2 * (size_t)n : nullptr, s + 3 * (size_t)n,
-                                   n, stream);
-        M1_CK(cudaGetLastError());
-        M1_CK(cudaMemcpyAsync(E, s, n * 8, cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaMemcpyAsync(Fx, s + n, n * 8, cudaMemcpyDeviceToHost, stream));
-        if (Fy) M1_CK(cudaMemcpyAsync(Fy, s + 2 * (size_t)n, n * 8, cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaMemcpyAsync(T, s + 3 * (size_t)n, n * 8, cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaStreamSynchronize(stream));
-        return M1_OK;
-    }
-
-    m1_status set_state(const double* E, const double* Fx, const double* Fy, const double* T,
-                        const double* sa, const double* ss, int dev) override
-    {
-        const int n = h[0].n;
-        if (!E || !Fx || !T || (desc.dim == 2 && !Fy) || (!sa != !ss)) return M1_ERR_INVALID_ARG;
-        // stage into u[1] / sig_stage, check, then commit
-        M1_TRY(pack_into(h[0].u[1], E, Fx, Fy, T, 1.0, dev));
-        const Sig2<R>* sig_chk = nullptr;
-        if (sa) {
-            const double *a = sa, *b = ss;
-            if (!dev) {
-                M1_CK(cudaMemcpyAsync(stage + 4 * (size_t)n, sa, n * 8, cudaMemcpyHostToDevice, stream));
-                M1_CK(cudaMemcpyAsync(stage + 5 * (size_t)n, ss, n * 8, cudaMemcpyHostToDevice, stream));
-                a = stage + 4 * (size_t)n; b = stage + 5 * (size_t)n;
-            }
-            m1::launch_pack_sig<R>(a, b, sig_stage, n, stream);
-            sig_chk = sig_stage;
-        }
-        M1_CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), stream));
-        m1::launch_check_state<R>(h[0].u[1], sig_chk, n, desc.c, bad, stream);
-        M1_CK(cudaGetLastError());
-        M1_CK(cudaMemcpyAsync(bad_h, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaStreamSynchronize(stream));
-        if (*bad_h) return M1_ERR_NONADMISSIBLE_INPUT;
-        M1_CK(cudaMemcpyAsync(h[0].u[0], h[0].u[1], sizeof(Cell4<R>) * n, cudaMemcpyDeviceToDevice, stream));
-        if (sa) {
-            M1_CK(cudaMemcpyAsync(h[0].sig, sig_stage, sizeof(Sig2<R>) * n, cudaMemcpyDeviceToDevice, stream));
-            for (int l = 1; l < L; ++l) m1::launch_restrict_sig<R>(d + l - 1, d + l, h[l], stream);
-            M1_CK(cudaGetLastError());
-        }
-        rhs_valid = false;
-        M1_CK(cudaStreamSynchronize(stream));
-        return M1_OK;
-    }
-
-    m1_status set_inflow(int side, const double* E, const double* Fx, const double* Fy) override
-    {
-        if (side < 0 || side > 3 || !E || !Fx || !Fy) return M1_ERR_INVALID_ARG;
-        for (int l = 0; l < L; ++l) {
-            const int len = side < 2 ? h[l].ny : h[l].nx;
-            const int pl = h[l].prof_len;
-            for (int fld = 0; fld < 3; ++fld) {
-                double* dst = prof[l].data() + (size_t)(side * 3 + fld) * pl;
-                if (l == 0) {
-                    const double* src = fld == 0 ? E : (fld == 1 ? Fx : Fy);
-                    std::copy(src, src + len, dst);
-                } else {
-                    const int plf = h[l - 1].prof_len;
-                    const int nf = side < 2 ? h[l - 1].ny : h[l - 1].nx;
-                    restrict_profile(prof[l - 1].data() + (size_t)(side * 3 + fld) * plf, nf, dst, len);
-                }
-            }
-            std::vector<R> tmp(prof[l].begin(), prof[l].end());
-            M1_CK(cudaMemcpyAsync(h[l].inflow, tmp.data(), sizeof(R) * tmp.size(), cudaMemcpyHostToDevice, stream));
-            M1_CK(cudaStreamSynchronize(stream));
-        }
-        return M1_OK;
-    }
-
-    m1_status get_state(double* E, double* Fx, double* Fy, double* T, int dev) override
-    {
-        if (!E || !Fx || !T) return M1_ERR_INVALID_ARG;
-        return unpack_from(h[0].u[0], h[0].n, E, Fx, Fy, T, dev);
-    }
-
-    // ---- the V-cycle ------------------------------------------------------------
-    void sweeps_fine(int& cur, int count, cudaStream_t s)
-    {
-        for (int k = 0; k < count; ++k) {
-            m1::launch_sweep<R>(d, h[0], false, cur, 1 - cur, ctl, s, delta);
-            cur = 1 - cur;
-        }
-    }
-
-    // m pseudo-time steps (nu_l = 1 Jacobi sweep each) at level l; from_v: the
-    // first step starts from v_l (initial guess u_l = v_l, Algorithm 4).
-    void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
-    {
-        for (int k = 0; k < m; ++k) {
-            if (k == 0 && from_v) { m1::launch_sweep<R>(d + l, h[l], true, -1, 0, ctl, s, delta); cur = 0; }
-            else { m1::launch_sweep<R>(d + l, h[l], true, cur, 1 - cur, ctl, s, delta); cur = 1 - cur; }
-        }
-    }
-
-    // One V-cycle of Algorithm 4 on this hierarchy.  tail: end with the fine
-    // residual norm and the stop test (the mixed-precision driver does its own).
-    void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true)
-    {
-        std::vector<int> cur(L, 0);
-        cur[0] = cur0;
-        for (int l = 0; l < L - 1; ++l) {
-            if (l == 0) {
-                sweeps_fine(cur[0], p.nu0, s);
-                m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], nullptr, 1, ctl, s, delta);
-            } else {
-                m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s, delta);
-                pseudo(l, cur[l], p.m, true, s);
-                m1::launch_apply<R>(d + l, h[l], m1::APPLY_RESID, cur[l], nullptr, 1, ctl, s, delta);
-            }
-            m1::launch_restrict<R>(d + l, d + l + 1, h[l + 1], cur[l], ctl, s, delta);
-        }
-        if (L == 1) {
-            sweeps_fine(cur[0], p.nu0, s);
-        } else {
-            const int l = L - 1;
-            m1::launch_apply<R>(d + l, h[l], m1::APPLY_FAS, -1, nullptr, 0, ctl, s, delta);
-            pseudo(l, cur[l], p.mc, true, s);
-        }
-        for (int l = L - 2; l >= 0; --l) {
-            m1::launch_prolong<R>(d + l + 1, d + l, h[l], cur[l + 1], cur[l], ctl, s, delta);
-            if (l == 0) sweeps_fine(cur[0], p.nu0, s);
-            else pseudo(l, cur[l], p.m, false, s);
-        }
-        if (tail) {
-            m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, cur[0], part, 0, ctl, s);
-            m1::launch_finalize(ctl, part, h[0].tiles, nullptr, 0, m1::FIN_CYCLE, cur[0], s);
-        }
-        cur0 = cur[0];
-    }
-
-    long long kernels_per_cycle(const Params& p) const
-    {
-        if (L == 1) return p.nu0 + 2;
-        long long k = p.nu0 + 2;                           // fine pre-smooth, residual, restrict
-        k += (long long)(L - 2) * (p.m + 3);               // FAS rhs, pseudo, residual, restrict
-        k += 1 + p.mc;                                     // coarsest
-        k += (long long)(L - 2) * (1 + p.m) + 1 + p.nu0;   // prolong + post-smooth
-        return k + 2;                                      // final residual, finalize
-    }
-
-    m1_status build_graph(const Params& p)
-    {
-        if (graph && gparams == p) return M1_OK;
-        if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
-        // a captured graph must return the fine iterate to buffer 0
-        const int per_cycle = L == 1 ? p.nu0 : 2 * p.nu0;
-        graph_cycles = (per_cycle % 2) ? 2 : 1;
-        cudaGraph_t g = nullptr;
-        M1_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        int cur0 = 0;
-        for (int c = 0; c < graph_cycles; ++c) record_cycle(p, cur0, cap);
-        cudaError_t e = cudaStreamEndCapture(cap, &g);
-        if (e != cudaSuccess) { set_err(e, "cudaStreamEndCapture"); return M1_ERR_CUDA; }
-        if (cur0 != 0) { cudaGraphDestroy(g); return M1_ERR_INVALID_ARG; }
-        e = cudaGraphInstantiate(&graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { set_err(e, "cudaGraphInstantiate"); graph = nullptr; return M1_ERR_CUDA; }
-        gparams = p;
-        return M1_OK;
-    }
-
-    m1_status step(double dt, const m1_solve_params& sp, m1_step_stats* st) override
-    {
-        if (!(dt > 0) || sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 ||
-            sp.max_cycles < 1 || !(sp.tol >= 0))
-            return M1_ERR_INVALID_ARG;
-        M1_TRY(set_dt(dt));
-        Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
-        M1_TRY(build_graph(p));
-        // control block: parameters, reset counters
-        Ctl c{};
-        c.tol = sp.tol; c.grow = sp.grow; c.shrink = sp.shrink; c.eps_i = sp.eps_i;
-        c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
-        c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
-        c.hist_len = hist_len; c.hist = hist; c.dtau_hist = dtau_hist;
-        c.res0_floor = 1e-14 * (double)h[0].diag;   // rounding floor of evaluating A
-        *ctl_h = c;
-        M1_CK(cudaEventRecord(ev0, stream));
-        M1_CK(cudaMemcpyAsync(ctl, ctl_h, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
-        // b = (E^n, F^n, C_v T^n); r_0 = b - A(v^n); ||b||
-        m1::launch_make_rhs<R>(d, h[0], 0, stream);
-        m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, 0, part, 0, ctl, stream);
-        m1::launch_norm_state<R>(d, h[0], h[0].f, partb, stream);
-        m1::launch_finalize(ctl, part, h[0].tiles, partb, h[0].tiles, m1::FIN_INIT, 0, stream);
-        M1_CK(cudaGetLastError());
-        dt_rhs = dt; rhs_valid = true;
-        long long launched = 0;
-        M1_TRY(run_until_done(graph, graph_cycles, sp.max_cycles, stream, ctl, done_h, poll, &launched));
-        M1_CK(cudaMemcpyAsync(ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaStreamSynchronize(stream));
-        if (ctl_h->result_buf == 1) {
-            M1_CK(cudaMemcpyAsync(h[0].u[0], h[0].u[1], sizeof(Cell4<R>) * h[0].n,
-                                  cudaMemcpyDeviceToDevice, stream));
-        }
-        M1_CK(cudaEventRecord(ev1, stream));
-        M1_CK(cudaEventSynchronize(ev1));
-        last_cycles = ctl_h->kappa;
-        if (st) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev0, ev1);
-            st->cycles = ctl_h->kappa;
-            st->res0 = ctl_h->res0;
-            st->res = ctl_h->kappa > 0 ? ctl_h->res : ctl_h->res0;
-            st->dtau_final = ctl_h->dtau;
-            st->sweeps = (long long)ctl_h->kappa * (L == 1 ? p.nu0 : 2 * p.nu0);
-            st->ms = ms;
-            st->status = ctl_h->status;
-            st->newton_fail = ctl_h->newton_fail;
-            st->damped = ctl_h->damped;
-            st->launches = 4 + launched * (long long)kernels_per_cycle(p);
-        }
-        return ctl_h->status == m1::CTL_OK ? M1_OK : M1_ERR_NOT_CONVERGED;
-    }
-
-    m1_status residual_norm(double dt, double* out) override
-    {
-        if (!out || !(dt > 0)) return M1_ERR_INVALID_ARG;
-        M1_TRY(set_dt(dt));
-        if (!(rhs_valid && dt == dt_rhs)) m1::launch_make_rhs<R>(d, h[0], 0, stream);
-        m1::launch_apply<R>(d, h[0], m1::APPLY_RESID, 0, part, 0, nullptr, stream);
-        M1_CK(cudaGetLastError());
-        std::vector<double> p(h[0].tiles);
-        M1_CK(cudaMemcpyAsync(p.data(), part, sizeof(double) * p.size(), cudaMemcpyDeviceToHost, stream));
-        M1_CK(cudaStreamSynchronize(stream));
-        double s = 0.0;
-        for (double x : p) s += x;
-        *out = std::sqrt(s);
-        return M1_OK;
-    }
-
-    m1_status jacobi(double dt, int sweeps) override
-    {
-        if (!(dt > 0) || sweeps < 0) return M1_ERR_INVALID_ARG;
-        M1_TRY(set_dt(dt));
-        M1_TRY(set_ctl_simple(0.0, 0.5, 0.5));
-        m1::launch_make_rhs<R>(d, h[0], 0, stream);
-        int cur = 0;
-        sweeps_fine(cur, sweeps, stream);
-        M1_CK(cudaGetLastError());
-        if (cur == 1)
-            M1_CK(cudaMemcpyAsync(h[0].u[0], h[0].u[1], sizeof(Cell4<R>) * h[0].n,
-                                  cudaMemcpyDeviceToDevice, stream));
-        dt_rhs = dt; rhs_valid = true;
-        return M1_OK;
-    }
-
-    m1_status history(double* hs, double* dt, int len) override
-    {
-        const int n = std::min(len, std::min(last_cycles + 1, hist_len));
-        if (n <= 0) return M1_OK;
-        if (hs) M1_CK(cudaMemcpy(hs, hist, sizeof(double) * n, cudaMemcpyDeviceToHost));
-        if (dt && n > 1) M1_CK(cudaMemcpy(dt, dtau_hist, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost));
-        return M1_OK;
-    }
-
-    // ---- single-kernel checks ----------------------------------------------------
-    m1_status pack_planar(Cell4<R>* dst, int n, const double* planar)
-    {
-        M1_CK(cudaMemcpyAsync(stage, planar, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, stream));
-        m1::launch_pack_state<R>(stage, stage + n, stage + 2 * (size_t)n, stage + 3 * (size_t)n, 1.0, dst, n, stream);
-        M1_CK(cudaGetLastError());
-        return M1_OK;
-    }
-    m1_status unpack_planar(const Cell4<R>* src, int n, double* planar)
-    {
-        return unpack_from(src, n, planar, planar + n, planar + 2 * (size_t)n, planar + 3 * (size_t)n, 0);
-    }
-    m1_status set_sig_planar(const double* sig)
-    {
-        const int n = h[0].n;
-        M1_CK(cudaMemcpyAsync(stage + 4 * (size_t)n, sig, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, stream));
-        m1::launch_pack_sig<R>(stage + 4 * (size_t)n, stage + 5 * (size_t)n, h[0].sig, n, stream);
-        M1_CK(cudaGetLastError());
-        return M1_OK;
-    }
-    m1_status set_ctl_simple(double dtau, double theta_ex, double theta_c)
-    {
-        Ctl c{};
-        c.dtau = dtau; c.theta_ex = theta_ex; c.theta_c = theta_c;
-        *ctl_h = c;
-        M1_CK(cudaMemcpyAsync(ctl, ctl_h, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
-        return M1_OK;
-    }
-
-    m1_status op_level(double dt, const double* sig, const double* state, const double* rhs,
-                       int mode, double dtau, double theta, double* out, double* norm)
-    {
-        const int n = h[0].n;
-        M1_TRY(set_dt(dt));
-        M1_TRY(set_sig_planar(sig));
-        M1_TRY(set_ctl_simple(dtau, theta, 0.5));
-        const Level<R>& q = h[0];
-        switch (mode) {
-        case M1_OP_APPLY:
-            M1_TRY(pack_planar(q.u[0], n, state));
-            m1::launch_apply<R>(d, q, m1::APPLY_A, 0, nullptr, 0, ctl, stream);
-            M1_CK(cudaGetLastError());
-            return unpack_planar(q.r, n, out);
-        case M1_OP_RESIDUAL: {
-            M1_TRY(pack_planar(q.u[0], n, state));
-            M1_TRY(pack_planar(q.f, n, rhs));
-            m1::launch_apply<R>(d, q, m1::APPLY_RESID, 0, part, 1, ctl, stream);
-            M1_CK(cudaGetLastError());
-            M1_TRY(unpack_planar(q.r, n, out));
-            if (norm) {
-                std::vector<double> p(q.tiles);
-                M1_CK(cudaMemcpy(p.data(), part, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
-                double s = 0.0;
-                for (double x : p) s += x;
-                *norm = std::sqrt(s);
-            }
-            return M1_OK;
-        }
-        case M1_OP_FAS_RHS:
-            M1_TRY(pack_planar(q.v, n, state));
-            M1_TRY(pack_planar(q.r, n, rhs));
-            m1::launch_apply<R>(d, q, m1::APPLY_FAS, -1, nullptr, 0, ctl, stream);
-            M1_CK(cudaGetLastError());
-            return unpack_planar(q.f, n, out);
-        case M1_OP_JACOBI:
-        case M1_OP_PSEUDO:
-            M1_TRY(pack_planar(q.u[0], n, state));
-            M1_TRY(pack_planar(q.f, n, rhs));
-            m1::launch_sweep<R>(d, q, mode == M1_OP_PSEUDO, 0, 1, ctl, stream);
-            M1_CK(cudaGetLastError());
-            return unpack_planar(q.u[1], n, out);
-        default:
-            return M1_ERR_INVALID_ARG;
-        }
-    }
-
-    m1_status op_restrict(const double* state, const double* resid, double* cs, double* cr)
-    {
-        const int n = h[0].n;
-        M1_TRY(set_ctl_simple(0, 0.5, 0.5));
-        M1_TRY(pack_planar(h[0].u[0], n, state));
-        M1_TRY(pack_planar(h[0].r, n, resid));
-        m1::launch_restrict<R>(d, d + 1, h[1], 0, ctl, stream);
-        M1_CK(cudaGetLastError());
-        M1_TRY(unpack_planar(h[1].v, h[1].n, cs));
-        return unpack_planar(h[1].r, h[1].n, cr);
-    }
-
-    m1_status op_prolong(const double* uc, const double* vc, const double* uf, double theta,
-                         double* out, int* damped)
-    {
-        M1_TRY(set_ctl_simple(0, 0.5, theta));
-        M1_TRY(pack_planar(h[1].u[0], h[1].n, uc));
-        M1_TRY(pack_planar(h[1].v, h[1].n, vc));
-        M1_TRY(pack_planar(h[0].u[0], h[0].n, uf));
-        m1::launch_prolong<R>(d + 1, d, h[0], 0, 0, ctl, stream);
-        M1_CK(cudaGetLastError());
-        M1_TRY(unpack_planar(h[0].u[0], h[0].n, out));
-        if (damped) {
-            M1_CK(cudaMemcpy(ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-            *damped = (int)ctl_h->damped;
-        }
-        return M1_OK;
-    }
-};
-
-// Mixed precision (row a11): the FP32 hierarchy `lo` runs the V-cycles of
-// Algorithm 4 on the correction problem A32(u) = A32(v32) + r64; the FP64 fine
-// level `hi` holds v^n, b and the opacities, computes the residual r64 and its
-// norm (stop test, dtau control), and accumulates the corrections in FP64.
-// Both share `hi`'s control block and stream.
-struct MixedImpl : ImplBase {
-    Impl<double> hi;
-    Impl<float> lo;
-    cudaGraphExec_t graph = nullptr;
-    Params gparams{};
-
-    ~MixedImpl() override
-    {
-        if (graph) cudaGraphExecDestroy(graph);
-    }
-
-    m1_status init(const m1_grid_desc& dsc, cudaStream_t s)
-    {
-        m1_grid_desc d = dsc;
-        d.lmax = 1;
-        d.precision = M1_FP64;
-        M1_TRY(hi.init(d, s));
-        M1_TRY(lo.init(dsc, hi.stream, true));
-        lo.ctl = hi.ctl;
-        return M1_OK;
-    }
-
-    m1_status set_state(const double* E, const double* Fx, const double* Fy, const double* T,
-                        const double* sa, const double* ss, int dev) override
-    {
-        M1_TRY(hi.set_state(E, Fx, Fy, T, sa, ss, dev));
-        return lo.set_state(E, Fx, Fy, T, sa, ss, dev);
-    }
-
-    m1_status set_inflow(int side, const double* E, const double* Fx, const double* Fy) override
-    {
-        M1_TRY(hi.set_inflow(side, E, Fx, Fy));
-        return lo.set_inflow(side, E, Fx, Fy);
-    }
-
-    m1_status get_state(double* E, double* Fx, double* Fy, double* T, int dev) override
-    {
-        return hi.get_state(E, Fx, Fy, T, dev);
-    }
-
-    m1_status residual_norm(double dt, double* out) override { return hi.residual_norm(dt, out); }
-    m1_status history(double* hs, double* dt, int len) override { return hi.history(hs, dt, len); }
-    m1_status jacobi(double, int) override { return M1_ERR_INVALID_ARG; }
-
-    // FP32 V-cycle, FP64 accumulation of its correction, FP64 defect of the new
-    // iterate with the FP32 right-hand side of the next cycle, stop test.
-    void record_mixed_cycle(const Params& p, cudaStream_t s)
-    {
-        int cur0 = 0;
-        lo.record_cycle(p, cur0, s, false);
-        m1::launch_accumulate(hi.d, hi.h[0], lo.d, cur0, hi.ctl, s);
-        m1::launch_defect(hi.d, hi.h[0], lo.d, hi.part, hi.ctl, s);
-        m1::launch_finalize(hi.ctl, hi.part, hi.h[0].tiles, nullptr, 0, m1::FIN_CYCLE, 0, s);
-    }
-
-    m1_status build_graph(const Params& p)
-    {
-        if (graph && gparams == p) return M1_OK;
-        if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
-        cudaGraph_t g = nullptr;
-        M1_CK(cudaStreamBeginCapture(lo.cap, cudaStreamCaptureModeThreadLocal));
-        record_mixed_cycle(p, lo.cap);
-        cudaError_t e = cudaStreamEndCapture(lo.cap, &g);
-        if (e != cudaSuccess) { set_err(e, "cudaStreamEndCapture"); return M1_ERR_CUDA; }
-        e = cudaGraphInstantiate(&graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { set_err(e, "cudaGraphInstantiate"); graph = nullptr; return M1_ERR_CUDA; }
-        gparams = p;
-        return M1_OK;
-    }
-
-    m1_status step(double dt, const m1_solve_params& sp, m1_step_stats* st) override
-    {
-        if (!(dt > 0) || sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 ||
-            sp.max_cycles < 1 || !(sp.tol >= 0))
-            return M1_ERR_INVALID_ARG;
-        M1_TRY(hi.set_dt(dt));
-        M1_TRY(lo.set_dt(dt));
-        Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
-        M1_TRY(build_graph(p));
-        Ctl c{};
-        c.tol = sp.tol; c.grow = sp.grow; c.shrink = sp.shrink; c.eps_i = sp.eps_i;
-        c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
-        c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
-        c.hist_len = hi.hist_len; c.hist = hi.hist; c.dtau_hist = hi.dtau_hist;
-        c.res0_floor = 1e-14 * (double)hi.h[0].diag;
-        *hi.ctl_h = c;
-        cudaStream_t s = hi.stream;
-        M1_CK(cudaEventRecord(hi.ev0, s));
-        M1_CK(cudaMemcpyAsync(hi.ctl, hi.ctl_h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        m1::launch_make_rhs<double>(hi.d, hi.h[0], 0, s);
-        m1::launch_norm_state<double>(hi.d, hi.h[0], hi.h[0].f, hi.partb, s);
-        m1::launch_defect(hi.d, hi.h[0], lo.d, hi.part, hi.ctl, s);
-        m1::launch_finalize(hi.ctl, hi.part, hi.h[0].tiles, hi.partb, hi.h[0].tiles, m1::FIN_INIT, 0, s);
-        M1_CK(cudaGetLastError());
-        hi.dt_rhs = dt; hi.rhs_valid = true;
-        long long launched = 0;
-        M1_TRY(run_until_done(graph, 1, sp.max_cycles, s, hi.ctl, hi.done_h, hi.poll, &launched));
-        M1_CK(cudaMemcpyAsync(hi.ctl_h, hi.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        M1_CK(cudaEventRecord(hi.ev1, s));
-        M1_CK(cudaEventSynchronize(hi.ev1));
-        hi.last_cycles = hi.ctl_h->kappa;
-        if (st) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, hi.ev0, hi.ev1);
-            st->cycles = hi.ctl_h->kappa;
-            st->res0 = hi.ctl_h->res0;
-            st->res = hi.ctl_h->kappa > 0 ? hi.ctl_h->res : hi.ctl_h->res0;
-            st->dtau_final = hi.ctl_h->dtau;
-            st->sweeps = (long long)hi.ctl_h->kappa * (lo.L == 1 ? p.nu0 : 2 * p.nu0);
-            st->ms = ms;
-            st->status = hi.ctl_h->status;
-            st->newton_fail = hi.ctl_h->newton_fail;
-            st->damped = hi.ctl_h->damped;
-            st->launches = 4 + launched * (lo.kernels_per_cycle(p) + 1);
-        }
-        return hi.ctl_h->status == m1::CTL_OK ? M1_OK : M1_ERR_NOT_CONVERGED;
-    }
-};
-
-m1_status validate(const m1_grid_desc* d)
+m1_status validate_desc(const m1_grid_desc* d)
 {
     if (!d) return M1_ERR_INVALID_ARG;
     if (d->dim != 1 && d->dim != 2) return M1_ERR_INVALID_ARG;
@@ -784,38 +90,966 @@ m1_status validate(const m1_grid_desc* d)
     return M1_OK;
 }
 
-template <typename R>
-m1_status make_op_impl(const m1_grid_desc* desc, int lmax, const double* inflow,
-                       std::unique_ptr<Impl<R>>& out)
+m1_status validate_params(const m1_solve_params& sp)
 {
-    m1_grid_desc d = *desc;
-    d.lmax = lmax;
-    M1_TRY(validate(&d));
-    out.reset(new Impl<R>());
-    M1_TRY(out->init(d, nullptr));
+    if (sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 || sp.max_cycles < 1 ||
+        !(sp.tol >= 0) || !(sp.dtau0 > 0) || !(sp.theta_ex > 0) || !(sp.theta_c > 0))
+        return M1_ERR_INVALID_ARG;
+    return M1_OK;
+}
+
+Ctl make_ctl(const m1_solve_params& sp, double diag0)
+{
+    Ctl c{};
+    c.tol = sp.tol; c.grow = sp.grow; c.shrink = sp.shrink; c.eps_i = sp.eps_i;
+    c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
+    c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
+    c.res0_floor = 1e-14 * diag0;   // rounding floor of evaluating A
+    c.active = 1;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+Engine<R>::~Engine()
+{
+    if (graph) cudaGraphExecDestroy(graph);
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& v : mem)
+        for (void* p : v) cudaFree(p);
+    for (void* p : common) cudaFree(p);
+    for (DevList* l : all_lists()) {
+        if (l->items) cudaFree(l->items);
+        if (l->count) cudaFree(l->count);
+    }
+    if (ctl_h) cudaFreeHost(ctl_h);
+    if (bctl_h) cudaFreeHost(bctl_h);
+    if (done_h) cudaFreeHost(done_h);
+    if (bad_h) cudaFreeHost(bad_h);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (auto& e : poll)
+        if (e) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+template <typename R>
+std::vector<DevList*> Engine<R>::all_lists()
+{
+    std::vector<DevList*> v;
+    for (auto& l : tiles) v.push_back(&l);
+    for (auto& l : chunks) v.push_back(&l);
+    v.push_back(&init_tiles);
+    v.push_back(&init_chunks);
+    return v;
+}
+
+template <typename R>
+m1_status Engine<R>::calloc_common(void** p, size_t bytes)
+{
+    M1_CK(cudaMalloc(p, std::max<size_t>(bytes, 8)));
+    common.push_back(*p);
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::init(int capacity, int levels, bool correction_form, cudaStream_t s,
+                          int history_len)
+{
+    cap = capacity;
+    L = levels;
+    delta = correction_form;
+    if (s) stream = s;
+    else { M1_CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking)); own_stream = true; }
+    M1_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    M1_CK(cudaEventCreate(&ev0));
+    M1_CK(cudaEventCreate(&ev1));
+    M1_CK(cudaEventCreateWithFlags(&poll[0], cudaEventDisableTiming));
+    M1_CK(cudaEventCreateWithFlags(&poll[1], cudaEventDisableTiming));
+    desc.assign(cap, m1_grid_desc{});
+    used.assign(cap, 0);
+    mem.assign(cap, {});
+    h.assign((size_t)L * cap, Level<R>{});
+    prof.assign((size_t)L * cap, {});
+    dt_set.assign(cap, NAN);
+    dt_rhs.assign(cap, NAN);
+    rhs_valid.assign(cap, 0);
+    last_cycles.assign(cap, 0);
+    tiles.assign(L, DevList{});
+    chunks.assign(L, DevList{});
+    M1_TRY(calloc_common((void**)&d, sizeof(Level<R>) * L * cap));
+    M1_TRY(calloc_common((void**)&ctl, sizeof(Ctl) * cap));
+    M1_TRY(calloc_common((void**)&bctl, sizeof(BatchCtl)));
+    M1_TRY(calloc_common((void**)&init_slots, sizeof(int) * cap));
+    M1_TRY(calloc_common((void**)&bad, sizeof(unsigned int)));
+    M1_CK(cudaMallocHost(&ctl_h, sizeof(Ctl) * cap));
+    M1_CK(cudaMallocHost(&bctl_h, sizeof(BatchCtl)));
+    M1_CK(cudaMallocHost(&done_h, 2 * sizeof(int)));
+    M1_CK(cudaMallocHost(&bad_h, sizeof(unsigned int)));
+    std::memset(ctl_h, 0, sizeof(Ctl) * cap);
+    std::memset(bctl_h, 0, sizeof(BatchCtl));
+    M1_CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * cap, stream));
+    M1_CK(cudaMemsetAsync(bctl, 0, sizeof(BatchCtl), stream));
+    hist_len = history_len;
+    if (hist_len > 0) {
+        M1_TRY(calloc_common((void**)&hist, sizeof(double) * hist_len * cap));
+        M1_TRY(calloc_common((void**)&dtau_hist, sizeof(double) * hist_len * cap));
+    }
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::slot_alloc(int i, void** p, size_t bytes)
+{
+    M1_CK(cudaMalloc(p, std::max<size_t>(bytes, 16)));
+    mem[i].push_back(*p);
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
+{
+    int i = -1;
+    for (int k = 0; k < cap; ++k)
+        if (!used[k]) { i = k; break; }
+    if (i < 0) return M1_ERR_REJECTED;
+    m1_grid_desc g = dsc;
+    g.lmax = L;
+    desc[i] = g;
+    int nx = g.nx, ny = g.dim == 2 ? g.ny : 1;
+    double hx = g.lx / g.nx, hy = g.dim == 2 ? g.ly / g.ny : 1.0;
+    for (int l = 0; l < L; ++l) {
+        Level<R>& q = h[(size_t)l * cap + i];
+        std::memset(&q, 0, sizeof(q));
+        q.dim = g.dim; q.nx = nx; q.ny = ny; q.n = nx * ny;
+        for (int w = 0; w < 4; ++w) q.bc[w] = g.bc[w];
+        q.tx = g.dim == 2 ? kTx2 : kTx1;
+        q.ty = g.dim == 2 ? kTy2 : 1;
+        q.tiles_x = (nx + q.tx - 1) / q.tx;
+        q.tiles = q.tiles_x * ((ny + q.ty - 1) / q.ty);
+        q.chunks = (q.n + kThreads - 1) / kThreads;
+        q.prof_len = std::max(nx, ny);
+        q.c = (R)g.c; q.a_r = (R)g.a_r; q.c_v = (R)g.c_v;
+        q.vol = g.dim == 2 ? hx * hy : hx;
+        const size_t c4 = sizeof(Cell4<R>) * q.n;
+        M1_TRY(slot_alloc(i, (void**)&q.v, c4));
+        M1_TRY(slot_alloc(i, (void**)&q.u[0], c4));
+        M1_TRY(slot_alloc(i, (void**)&q.u[1], c4));
+        M1_TRY(slot_alloc(i, (void**)&q.f, c4));
+        M1_TRY(slot_alloc(i, (void**)&q.r, c4));
+        if (delta) {
+            M1_TRY(slot_alloc(i, (void**)&q.w, c4));
+            M1_TRY(slot_alloc(i, (void**)&q.aw, c4));
+        }
+        M1_TRY(slot_alloc(i, (void**)&q.sig, sizeof(Sig2<R>) * q.n));
+        M1_TRY(slot_alloc(i, (void**)&q.inflow, sizeof(R) * 12 * q.prof_len));
+        M1_CK(cudaMemsetAsync(q.inflow, 0, sizeof(R) * 12 * q.prof_len, stream));
+        M1_CK(cudaMemsetAsync(q.sig, 0, sizeof(Sig2<R>) * q.n, stream));
+        prof[(size_t)l * cap + i].assign((size_t)12 * q.prof_len, 0.0);
+        nx /= 2; if (g.dim == 2) ny /= 2;
+        hx *= 2; if (g.dim == 2) hy *= 2;
+    }
+    used[i] = 1;
+    dt_set[i] = NAN;
+    rhs_valid[i] = 0;
+    last_cycles[i] = 0;
+    ctl_h[i] = Ctl{};
+    M1_CK(cudaMemcpyAsync(ctl + i, ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
+    M1_TRY(ensure_stage((size_t)h[i].n));
+    M1_CK(cudaStreamSynchronize(stream));
+    *out = i;
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::remove_slot(int i)
+{
+    if (i < 0 || i >= cap || !used[i]) return M1_ERR_INVALID_ARG;
+    M1_CK(cudaStreamSynchronize(stream));
+    for (void* p : mem[i]) cudaFree(p);
+    mem[i].clear();
+    used[i] = 0;
+    for (int l = 0; l < L; ++l) std::memset(&h[(size_t)l * cap + i], 0, sizeof(Level<R>));
+    ctl_h[i] = Ctl{};
+    M1_CK(cudaMemcpyAsync(ctl + i, ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::ensure_stage(size_t n)
+{
+    if (n <= stage_n) return M1_OK;
+    M1_CK(cudaStreamSynchronize(stream));
+    auto drop = [this](void* p) {
+        if (!p) return;
+        cudaFree(p);
+        common.erase(std::find(common.begin(), common.end(), p));
+    };
+    drop(stage);
+    drop(sig_stage);
+    void* p = nullptr;
+    M1_TRY(calloc_common(&p, sizeof(double) * 6 * n));
+    stage = static_cast<double*>(p);
+    M1_TRY(calloc_common(&p, sizeof(Sig2<R>) * n));
+    sig_stage = static_cast<Sig2<R>*>(p);
+    stage_n = n;
+    return M1_OK;
+}
+
+// Upload a host list into its device buffer, growing the buffer (which changes
+// the pointers a captured graph holds, so the graph is rebuilt) when needed.
+template <typename R>
+m1_status Engine<R>::upload_list(DevList& l)
+{
+    const int n = (int)l.host.size();
+    if (n > l.capacity || !l.items) {
+        int capn = 1;
+        while (capn < n) capn <<= 1;
+        M1_CK(cudaStreamSynchronize(stream));
+        if (l.items) cudaFree(l.items);
+        if (l.count) cudaFree(l.count);
+        l.items = nullptr;
+        l.count = nullptr;
+        M1_CK(cudaMalloc(&l.items, sizeof(int2) * capn));
+        M1_CK(cudaMalloc(&l.count, sizeof(int)));
+        l.capacity = capn;
+        graph_dirty = true;
+    }
+    l.n = n;
+    if (n)
+        M1_CK(cudaMemcpyAsync(l.items, l.host.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaMemcpyAsync(l.count, &l.n, sizeof(int), cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+// Work lists of every level over the used slots, the slots' offsets into the
+// norm partials, and the descriptors, uploaded to the device.
+template <typename R>
+m1_status Engine<R>::rebuild()
+{
+    int off = 0;
+    for (int i = 0; i < cap; ++i)
+        if (used[i]) { h[i].part_off = off; off += h[i].tiles; }
+    if (off > part_cap || !part) {
+        int capn = 1;
+        while (capn < off) capn <<= 1;
+        M1_CK(cudaStreamSynchronize(stream));
+        auto drop = [this](void* p) {
+            if (!p) return;
+            cudaFree(p);
+            common.erase(std::find(common.begin(), common.end(), p));
+        };
+        drop(part);
+        drop(partb);
+        M1_TRY(calloc_common((void**)&part, sizeof(double) * capn));
+        M1_TRY(calloc_common((void**)&partb, sizeof(double) * capn));
+        part_cap = capn;
+        graph_dirty = true;
+    }
+    for (int l = 0; l < L; ++l) {
+        tiles[l].host.clear();
+        chunks[l].host.clear();
+        for (int i = 0; i < cap; ++i) {
+            if (!used[i]) continue;
+            const Level<R>& q = h[(size_t)l * cap + i];
+            for (int t = 0; t < q.tiles; ++t) tiles[l].host.push_back(make_int2(i, t));
+            for (int c = 0; c < q.chunks; ++c) chunks[l].host.push_back(make_int2(i, c));
+        }
+        M1_TRY(upload_list(tiles[l]));
+        M1_TRY(upload_list(chunks[l]));
+    }
+    M1_CK(cudaMemcpyAsync(d, h.data(), sizeof(Level<R>) * h.size(), cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::set_dt(int i, double dt)
+{
+    if (dt == dt_set[i]) return M1_OK;
+    const m1_grid_desc& g = desc[i];
+    for (int l = 0; l < L; ++l) {
+        Level<R>& q = h[(size_t)l * cap + i];
+        const double hx = g.lx / g.nx * (double)(1 << l);
+        const double hy = g.dim == 2 ? g.ly / g.ny * (double)(1 << l) : 1.0;
+        const double ax = g.c * dt / hx, ay = g.dim == 2 ? g.c * dt / hy : 0.0;
+        q.ax = (R)ax; q.ay = (R)ay;
+        q.bx = (R)(dt / (2.0 * hx)); q.by = g.dim == 2 ? (R)(dt / (2.0 * hy)) : R(0);
+        q.diag = (R)(1.0 + ax + ay);
+        q.cdt = (R)(g.c * dt);
+        M1_CK(cudaMemcpyAsync(d + (size_t)l * cap + i, &q, sizeof(Level<R>), cudaMemcpyHostToDevice,
+                              stream));
+    }
+    M1_CK(cudaStreamSynchronize(stream));   // h may change right after
+    dt_set[i] = dt;
+    return M1_OK;
+}
+
+// ---- state in / out ---------------------------------------------------------
+template <typename R>
+m1_status Engine<R>::pack_into(int i, Cell4<R>* dst, const double* E, const double* Fx,
+                               const double* Fy, const double* T, int dev)
+{
+    const int n = h[i].n;
+    if (!dev) {
+        M1_CK(cudaMemcpyAsync(stage, E, n * 8, cudaMemcpyHostToDevice, stream));
+        M1_CK(cudaMemcpyAsync(stage + n, Fx, n * 8, cudaMemcpyHostToDevice, stream));
+        if (Fy) M1_CK(cudaMemcpyAsync(stage + 2 * (size_t)n, Fy, n * 8, cudaMemcpyHostToDevice, stream));
+        M1_CK(cudaMemcpyAsync(stage + 3 * (size_t)n, T, n * 8, cudaMemcpyHostToDevice, stream));
+        E = stage; Fx = stage + n; Fy = Fy ? stage + 2 * (size_t)n : nullptr; T = stage + 3 * (size_t)n;
+    }
+    launch_pack_state<R>(E, Fx, Fy, T, 1.0, dst, n, stream);
+    M1_CK(cudaGetLastError());
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::unpack_from(const Cell4<R>* src, int n, double* E, double* Fx, double* Fy,
+                                 double* T, int dev)
+{
+    if (dev) {
+        launch_unpack_state<R>(src, E, Fx, Fy, T, n, stream);
+        M1_CK(cudaGetLastError());
+        M1_CK(cudaStreamSynchronize(stream));
+        return M1_OK;
+    }
+    double* s = stage;
+    launch_unpack_state<R>(src, s, s + n, Fy ? s + 2 * (size_t)n : nullptr, s + 3 * (size_t)n, n, stream);
+    M1_CK(cudaGetLastError());
+    M1_CK(cudaMemcpyAsync(E, s, n * 8, cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaMemcpyAsync(Fx, s + n, n * 8, cudaMemcpyDeviceToHost, stream));
+    if (Fy) M1_CK(cudaMemcpyAsync(Fy, s + 2 * (size_t)n, n * 8, cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaMemcpyAsync(T, s + 3 * (size_t)n, n * 8, cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::set_state(int i, const double* E, const double* Fx, const double* Fy,
+                               const double* T, const double* sa, const double* ss, int dev)
+{
+    if (i < 0 || i >= cap || !used[i]) return M1_ERR_INVALID_ARG;
+    const Level<R>& q0 = h[i];
+    const int n = q0.n;
+    if (!E || !Fx || !T || (q0.dim == 2 && !Fy) || (!sa != !ss)) return M1_ERR_INVALID_ARG;
+    // stage into u[1] / sig_stage, check, then commit
+    M1_TRY(pack_into(i, q0.u[1], E, Fx, Fy, T, dev));
+    const Sig2<R>* sig_chk = nullptr;
+    if (sa) {
+        const double *a = sa, *b = ss;
+        if (!dev) {
+            M1_CK(cudaMemcpyAsync(stage + 4 * (size_t)n, sa, n * 8, cudaMemcpyHostToDevice, stream));
+            M1_CK(cudaMemcpyAsync(stage + 5 * (size_t)n, ss, n * 8, cudaMemcpyHostToDevice, stream));
+            a = stage + 4 * (size_t)n;
+            b = stage + 5 * (size_t)n;
+        }
+        launch_pack_sig<R>(a, b, sig_stage, n, stream);
+        sig_chk = sig_stage;
+    }
+    M1_CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), stream));
+    launch_check_state<R>(q0.u[1], sig_chk, n, desc[i].c, bad, stream);
+    M1_CK(cudaGetLastError());
+    M1_CK(cudaMemcpyAsync(bad_h, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    if (*bad_h) return M1_ERR_NONADMISSIBLE_INPUT;
+    M1_CK(cudaMemcpyAsync(q0.u[0], q0.u[1], sizeof(Cell4<R>) * n, cudaMemcpyDeviceToDevice, stream));
+    if (sa) {
+        M1_CK(cudaMemcpyAsync(q0.sig, sig_stage, sizeof(Sig2<R>) * n, cudaMemcpyDeviceToDevice, stream));
+        // opacities of the coarse levels: full weighting, one level after another
+        for (int l = 1; l < L; ++l) {
+            init_chunks.host.clear();
+            for (int c = 0; c < h[(size_t)l * cap + i].chunks; ++c)
+                init_chunks.host.push_back(make_int2(i, c));
+            M1_TRY(upload_list(init_chunks));
+            launch_restrict_sig<R>(d + (size_t)(l - 1) * cap, d + (size_t)l * cap, init_chunks.view(),
+                                   stream);
+            M1_CK(cudaGetLastError());
+        }
+    }
+    rhs_valid[i] = 0;
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::set_inflow(int i, int side, const double* E, const double* Fx, const double* Fy)
+{
+    if (i < 0 || i >= cap || !used[i] || side < 0 || side > 3 || !E || !Fx || !Fy)
+        return M1_ERR_INVALID_ARG;
+    for (int l = 0; l < L; ++l) {
+        const Level<R>& q = h[(size_t)l * cap + i];
+        const int len = side < 2 ? q.ny : q.nx;
+        const int pl = q.prof_len;
+        std::vector<double>& P = prof[(size_t)l * cap + i];
+        for (int fld = 0; fld < 3; ++fld) {
+            double* dst = P.data() + (size_t)(side * 3 + fld) * pl;
+            if (l == 0) {
+                const double* src = fld == 0 ? E : (fld == 1 ? Fx : Fy);
+                std::copy(src, src + len, dst);
+            } else {
+                const Level<R>& p = h[(size_t)(l - 1) * cap + i];
+                const int nf = side < 2 ? p.ny : p.nx;
+                restrict_profile(prof[(size_t)(l - 1) * cap + i].data() + (size_t)(side * 3 + fld) * p.prof_len,
+                                 nf, dst, len);
+            }
+        }
+        std::vector<R> tmp(P.begin(), P.end());
+        M1_CK(cudaMemcpyAsync(q.inflow, tmp.data(), sizeof(R) * tmp.size(), cudaMemcpyHostToDevice, stream));
+        M1_CK(cudaStreamSynchronize(stream));
+    }
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev)
+{
+    if (i < 0 || i >= cap || !used[i] || !E || !Fx || !T) return M1_ERR_INVALID_ARG;
+    return unpack_from(h[i].u[0], h[i].n, E, Fx, Fy, T, dev);
+}
+
+// ---- the V-cycle ----------------------------------------------------------------
+template <typename R>
+void Engine<R>::sweeps_fine(int& cur, int count, cudaStream_t s)
+{
+    for (int k = 0; k < count; ++k) {
+        launch_sweep<R>(d, tiles[0].view(), ctl, false, cur, 1 - cur, s, delta);
+        cur = 1 - cur;
+    }
+}
+
+// m pseudo-time steps (nu_l = 1 Jacobi sweep each) at level l; from_v: the
+// first step starts from v_l (initial guess u_l = v_l, Algorithm 4).
+template <typename R>
+void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
+{
+    Level<R>* dl = d + (size_t)l * cap;
+    for (int k = 0; k < m; ++k) {
+        if (k == 0 && from_v) {
+            launch_sweep<R>(dl, tiles[l].view(), ctl, true, -1, 0, s, delta);
+            cur = 0;
+        } else {
+            launch_sweep<R>(dl, tiles[l].view(), ctl, true, cur, 1 - cur, s, delta);
+            cur = 1 - cur;
+        }
+    }
+}
+
+// One V-cycle of Algorithm 4 over every instance.  tail: end with the fine
+// residual norm and the stop test (the mixed-precision driver does its own).
+template <typename R>
+void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail)
+{
+    std::vector<int> cur(L, 0);
+    cur[0] = cur0;
+    for (int l = 0; l < L - 1; ++l) {
+        Level<R>* dl = d + (size_t)l * cap;
+        if (l == 0) {
+            sweeps_fine(cur[0], p.nu0, s);
+            launch_apply<R>(dl, tiles[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
+        } else {
+            if (delta) launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
+            launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+            pseudo(l, cur[l], p.m, true, s);
+            launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
+        }
+        launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
+    }
+    if (L == 1) {
+        sweeps_fine(cur[0], p.nu0, s);
+    } else {
+        const int l = L - 1;
+        if (delta)
+            launch_apply<R>(d + (size_t)l * cap, tiles[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
+        launch_apply<R>(d + (size_t)l * cap, tiles[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+        pseudo(l, cur[l], p.mc, true, s);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        Level<R>* dl = d + (size_t)l * cap;
+        launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
+        if (l == 0) sweeps_fine(cur[0], p.nu0, s);
+        else pseudo(l, cur[l], p.m, false, s);
+    }
+    if (tail) {
+        launch_apply<R>(d, tiles[0].view(), ctl, APPLY_RESID, cur[0], part, 0, s, delta);
+        launch_finalize<R>(ctl, d, cap, part, nullptr, FIN_CYCLE, cur[0], bctl, s);
+    }
+    cur0 = cur[0];
+}
+
+template <typename R>
+long long Engine<R>::kernels_per_cycle(const Params& p) const
+{
+    if (L == 1) return p.nu0 + 2;
+    const int aw = delta ? 1 : 0;                      // A(w) of the base (correction form)
+    long long k = p.nu0 + 2;                           // fine pre-smooth, residual, restrict
+    k += (long long)(L - 2) * (p.m + 3 + aw);          // FAS rhs, pseudo, residual, restrict
+    k += 1 + p.mc + aw;                                // coarsest
+    k += (long long)(L - 2) * (1 + p.m) + 1 + p.nu0;   // prolong + post-smooth
+    return k + 2;                                      // final residual, finalize
+}
+
+template <typename R>
+m1_status Engine<R>::build_graph(const Params& p)
+{
+    if (graph && gparams == p && !graph_dirty) return M1_OK;
+    if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+    // a captured graph must return the fine iterate to buffer 0
+    const int per_cycle = L == 1 ? p.nu0 : 2 * p.nu0;
+    graph_cycles = (per_cycle % 2) ? 2 : 1;
+    cudaGraph_t g = nullptr;
+    M1_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    int cur0 = 0;
+    for (int c = 0; c < graph_cycles; ++c) record_cycle(p, cur0, cap_stream);
+    cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
+    if (e != cudaSuccess) { set_err(e, "cudaStreamEndCapture"); return M1_ERR_CUDA; }
+    if (cur0 != 0) { cudaGraphDestroy(g); return M1_ERR_INVALID_ARG; }
+    e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { set_err(e, "cudaGraphInstantiate"); graph = nullptr; return M1_ERR_CUDA; }
+    gparams = p;
+    graph_dirty = false;
+    return M1_OK;
+}
+
+// Control blocks of the used slots for a step (all used slots take part) and the
+// batch completion counter.
+template <typename R>
+m1_status Engine<R>::begin_step(const double* dts, const m1_solve_params& sp)
+{
+    int nact = 0;
+    for (int i = 0; i < cap; ++i) {
+        if (!used[i]) { ctl_h[i] = Ctl{}; continue; }
+        M1_TRY(set_dt(i, dts[i]));
+        ctl_h[i] = make_ctl(sp, (double)h[i].diag);
+        if (hist_len > 0) {
+            ctl_h[i].hist_len = hist_len;
+            ctl_h[i].hist = hist + (size_t)i * hist_len;
+            ctl_h[i].dtau_hist = dtau_hist + (size_t)i * hist_len;
+        }
+        ++nact;
+    }
+    *bctl_h = BatchCtl{ 0, nact, 0, 0 };
+    M1_CK(cudaMemcpyAsync(ctl, ctl_h, sizeof(Ctl) * cap, cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaMemcpyAsync(bctl, bctl_h, sizeof(BatchCtl), cudaMemcpyHostToDevice, stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::step(const double* dts, const m1_solve_params& sp, m1_step_stats* st)
+{
+    M1_TRY(validate_params(sp));
+    for (int i = 0; i < cap; ++i)
+        if (used[i] && !(dts[i] > 0)) return M1_ERR_INVALID_ARG;
+    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
+    M1_TRY(build_graph(p));
+    M1_TRY(begin_step(dts, sp));
+    M1_CK(cudaEventRecord(ev0, stream));
+    const WorkList t0 = tiles[0].view(), c0 = chunks[0].view();
+    launch_make_rhs<R>(d, c0, ctl, 0, stream);
+    launch_apply<R>(d, t0, ctl, APPLY_RESID, 0, part, 0, stream);
+    launch_norm_state<R>(d, t0, ctl, partb, stream);
+    launch_finalize<R>(ctl, d, cap, part, partb, FIN_INIT, 0, bctl, stream);
+    M1_CK(cudaGetLastError());
+    for (int i = 0; i < cap; ++i)
+        if (used[i]) { dt_rhs[i] = dts[i]; rhs_valid[i] = 1; }
+    long long launched = 0;
+    M1_TRY(run_until_done(graph, graph_cycles, sp.max_cycles, stream, bctl, done_h, poll, &launched));
+    M1_CK(cudaMemcpyAsync(ctl_h, ctl, sizeof(Ctl) * cap, cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < cap; ++i)
+        if (used[i] && ctl_h[i].result_buf == 1)
+            M1_CK(cudaMemcpyAsync(h[i].u[0], h[i].u[1], sizeof(Cell4<R>) * h[i].n,
+                                  cudaMemcpyDeviceToDevice, stream));
+    M1_CK(cudaEventRecord(ev1, stream));
+    M1_CK(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    bool all_ok = true;
+    int k = 0;
+    for (int i = 0; i < cap; ++i) {
+        if (!used[i]) continue;
+        const Ctl& c = ctl_h[i];
+        last_cycles[i] = c.kappa;
+        all_ok = all_ok && c.status == CTL_OK;
+        if (st) {
+            m1_step_stats& s = st[k];
+            s.cycles = c.kappa;
+            s.res0 = c.res0;
+            s.res = c.kappa > 0 ? c.res : c.res0;
+            s.dtau_final = c.dtau;
+            s.sweeps = (long long)c.kappa * (L == 1 ? p.nu0 : 2 * p.nu0);
+            s.ms = ms;
+            s.status = c.status;
+            s.newton_fail = c.newton_fail;
+            s.damped = c.damped;
+            s.launches = 4 + launched * kernels_per_cycle(p);
+        }
+        ++k;
+    }
+    return all_ok ? M1_OK : M1_ERR_NOT_CONVERGED;
+}
+
+template <typename R>
+m1_status Engine<R>::residual_norm(int i, double dt, double* out)
+{
+    if (i < 0 || i >= cap || !used[i] || !out || !(dt > 0)) return M1_ERR_INVALID_ARG;
+    M1_TRY(set_dt(i, dt));
+    init_tiles.host.clear();
+    init_chunks.host.clear();
+    for (int t = 0; t < h[i].tiles; ++t) init_tiles.host.push_back(make_int2(i, t));
+    for (int c = 0; c < h[i].chunks; ++c) init_chunks.host.push_back(make_int2(i, c));
+    M1_TRY(upload_list(init_tiles));
+    M1_TRY(upload_list(init_chunks));
+    if (!(rhs_valid[i] && dt == dt_rhs[i]))
+        launch_make_rhs<R>(d, init_chunks.view(), nullptr, 0, stream);
+    launch_apply<R>(d, init_tiles.view(), nullptr, APPLY_RESID, 0, part, 0, stream);
+    M1_CK(cudaGetLastError());
+    std::vector<double> p(h[i].tiles);
+    M1_CK(cudaMemcpyAsync(p.data(), part + h[i].part_off, sizeof(double) * p.size(),
+                          cudaMemcpyDeviceToHost, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    double s = 0.0;
+    for (double x : p) s += x;
+    *out = std::sqrt(s);
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::history(int i, double* hs, double* dt, int len)
+{
+    if (i < 0 || i >= cap || !used[i]) return M1_ERR_INVALID_ARG;
+    const int n = std::min(len, std::min(last_cycles[i] + 1, hist_len));
+    if (n <= 0) return M1_OK;
+    if (hs) M1_CK(cudaMemcpy(hs, hist + (size_t)i * hist_len, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (dt && n > 1)
+        M1_CK(cudaMemcpy(dt, dtau_hist + (size_t)i * hist_len, sizeof(double) * (n - 1),
+                         cudaMemcpyDeviceToHost));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::set_ctl_simple(int i, double dtau, double theta_ex, double theta_c)
+{
+    Ctl c{};
+    c.dtau = dtau; c.theta_ex = theta_ex; c.theta_c = theta_c; c.active = 1;
+    ctl_h[i] = c;
+    M1_CK(cudaMemcpyAsync(ctl + i, ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::jacobi(int i, double dt, int sweeps)
+{
+    if (cap != 1 || i != 0 || !used[0] || !(dt > 0) || sweeps < 0) return M1_ERR_INVALID_ARG;
+    M1_TRY(set_dt(0, dt));
+    M1_TRY(set_ctl_simple(0, 0.0, 0.5, 0.5));
+    launch_make_rhs<R>(d, chunks[0].view(), ctl, 0, stream);
+    int cur = 0;
+    sweeps_fine(cur, sweeps, stream);
+    M1_CK(cudaGetLastError());
+    if (cur == 1)
+        M1_CK(cudaMemcpyAsync(h[0].u[0], h[0].u[1], sizeof(Cell4<R>) * h[0].n,
+                              cudaMemcpyDeviceToDevice, stream));
+    dt_rhs[0] = dt;
+    rhs_valid[0] = 1;
+    return M1_OK;
+}
+
+// ---- single-kernel checks (slot 0) -----------------------------------------------
+template <typename R>
+m1_status Engine<R>::pack_planar(Cell4<R>* dst, int n, const double* planar)
+{
+    M1_CK(cudaMemcpyAsync(stage, planar, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, stream));
+    launch_pack_state<R>(stage, stage + n, stage + 2 * (size_t)n, stage + 3 * (size_t)n, 1.0, dst, n,
+                         stream);
+    M1_CK(cudaGetLastError());
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::unpack_planar(const Cell4<R>* src, int n, double* planar)
+{
+    return unpack_from(src, n, planar, planar + n, planar + 2 * (size_t)n, planar + 3 * (size_t)n, 0);
+}
+
+template <typename R>
+m1_status Engine<R>::op_level(double dt, const double* sig, const double* state, const double* rhs,
+                              int mode, double dtau, double theta, double* out, double* norm)
+{
+    const Level<R>& q = h[0];
+    const int n = q.n;
+    M1_TRY(set_dt(0, dt));
+    M1_CK(cudaMemcpyAsync(stage + 4 * (size_t)n, sig, sizeof(double) * 2 * n, cudaMemcpyHostToDevice,
+                          stream));
+    launch_pack_sig<R>(stage + 4 * (size_t)n, stage + 5 * (size_t)n, q.sig, n, stream);
+    M1_TRY(set_ctl_simple(0, dtau, theta, 0.5));
+    const WorkList t0 = tiles[0].view();
+    switch (mode) {
+    case M1_OP_APPLY:
+        M1_TRY(pack_planar(q.u[0], n, state));
+        launch_apply<R>(d, t0, ctl, APPLY_A, 0, nullptr, 0, stream);
+        M1_CK(cudaGetLastError());
+        return unpack_planar(q.r, n, out);
+    case M1_OP_RESIDUAL: {
+        M1_TRY(pack_planar(q.u[0], n, state));
+        M1_TRY(pack_planar(q.f, n, rhs));
+        launch_apply<R>(d, t0, ctl, APPLY_RESID, 0, part, 1, stream);
+        M1_CK(cudaGetLastError());
+        M1_TRY(unpack_planar(q.r, n, out));
+        if (norm) {
+            std::vector<double> p(q.tiles);
+            M1_CK(cudaMemcpy(p.data(), part, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
+            double s = 0.0;
+            for (double x : p) s += x;
+            *norm = std::sqrt(s);
+        }
+        return M1_OK;
+    }
+    case M1_OP_FAS_RHS:
+        M1_TRY(pack_planar(q.v, n, state));
+        M1_TRY(pack_planar(q.r, n, rhs));
+        launch_apply<R>(d, t0, ctl, APPLY_FAS, -1, nullptr, 0, stream);
+        M1_CK(cudaGetLastError());
+        return unpack_planar(q.f, n, out);
+    case M1_OP_JACOBI:
+    case M1_OP_PSEUDO:
+        M1_TRY(pack_planar(q.u[0], n, state));
+        M1_TRY(pack_planar(q.f, n, rhs));
+        launch_sweep<R>(d, t0, ctl, mode == M1_OP_PSEUDO, 0, 1, stream);
+        M1_CK(cudaGetLastError());
+        return unpack_planar(q.u[1], n, out);
+    default:
+        return M1_ERR_INVALID_ARG;
+    }
+}
+
+template <typename R>
+m1_status Engine<R>::op_restrict(const double* state, const double* resid, double* cs, double* cr)
+{
+    M1_TRY(set_ctl_simple(0, 0, 0.5, 0.5));
+    M1_TRY(pack_planar(h[0].u[0], h[0].n, state));
+    M1_TRY(pack_planar(h[0].r, h[0].n, resid));
+    launch_restrict<R>(d, d + cap, chunks[1].view(), ctl, 0, stream);
+    M1_CK(cudaGetLastError());
+    M1_TRY(unpack_planar(h[cap].v, h[cap].n, cs));
+    return unpack_planar(h[cap].r, h[cap].n, cr);
+}
+
+template <typename R>
+m1_status Engine<R>::op_prolong(const double* uc, const double* vc, const double* uf, double theta,
+                                double* out, int* damped)
+{
+    M1_TRY(set_ctl_simple(0, 0, 0.5, theta));
+    M1_TRY(pack_planar(h[cap].u[0], h[cap].n, uc));
+    M1_TRY(pack_planar(h[cap].v, h[cap].n, vc));
+    M1_TRY(pack_planar(h[0].u[0], h[0].n, uf));
+    launch_prolong<R>(d + cap, d, chunks[0].view(), ctl, 0, 0, stream);
+    M1_CK(cudaGetLastError());
+    M1_TRY(unpack_planar(h[0].u[0], h[0].n, out));
+    if (damped) {
+        M1_CK(cudaMemcpy(ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        *damped = (int)ctl_h[0].damped;
+    }
+    return M1_OK;
+}
+
+template struct Engine<double>;
+template struct Engine<float>;
+
+// ---------------------------------------------------------------------------
+m1_status PlainModel::create(const std::vector<m1_grid_desc>& descs, cudaStream_t s)
+{
+    const int L = descs[0].lmax;
+    M1_TRY(e.init((int)descs.size(), L, false, s, descs.size() == 1 ? 20001 : 0));
+    for (const auto& d : descs) {
+        int slot;
+        M1_TRY(e.add_slot(d, &slot));
+    }
+    return e.rebuild();
+}
+
+m1_status MixedModel::create(const std::vector<m1_grid_desc>& descs, cudaStream_t s)
+{
+    const int L = descs[0].lmax;
+    const int n = (int)descs.size();
+    M1_TRY(hi.init(n, 1, false, s, n == 1 ? 20001 : 0));
+    M1_TRY(lo.init(n, L, true, hi.stream, 0));
+    for (const auto& d : descs) {
+        m1_grid_desc g = d;
+        g.lmax = 1;
+        g.precision = M1_FP64;
+        int a, b;
+        M1_TRY(hi.add_slot(g, &a));
+        M1_TRY(lo.add_slot(d, &b));
+    }
+    M1_TRY(hi.rebuild());
+    M1_TRY(lo.rebuild());
+    lo.ctl = hi.ctl;   // the FP32 cycle reads the FP64 level's control blocks
+    return M1_OK;
+}
+
+m1_status MixedModel::set_state(int i, const double* E, const double* Fx, const double* Fy,
+                                const double* T, const double* sa, const double* ss, int dev)
+{
+    M1_TRY(hi.set_state(i, E, Fx, Fy, T, sa, ss, dev));
+    return lo.set_state(i, E, Fx, Fy, T, sa, ss, dev);
+}
+
+m1_status MixedModel::set_inflow(int i, int side, const double* E, const double* Fx,
+                                 const double* Fy)
+{
+    M1_TRY(hi.set_inflow(i, side, E, Fx, Fy));
+    return lo.set_inflow(i, side, E, Fx, Fy);
+}
+
+// FP32 V-cycle in correction form, FP64 accumulation of its correction, FP64
+// defect of the new iterate with the FP32 source of the next cycle, stop test.
+void MixedModel::record_cycle(const Params& p, cudaStream_t s)
+{
+    int cur0 = 0;
+    lo.record_cycle(p, cur0, s, false);
+    launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s);
+    launch_defect(hi.d, lo.d, hi.tiles[0].view(), hi.ctl, hi.part, s);
+    launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, nullptr, FIN_CYCLE, 0, hi.bctl, s);
+}
+
+m1_status MixedModel::build_graph(const Params& p)
+{
+    if (graph && gparams == p && !hi.graph_dirty && !lo.graph_dirty) return M1_OK;
+    if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    M1_CK(cudaStreamBeginCapture(lo.cap_stream, cudaStreamCaptureModeThreadLocal));
+    record_cycle(p, lo.cap_stream);
+    cudaError_t e = cudaStreamEndCapture(lo.cap_stream, &g);
+    if (e != cudaSuccess) { set_err(e, "cudaStreamEndCapture"); return M1_ERR_CUDA; }
+    e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { set_err(e, "cudaGraphInstantiate"); graph = nullptr; return M1_ERR_CUDA; }
+    gparams = p;
+    hi.graph_dirty = lo.graph_dirty = false;
+    return M1_OK;
+}
+
+m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step_stats* st)
+{
+    M1_TRY(validate_params(sp));
+    for (int i = 0; i < hi.cap; ++i)
+        if (hi.used[i] && !(dts[i] > 0)) return M1_ERR_INVALID_ARG;
+    for (int i = 0; i < lo.cap; ++i)
+        if (lo.used[i]) M1_TRY(lo.set_dt(i, dts[i]));
+    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
+    M1_TRY(build_graph(p));
+    M1_TRY(hi.begin_step(dts, sp));
+    cudaStream_t s = hi.stream;
+    M1_CK(cudaEventRecord(hi.ev0, s));
+    const WorkList t0 = hi.tiles[0].view(), c0 = hi.chunks[0].view();
+    launch_make_rhs<double>(hi.d, c0, hi.ctl, 0, s);
+    launch_norm_state<double>(hi.d, t0, hi.ctl, hi.partb, s);
+    launch_defect(hi.d, lo.d, t0, hi.ctl, hi.part, s);
+    launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, hi.partb, FIN_INIT, 0, hi.bctl, s);
+    M1_CK(cudaGetLastError());
+    for (int i = 0; i < hi.cap; ++i)
+        if (hi.used[i]) { hi.dt_rhs[i] = dts[i]; hi.rhs_valid[i] = 1; }
+    long long launched = 0;
+    M1_TRY(run_until_done(graph, 1, sp.max_cycles, s, hi.bctl, hi.done_h, hi.poll, &launched));
+    M1_CK(cudaMemcpyAsync(hi.ctl_h, hi.ctl, sizeof(Ctl) * hi.cap, cudaMemcpyDeviceToHost, s));
+    M1_CK(cudaEventRecord(hi.ev1, s));
+    M1_CK(cudaEventSynchronize(hi.ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, hi.ev0, hi.ev1);
+    bool all_ok = true;
+    int k = 0;
+    for (int i = 0; i < hi.cap; ++i) {
+        if (!hi.used[i]) continue;
+        const Ctl& c = hi.ctl_h[i];
+        hi.last_cycles[i] = c.kappa;
+        all_ok = all_ok && c.status == CTL_OK;
+        if (st) {
+            m1_step_stats& o = st[k];
+            o.cycles = c.kappa;
+            o.res0 = c.res0;
+            o.res = c.kappa > 0 ? c.res : c.res0;
+            o.dtau_final = c.dtau;
+            o.sweeps = (long long)c.kappa * (lo.L == 1 ? p.nu0 : 2 * p.nu0);
+            o.ms = ms;
+            o.status = c.status;
+            o.newton_fail = c.newton_fail;
+            o.damped = c.damped;
+            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 1);
+        }
+        ++k;
+    }
+    return all_ok ? M1_OK : M1_ERR_NOT_CONVERGED;
+}
+
+MixedModel::~MixedModel()
+{
+    if (graph) cudaGraphExecDestroy(graph);
+}
+
+m1_status make_model(const std::vector<m1_grid_desc>& descs, cudaStream_t s,
+                     std::unique_ptr<Model>& out)
+{
+    if (descs.empty()) return M1_ERR_INVALID_ARG;
+    for (const auto& d : descs) {
+        M1_TRY(validate_desc(&d));
+        if (d.lmax != descs[0].lmax || d.precision != descs[0].precision) return M1_ERR_INVALID_ARG;
+    }
+    if (descs[0].precision == M1_MIXED) {
+        std::unique_ptr<MixedModel> m(new MixedModel());
+        m1_status st = m->create(descs, s);
+        out = std::move(m);
+        return st;
+    }
+    std::unique_ptr<PlainModel> m(new PlainModel());
+    m1_status st = m->create(descs, s);
+    out = std::move(m);
+    return st;
+}
+
+template <typename R>
+m1_status make_op_engine(const m1_grid_desc* desc, int lmax, const double* inflow,
+                         std::unique_ptr<Engine<R>>& out)
+{
+    m1_grid_desc g = *desc;
+    g.lmax = lmax;
+    M1_TRY(validate_desc(&g));
+    out.reset(new Engine<R>());
+    M1_TRY(out->init(1, lmax, false, nullptr, 0));
+    int slot;
+    M1_TRY(out->add_slot(g, &slot));
+    M1_TRY(out->rebuild());
     if (inflow) {
-        const int Lp = std::max(d.nx, d.dim == 2 ? d.ny : 1);
+        const int Lp = std::max(g.nx, g.dim == 2 ? g.ny : 1);
         for (int w = 0; w < 4; ++w)
-            if (d.bc[w] == M1_BC_INFLOW)
-                M1_TRY(out->set_inflow(w, inflow + (size_t)(w * 3) * Lp, inflow + (size_t)(w * 3 + 1) * Lp,
+            if (g.bc[w] == M1_BC_INFLOW)
+                M1_TRY(out->set_inflow(0, w, inflow + (size_t)(w * 3) * Lp,
+                                       inflow + (size_t)(w * 3 + 1) * Lp,
                                        inflow + (size_t)(w * 3 + 2) * Lp));
     }
     return M1_OK;
 }
 
-}  // namespace
-
-namespace m1 {
-void set_error_text(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace m1
 
+using m1::Model;
+
 struct m1_grid {
-    std::unique_ptr<ImplBase> impl;
+    std::unique_ptr<Model> model;
+};
+
+struct m1_batch {
+    std::unique_ptr<Model> model;
+    int count = 0;
 };
 
 extern "C" {
 
-const char* m1_last_error(void) { return g_err; }
+const char* m1_last_error(void) { return m1::g_err; }
 
 m1_status m1_default_params(m1_solve_params* p)
 {
@@ -829,21 +1063,14 @@ m1_status m1_default_params(m1_solve_params* p)
 
 m1_status m1_create_grid(const m1_grid_desc* desc, void* cuda_stream, m1_grid_t* out)
 {
-    if (!out) return M1_ERR_INVALID_ARG;
+    if (!out || !desc) return M1_ERR_INVALID_ARG;
     *out = nullptr;
-    M1_TRY(validate(desc));
+    M1_TRY(m1::validate_desc(desc));
+    std::unique_ptr<Model> model;
+    m1_status s = m1::make_model({ *desc }, static_cast<cudaStream_t>(cuda_stream), model);
+    if (s != M1_OK) return s;
     m1_grid* g = new m1_grid;
-    m1_status s;
-    if (desc->precision == M1_MIXED) {
-        std::unique_ptr<MixedImpl> impl(new MixedImpl());
-        s = impl->init(*desc, static_cast<cudaStream_t>(cuda_stream));
-        g->impl = std::move(impl);
-    } else {
-        std::unique_ptr<Impl<double>> impl(new Impl<double>());
-        s = impl->init(*desc, static_cast<cudaStream_t>(cuda_stream));
-        g->impl = std::move(impl);
-    }
-    if (s != M1_OK) { delete g; return s; }
+    g->model = std::move(model);
     *out = g;
     return M1_OK;
 }
@@ -859,19 +1086,19 @@ m1_status m1_set_state(m1_grid_t g, const double* E, const double* Fx, const dou
                        const double* T, const double* sig_a, const double* sig_s, int on_device)
 {
     if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->set_state(E, Fx, Fy, T, sig_a, sig_s, on_device);
+    return g->model->set_state(0, E, Fx, Fy, T, sig_a, sig_s, on_device);
 }
 
 m1_status m1_set_inflow(m1_grid_t g, int side, const double* E, const double* Fx, const double* Fy)
 {
     if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->set_inflow(side, E, Fx, Fy);
+    return g->model->set_inflow(0, side, E, Fx, Fy);
 }
 
 m1_status m1_get_state(m1_grid_t g, double* E, double* Fx, double* Fy, double* T, int on_device)
 {
     if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->get_state(E, Fx, Fy, T, on_device);
+    return g->model->get_state(0, E, Fx, Fy, T, on_device);
 }
 
 m1_status m1_implicit_step(m1_grid_t g, double dt, const m1_solve_params* params,
@@ -880,25 +1107,78 @@ m1_status m1_implicit_step(m1_grid_t g, double dt, const m1_solve_params* params
     if (!g) return M1_ERR_INVALID_ARG;
     m1_solve_params p;
     if (params) p = *params; else m1_default_params(&p);
-    return g->impl->step(dt, p, stats);
-}
-
-m1_status m1_residual_norm(m1_grid_t g, double dt, double* out)
-{
-    if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->residual_norm(dt, out);
+    return g->model->step(&dt, p, stats);
 }
 
 m1_status m1_jacobi(m1_grid_t g, double dt, int sweeps)
 {
     if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->jacobi(dt, sweeps);
+    return g->model->jacobi(0, dt, sweeps);
+}
+
+m1_status m1_residual_norm(m1_grid_t g, double dt, double* out)
+{
+    if (!g) return M1_ERR_INVALID_ARG;
+    return g->model->residual_norm(0, dt, out);
 }
 
 m1_status m1_step_history(m1_grid_t g, double* hist, double* dtau, int len)
 {
     if (!g) return M1_ERR_INVALID_ARG;
-    return g->impl->history(hist, dtau, len);
+    return g->model->history(0, hist, dtau, len);
+}
+
+m1_status m1_create_batch(const m1_grid_desc* descs, int count, void* cuda_stream, m1_batch_t* out)
+{
+    if (!out || !descs || count < 1) return M1_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<m1_grid_desc> v(descs, descs + count);
+    std::unique_ptr<Model> model;
+    m1_status s = m1::make_model(v, static_cast<cudaStream_t>(cuda_stream), model);
+    if (s != M1_OK) return s;
+    m1_batch* b = new m1_batch;
+    b->model = std::move(model);
+    b->count = count;
+    *out = b;
+    return M1_OK;
+}
+
+m1_status m1_destroy_batch(m1_batch_t b)
+{
+    if (!b) return M1_ERR_INVALID_ARG;
+    delete b;
+    return M1_OK;
+}
+
+m1_status m1_batch_set_state(m1_batch_t b, int index, const double* E, const double* Fx,
+                             const double* Fy, const double* T, const double* sig_a,
+                             const double* sig_s, int on_device)
+{
+    if (!b || index < 0 || index >= b->count) return M1_ERR_INVALID_ARG;
+    return b->model->set_state(index, E, Fx, Fy, T, sig_a, sig_s, on_device);
+}
+
+m1_status m1_batch_set_inflow(m1_batch_t b, int index, int side, const double* E, const double* Fx,
+                              const double* Fy)
+{
+    if (!b || index < 0 || index >= b->count) return M1_ERR_INVALID_ARG;
+    return b->model->set_inflow(index, side, E, Fx, Fy);
+}
+
+m1_status m1_batch_get_state(m1_batch_t b, int index, double* E, double* Fx, double* Fy, double* T,
+                             int on_device)
+{
+    if (!b || index < 0 || index >= b->count) return M1_ERR_INVALID_ARG;
+    return b->model->get_state(index, E, Fx, Fy, T, on_device);
+}
+
+m1_status m1_batch_implicit_step(m1_batch_t b, const double* dt, const m1_solve_params* params,
+                                 m1_step_stats* stats)
+{
+    if (!b || !dt) return M1_ERR_INVALID_ARG;
+    m1_solve_params p;
+    if (params) p = *params; else m1_default_params(&p);
+    return b->model->step(dt, p, stats);
 }
 
 m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt, const double* sig,
@@ -908,13 +1188,13 @@ m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt,
     if (!desc || !sig || !state || !out || !(dt > 0)) return M1_ERR_INVALID_ARG;
     if (mode != M1_OP_APPLY && !rhs) return M1_ERR_INVALID_ARG;
     if (desc->precision == M1_FP64) {
-        std::unique_ptr<Impl<double>> im;
-        M1_TRY(make_op_impl(desc, 1, inflow, im));
-        return im->op_level(dt, sig, state, rhs, mode, dtau, theta, out, norm);
+        std::unique_ptr<m1::Engine<double>> e;
+        M1_TRY(m1::make_op_engine(desc, 1, inflow, e));
+        return e->op_level(dt, sig, state, rhs, mode, dtau, theta, out, norm);
     }
-    std::unique_ptr<Impl<float>> im;
-    M1_TRY(make_op_impl(desc, 1, inflow, im));
-    return im->op_level(dt, sig, state, rhs, mode, dtau, theta, out, norm);
+    std::unique_ptr<m1::Engine<float>> e;
+    M1_TRY(m1::make_op_engine(desc, 1, inflow, e));
+    return e->op_level(dt, sig, state, rhs, mode, dtau, theta, out, norm);
 }
 
 m1_status m1_op_restrict(const m1_grid_desc* fine, const double* inflow, const double* state,
@@ -922,13 +1202,13 @@ m1_status m1_op_restrict(const m1_grid_desc* fine, const double* inflow, const d
 {
     if (!fine || !state || !resid || !coarse_state || !coarse_resid) return M1_ERR_INVALID_ARG;
     if (fine->precision == M1_FP64) {
-        std::unique_ptr<Impl<double>> im;
-        M1_TRY(make_op_impl(fine, 2, inflow, im));
-        return im->op_restrict(state, resid, coarse_state, coarse_resid);
+        std::unique_ptr<m1::Engine<double>> e;
+        M1_TRY(m1::make_op_engine(fine, 2, inflow, e));
+        return e->op_restrict(state, resid, coarse_state, coarse_resid);
     }
-    std::unique_ptr<Impl<float>> im;
-    M1_TRY(make_op_impl(fine, 2, inflow, im));
-    return im->op_restrict(state, resid, coarse_state, coarse_resid);
+    std::unique_ptr<m1::Engine<float>> e;
+    M1_TRY(m1::make_op_engine(fine, 2, inflow, e));
+    return e->op_restrict(state, resid, coarse_state, coarse_resid);
 }
 
 m1_status m1_op_prolong_correct(const m1_grid_desc* fine, const double* uc, const double* vc,
@@ -936,13 +1216,13 @@ m1_status m1_op_prolong_correct(const m1_grid_desc* fine, const double* uc, cons
 {
     if (!fine || !uc || !vc || !uf || !out) return M1_ERR_INVALID_ARG;
     if (fine->precision == M1_FP64) {
-        std::unique_ptr<Impl<double>> im;
-        M1_TRY(make_op_impl(fine, 2, nullptr, im));
-        return im->op_prolong(uc, vc, uf, theta, out, damped);
+        std::unique_ptr<m1::Engine<double>> e;
+        M1_TRY(m1::make_op_engine(fine, 2, nullptr, e));
+        return e->op_prolong(uc, vc, uf, theta, out, damped);
     }
-    std::unique_ptr<Impl<float>> im;
-    M1_TRY(make_op_impl(fine, 2, nullptr, im));
-    return im->op_prolong(uc, vc, uf, theta, out, damped);
+    std::unique_ptr<m1::Engine<float>> e;
+    M1_TRY(m1::make_op_engine(fine, 2, nullptr, e));
+    return e->op_prolong(uc, vc, uf, theta, out, damped);
 }
 
 }  // extern "C"

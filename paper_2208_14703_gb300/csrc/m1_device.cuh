@@ -38,6 +38,8 @@ struct Level {
     int dim, nx, ny, n;
     int bc[4];
     int tx, ty, tiles_x, tiles;   // tile shape and count
+    int chunks;                   // 256-cell chunks (cell-parallel kernels)
+    int part_off;                 // first norm partial of this instance (level 0)
     int prof_len;                 // stride of the inflow profile table
     R c, a_r, c_v;
     R ax, ay, bx, by;             // c dt / h and dt / (2 h) per axis (y: 0 in 1D)
@@ -49,6 +51,7 @@ struct Level {
     Cell4<R>* f;                  // right-hand side (b at level 0, FAS rhs above)
     Cell4<R>* r;                  // residual (restricted from below / computed here)
     Cell4<R>* w;                  // base state of the correction form (mixed path), else null
+    Cell4<R>* aw;                 // A(w) of the base state (correction form), else null
     Sig2<R>* sig;                 // opacities
     R* inflow;                    // [wall][E, Fx, Fy][prof_len] prescribed ghosts
 };
@@ -62,6 +65,7 @@ struct Ctl {
     double tol, grow, shrink, eps_i, eps_d, dtau0, dtau_min, dtau_max, theta_ex, theta_c;
     double res0_floor;            // stop at once if ||r_0|| <= res0_floor ||b||
     int max_cycles, hist_len;
+    int active;                   // the instance takes part in the batch
     // state
     double res0, res, res_prev, bnorm, dtau;
     int kappa, done, status, result_buf;
@@ -71,6 +75,24 @@ struct Ctl {
 };
 
 enum CtlStatus { CTL_OK = 0, CTL_NOT_CONVERGED = -4 };
+
+// Completion count of a batch: every instance that sets its `done` flag adds
+// one; `all_done` is set when the count reaches the number of active instances.
+struct BatchCtl {
+    int n_done, n_active, all_done, pad;
+};
+
+// A work list: items[0 .. *count) of (instance, tile or 256-cell chunk), read by
+// persistent kernels (a fixed grid striding over the items), so the list can
+// change between V-cycles without changing a captured graph.
+struct WorkList {
+    const int2* items;
+    const int* count;
+    int capacity;
+};
+
+// Blocks of a persistent launch: 4 resident CTAs on each of the 152 SMs.
+constexpr int kPersistentBlocks = 152 * 4;
 
 // ---------------------------------------------------------------------------
 // Per-cell arithmetic.
@@ -291,7 +313,7 @@ __device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, 
         const R dh = C + R(4) * K * Tx * Tx * Tx;
         const R dx = h / dh;
         x -= dx;
-        if (fabs(dx) <= R(2e-7) * fabs(x) || dx == R(0)) { ok = true; break; }
+        if (fabs(dx) <= R(1e-6) * fabs(x) || dx == R(0)) { ok = true; break; }
     }
     o.T = x;
     o.E = (bE + k * a_r * quartic_delta(T, x)) * iAk;

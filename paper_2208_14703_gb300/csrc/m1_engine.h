@@ -1,0 +1,225 @@
+// Host-side engine of libm1 (definitions in m1_api.cu).
+//
+// Engine<R>: a fixed number of slots, each holding one instance's level
+// hierarchy (all instances share the level count L and the precision R; sizes,
+// dimension, walls and time steps are per instance).  Device descriptors are
+// laid out [level][slot]; work lists per level enumerate (slot, tile) and
+// (slot, 256-cell chunk) items of the used slots.  A single grid is an engine
+// with one slot, a batch an engine with one slot per instance; the server adds
+// and removes slots between V-cycles.
+#pragma once
+#include <m1.h>
+
+#include <memory>
+#include <vector>
+
+#include "m1_kernels.cuh"
+
+namespace m1 {
+
+void set_err(cudaError_t e, const char* what);
+void set_error_text(const char* msg);
+
+#define M1_CK(call)                                                                                \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            ::m1::set_err(e_, #call);                                                              \
+            return e_ == cudaErrorMemoryAllocation ? M1_ERR_OOM : M1_ERR_CUDA;                     \
+        }                                                                                          \
+    } while (0)
+
+#define M1_TRY(expr)                                                                               \
+    do {                                                                                           \
+        m1_status s_ = (expr);                                                                     \
+        if (s_ != M1_OK) return s_;                                                                \
+    } while (0)
+
+struct Params {
+    int nu0, nu_l, m, mc;
+    bool operator==(const Params& o) const
+    {
+        return nu0 == o.nu0 && nu_l == o.nu_l && m == o.m && mc == o.mc;
+    }
+};
+
+// A device work list and its host mirror.
+struct DevList {
+    int2* items = nullptr;
+    int* count = nullptr;
+    int capacity = 0;
+    int n = 0;
+    std::vector<int2> host;
+    WorkList view() const { return WorkList{ items, count, capacity }; }
+};
+
+m1_status validate_desc(const m1_grid_desc* d);
+m1_status validate_params(const m1_solve_params& sp);
+Ctl make_ctl(const m1_solve_params& sp, double diag0);
+m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles,
+                         cudaStream_t stream, BatchCtl* bctl, int* done_h, cudaEvent_t* poll,
+                         long long* launched_out);
+void restrict_profile(const double* fine, int nf, double* coarse, int nc);
+
+template <typename R>
+struct Engine {
+    int cap = 0, L = 0;
+    bool delta = false;                     // correction form (mixed path's FP32 hierarchy)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<m1_grid_desc> desc;         // per slot
+    std::vector<char> used;
+    std::vector<std::vector<void*>> mem;    // per-slot device allocations
+    std::vector<void*> common;              // engine-wide device allocations
+    std::vector<Level<R>> h;                // host descriptors [level * cap + slot]
+    Level<R>* d = nullptr;                  // device descriptors
+    std::vector<std::vector<double>> prof;  // inflow profiles [level * cap + slot]
+    std::vector<DevList> tiles, chunks;     // work lists per level
+    DevList init_tiles, init_chunks;        // scratch lists for one slot
+    int* init_slots = nullptr;
+    Ctl* ctl = nullptr;                     // device control blocks [cap]
+    Ctl* ctl_h = nullptr;                   // pinned mirror
+    BatchCtl* bctl = nullptr;
+    BatchCtl* bctl_h = nullptr;
+    int* done_h = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t poll[2] = { nullptr, nullptr };
+    double* hist = nullptr;
+    double* dtau_hist = nullptr;
+    int hist_len = 0;
+    double* part = nullptr;                 // per-tile norm partials (level 0, all slots)
+    double* partb = nullptr;
+    int part_cap = 0;
+    double* stage = nullptr;                // planar FP64 staging, 6 * stage_n
+    size_t stage_n = 0;
+    Sig2<R>* sig_stage = nullptr;
+    unsigned int* bad = nullptr;
+    unsigned int* bad_h = nullptr;
+    std::vector<double> dt_set, dt_rhs;
+    std::vector<char> rhs_valid;
+    std::vector<int> last_cycles;
+    cudaGraphExec_t graph = nullptr;
+    Params gparams{};
+    int graph_cycles = 1;
+    bool graph_dirty = true;
+
+    ~Engine();
+    std::vector<DevList*> all_lists();
+    m1_status calloc_common(void** p, size_t bytes);
+    m1_status slot_alloc(int i, void** p, size_t bytes);
+    m1_status init(int capacity, int levels, bool correction_form, cudaStream_t s, int history_len);
+    m1_status add_slot(const m1_grid_desc& dsc, int* out);
+    m1_status remove_slot(int i);
+    m1_status ensure_stage(size_t n);
+    m1_status upload_list(DevList& l);
+    m1_status rebuild();
+    m1_status set_dt(int i, double dt);
+    m1_status pack_into(int i, Cell4<R>* dst, const double* E, const double* Fx, const double* Fy,
+                        const double* T, int dev);
+    m1_status unpack_from(const Cell4<R>* src, int n, double* E, double* Fx, double* Fy, double* T,
+                          int dev);
+    m1_status set_state(int i, const double* E, const double* Fx, const double* Fy, const double* T,
+                        const double* sa, const double* ss, int dev);
+    m1_status set_inflow(int i, int side, const double* E, const double* Fx, const double* Fy);
+    m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev);
+    void sweeps_fine(int& cur, int count, cudaStream_t s);
+    void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s);
+    void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true);
+    long long kernels_per_cycle(const Params& p) const;
+    m1_status build_graph(const Params& p);
+    m1_status begin_step(const double* dts, const m1_solve_params& sp);
+    m1_status step(const double* dts, const m1_solve_params& sp, m1_step_stats* st);
+    m1_status residual_norm(int i, double dt, double* out);
+    m1_status history(int i, double* hs, double* dt, int len);
+    m1_status set_ctl_simple(int i, double dtau, double theta_ex, double theta_c);
+    m1_status jacobi(int i, double dt, int sweeps);
+    m1_status pack_planar(Cell4<R>* dst, int n, const double* planar);
+    m1_status unpack_planar(const Cell4<R>* src, int n, double* planar);
+    m1_status op_level(double dt, const double* sig, const double* state, const double* rhs,
+                       int mode, double dtau, double theta, double* out, double* norm);
+    m1_status op_restrict(const double* state, const double* resid, double* cs, double* cr);
+    m1_status op_prolong(const double* uc, const double* vc, const double* uf, double theta,
+                         double* out, int* damped);
+};
+
+// One or more instances behind the C ABI: the plain FP64 engine, or the mixed
+// pair (FP64 fine level + FP32 correction-form hierarchy).
+struct Model {
+    virtual ~Model() = default;
+    virtual m1_status set_state(int i, const double* E, const double* Fx, const double* Fy,
+                                const double* T, const double* sa, const double* ss, int dev) = 0;
+    virtual m1_status set_inflow(int i, int side, const double* E, const double* Fx,
+                                 const double* Fy) = 0;
+    virtual m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev) = 0;
+    virtual m1_status step(const double* dts, const m1_solve_params& p, m1_step_stats* st) = 0;
+    virtual m1_status residual_norm(int i, double dt, double* out) = 0;
+    virtual m1_status history(int i, double* hist, double* dtau, int len) = 0;
+    virtual m1_status jacobi(int i, double dt, int sweeps) = 0;
+};
+
+struct PlainModel : Model {
+    Engine<double> e;
+    m1_status create(const std::vector<m1_grid_desc>& descs, cudaStream_t s);
+    m1_status set_state(int i, const double* E, const double* Fx, const double* Fy, const double* T,
+                        const double* sa, const double* ss, int dev) override
+    {
+        return e.set_state(i, E, Fx, Fy, T, sa, ss, dev);
+    }
+    m1_status set_inflow(int i, int side, const double* E, const double* Fx,
+                         const double* Fy) override
+    {
+        return e.set_inflow(i, side, E, Fx, Fy);
+    }
+    m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev) override
+    {
+        return e.get_state(i, E, Fx, Fy, T, dev);
+    }
+    m1_status step(const double* dts, const m1_solve_params& p, m1_step_stats* st) override
+    {
+        return e.step(dts, p, st);
+    }
+    m1_status residual_norm(int i, double dt, double* out) override
+    {
+        return e.residual_norm(i, dt, out);
+    }
+    m1_status history(int i, double* hs, double* dt, int len) override
+    {
+        return e.history(i, hs, dt, len);
+    }
+    m1_status jacobi(int i, double dt, int sweeps) override { return e.jacobi(i, dt, sweeps); }
+};
+
+struct MixedModel : Model {
+    Engine<double> hi;   // FP64 fine level: v^n, b, opacities, residual, norms, accumulation
+    Engine<float> lo;    // FP32 hierarchy in correction form
+    cudaGraphExec_t graph = nullptr;
+    Params gparams{};
+    ~MixedModel() override;
+    m1_status create(const std::vector<m1_grid_desc>& descs, cudaStream_t s);
+    m1_status set_state(int i, const double* E, const double* Fx, const double* Fy, const double* T,
+                        const double* sa, const double* ss, int dev) override;
+    m1_status set_inflow(int i, int side, const double* E, const double* Fx,
+                         const double* Fy) override;
+    m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev) override
+    {
+        return hi.get_state(i, E, Fx, Fy, T, dev);
+    }
+    void record_cycle(const Params& p, cudaStream_t s);
+    m1_status build_graph(const Params& p);
+    m1_status step(const double* dts, const m1_solve_params& p, m1_step_stats* st) override;
+    m1_status residual_norm(int i, double dt, double* out) override
+    {
+        return hi.residual_norm(i, dt, out);
+    }
+    m1_status history(int i, double* hs, double* dt, int len) override
+    {
+        return hi.history(i, hs, dt, len);
+    }
+    m1_status jacobi(int, double, int) override { return M1_ERR_INVALID_ARG; }
+};
+
+m1_status make_model(const std::vector<m1_grid_desc>& descs, cudaStream_t s,
+                     std::unique_ptr<Model>& out);
+
+}  // namespace m1

@@ -9,10 +9,14 @@
 //   k_prolong   prolongation of the coarse correction (Eq. (14)/(18)) with the
 //               per-cell damping of Eq. (34)
 //   k_finalize  deterministic norm reduction, cycle counter, stop test and the
-//               adaptive implicit pseudo-time step (Algorithm 4)
+//               adaptive implicit pseudo-time step (Algorithm 4), per instance
+//   k_defect, k_accumulate   FP64 ends of the mixed-precision cycle
 //
-// The stencil kernels stage a tile plus a one-cell halo in shared memory and
-// evaluate each cell's closure once per pass; neighbours read it from there.
+// Every kernel walks a work list of (instance, tile) or (instance, 256-cell
+// chunk) items with a fixed persistent grid, so one launch serves every
+// instance of a batch at one level; an instance whose control block says done
+// skips its items.  The stencil kernels stage a tile plus a one-cell halo in
+// shared memory and evaluate each cell's closure once per pass.
 #include <type_traits>
 
 #include "m1_kernels.cuh"
@@ -90,67 +94,102 @@ __device__ __forceinline__ void tile_origin(const Level<R>& L, int tile, int& x0
     y0 = (tile / L.tiles_x) * L.ty;
 }
 
-// ---------------------------------------------------------------------------
-template <typename R, bool PSEUDO, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__ Lp, int in_buf,
-                                                    int out_buf, Ctl* __restrict__ ctl)
+// The explicit pseudo-time step length min(dtau, theta tau*) of Algorithm 3
+// (tau* = the largest admissible step from u along f).  The admissible set is
+// convex, so when u + (dtau / theta) f is admissible tau* >= dtau / theta and
+// the step is dtau: the divisions and the square root of tau* are needed only
+// in cells where the bound may bind.
+template <typename R>
+__device__ __forceinline__ R limited_step(const Cell4<R>& u, const Cell4<R>& f, R dtau, R theta,
+                                          R c)
 {
-    if (ctl->done) return;
-    __shared__ Level<R> L;
-    __shared__ Tile<R> t;
-    load_level(L, Lp);
-    __syncthreads();
-    int x0, y0;
-    tile_origin(L, blockIdx.x, x0, y0);
-    const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-    load_tile<R, DELTA>(L, src, x0, y0, t);
-    __syncthreads();
-    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-    const int i = x0 + lx, j = y0 + ly;
-    if (i >= L.nx || j >= L.ny) return;
-    const size_t k = (size_t)j * L.nx + i;
-    const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
-    R NE, NFx, NFy;
-    neighbour_sum(L, t, ck, NE, NFx, NFy);
-    const Cell4<R> b = L.f[k];
-    const Sig2<R> sg = L.sig[k];
-    const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-    bool ok;
-    Cell4<R> out;
-    if (!PSEUDO) {
-        if (!DELTA)
-            out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE, b.Fx + NFx,
-                                 b.Fy + NFy, b.T, ok);
-        else
-            out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, L.w[k].T,
-                                       b.E + NE, b.Fx + NFx, b.Fy + NFy, b.T, ok);
-    } else {
-        // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*) (tau* = the
-        // largest admissible step along f); implicit half: one Jacobi sweep of
-        // u + dtau A(u) = u~ from the old iterate.  DELTA: u = w + e, and the
-        // sweep updates the correction e (u~ - w = e + tau f).
-        const R dtau = (R)ctl->dtau;
-        const Cell4<R> u = src[k];
-        if (!DELTA) {
-            R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(u, b, L.c));
-            out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
-                                 u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
-                                 u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
-        } else {
-            const Cell4<R> w = L.w[k];
-            const Cell4<R> full = { w.E + u.E, w.Fx + u.Fx, w.Fy + u.Fy, w.T + u.T };
-            R tau = fmin(dtau, (R)ctl->theta_ex * max_admissible_step(full, b, L.c));
-            out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, w.T,
-                                       u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
-                                       u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
-        }
-    }
-    if (!ok) atomicAdd(&ctl->newton_fail, 1u);
-    L.u[out_buf][k] = out;
+    const R s = dtau / theta;
+    const Cell4<R> p = { u.E + s * f.E, u.Fx + s * f.Fx, u.Fy + s * f.Fy, u.T + s * f.T };
+    if (p.E > R(0) && p.T > R(0) && p.Fx * p.Fx + p.Fy * p.Fy <= c * c * p.E * p.E) return dtau;
+    return fmin(dtau, theta * max_admissible_step(u, f, c));
+}
+
+__device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
+{
+    return ctls && (ctls[inst].done || !ctls[inst].active);
 }
 
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool PSEUDO, bool DELTA = false>
+__global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__ lv, WorkList wl,
+                                                    Ctl* __restrict__ ctls, int in_buf, int out_buf)
+{
+    __shared__ Level<R> L;
+    __shared__ Tile<R> t;
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        Ctl* ctl = ctls + it.x;
+        load_level(L, lv + it.x);
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, it.y, x0, y0);
+        const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
+        load_tile<R, DELTA>(L, src, x0, y0, t);
+        __syncthreads();
+        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+        const int i = x0 + lx, j = y0 + ly;
+        if (i < L.nx && j < L.ny) {
+            const size_t k = (size_t)j * L.nx + i;
+            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+            R NE, NFx, NFy;
+            neighbour_sum(L, t, ck, NE, NFx, NFy);
+            const Cell4<R> b = L.f[k];
+            const Sig2<R> sg = L.sig[k];
+            const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+            bool ok;
+            Cell4<R> out;
+            if (!PSEUDO) {
+                if (!DELTA)
+                    out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE,
+                                         b.Fx + NFx, b.Fy + NFy, b.T, ok);
+                else
+                    out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, L.w[k].T,
+                                               b.E + NE, b.Fx + NFx, b.Fy + NFy, b.T, ok);
+            } else {
+                // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit
+                // half: one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
+                // DELTA: u = w + e and the sweep updates the correction e.
+                const R dtau = (R)ctl->dtau;
+                const R theta = (R)ctl->theta_ex;
+                const Cell4<R> u = src[k];
+                if (!DELTA) {
+                    const R tau = limited_step(u, b, dtau, theta, L.c);
+                    out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
+                                         u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
+                                         u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+                } else {
+                    // u = w + e and f = A(w) + g: the full-form step
+                    // u' + dtau A(u') = u + tau f reads, for the correction,
+                    // e' + dtau (A(w+e') - A(w)) = e + tau g + (tau - dtau) A(w);
+                    // the last term is zero wherever the step is not limited
+                    const Cell4<R> wb = L.w[k], aw = L.aw[k];
+                    const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
+                    const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
+                    const R tau = limited_step(full, ff, dtau, theta, L.c);
+                    const R lim = tau - dtau;
+                    out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
+                                               u.E + tau * b.E + lim * aw.E + dtau * NE,
+                                               u.Fx + tau * b.Fx + lim * aw.Fx + dtau * NFx,
+                                               u.Fy + tau * b.Fy + lim * aw.Fy + dtau * NFy,
+                                               u.T + tau * b.T + lim * aw.T, ok);
+                }
+            }
+            if (!ok) atomicAdd(&ctl->newton_fail, 1u);
+            L.u[out_buf][k] = out;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block sum of one double per thread (result valid in thread 0).
 __device__ __forceinline__ double block_sum(double v, double* red)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -164,221 +203,269 @@ __device__ __forceinline__ double block_sum(double v, double* red)
 }
 
 template <typename R, int MODE, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__ Lp, int state_buf,
-                                                    double* __restrict__ partials, int write_r,
-                                                    Ctl* __restrict__ ctl)
+__global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__ lv, WorkList wl,
+                                                    Ctl* __restrict__ ctls, int state_buf,
+                                                    double* __restrict__ partials, int write_r)
 {
-    if (ctl && ctl->done) return;
     __shared__ Level<R> L;
     __shared__ Tile<R> t;
     __shared__ double red[kThreads / 32];
-    load_level(L, Lp);
-    __syncthreads();
-    int x0, y0;
-    tile_origin(L, blockIdx.x, x0, y0);
-    const Cell4<R>* __restrict__ src = state_buf < 0 ? L.v : L.u[state_buf];
-    load_tile<R, DELTA>(L, src, x0, y0, t);
-    __syncthreads();
-    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-    const int i = x0 + lx, j = y0 + ly;
-    double nrm = 0.0;
-    if (i < L.nx && j < L.ny) {
-        const size_t k = (size_t)j * L.nx + i;
-        const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
-        R NE, NFx, NFy;
-        neighbour_sum(L, t, ck, NE, NFx, NFy);
-        const Cell4<R> u = src[k];
-        const Sig2<R> sg = L.sig[k];
-        const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-        R src_e;
-        if (!DELTA) {
-            const R T2 = u.T * u.T;
-            src_e = ka * (u.E - L.a_r * T2 * T2);
-        } else {
-            // A(w + e) - A(w): the source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
-            src_e = ka * (u.E - L.a_r * quartic_delta(L.w[k].T, u.T));
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        load_level(L, lv + it.x);
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, it.y, x0, y0);
+        // state_buf: 0/1 the iterate, -1 the restricted iterate v, -2 the base w
+        const Cell4<R>* __restrict__ src =
+            state_buf == -2 ? L.w : (state_buf < 0 ? L.v : L.u[state_buf]);
+        load_tile<R, DELTA>(L, src, x0, y0, t);
+        __syncthreads();
+        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+        const int i = x0 + lx, j = y0 + ly;
+        double nrm = 0.0;
+        if (i < L.nx && j < L.ny) {
+            const size_t k = (size_t)j * L.nx + i;
+            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+            R NE, NFx, NFy;
+            neighbour_sum(L, t, ck, NE, NFx, NFy);
+            const Cell4<R> u = src[k];
+            const Sig2<R> sg = L.sig[k];
+            const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+            R src_e;
+            if (!DELTA) {
+                const R T2 = u.T * u.T;
+                src_e = ka * (u.E - L.a_r * T2 * T2);
+            } else {
+                // A(w + e) - A(w): source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
+                src_e = ka * (u.E - L.a_r * quartic_delta(L.w[k].T, u.T));
+            }
+            Cell4<R> a;
+            a.E = L.diag * u.E + src_e - NE;
+            a.Fx = (L.diag + kt) * u.Fx - NFx;
+            a.Fy = (L.diag + kt) * u.Fy - NFy;
+            a.T = L.c_v * u.T - src_e;
+            if (MODE == APPLY_RESID) {
+                const Cell4<R> f = L.f[k];
+                Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
+                if (write_r) L.r[k] = r;
+                const double ic2 = 1.0 / ((double)L.c * (double)L.c);
+                nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
+                      (double)r.T * r.T;
+            } else if (MODE == APPLY_FAS) {
+                const Cell4<R> r = L.r[k];
+                Cell4<R> o = { a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
+                L.f[k] = o;
+            } else if (state_buf == -2) {
+                L.aw[k] = a;
+            } else {
+                L.r[k] = a;
+            }
         }
-        Cell4<R> a;
-        a.E = L.diag * u.E + src_e - NE;
-        a.Fx = (L.diag + kt) * u.Fx - NFx;
-        a.Fy = (L.diag + kt) * u.Fy - NFy;
-        a.T = L.c_v * u.T - src_e;
-        if (MODE == APPLY_RESID) {
-            const Cell4<R> f = L.f[k];
-            Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
-            if (write_r) L.r[k] = r;
-            const double ic2 = 1.0 / ((double)L.c * (double)L.c);
-            nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
-                  (double)r.T * r.T;
-        } else if (MODE == APPLY_FAS) {
-            const Cell4<R> r = L.r[k];
-            Cell4<R> o = { a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
-            L.f[k] = o;
-        } else {
-            L.r[k] = a;
+        if (MODE == APPLY_RESID && partials) {
+            double s = block_sum(nrm, red);
+            if (threadIdx.x == 0) partials[L.part_off + it.y] = s * L.vol;
         }
-    }
-    if (MODE == APPLY_RESID && partials) {
-        double s = block_sum<R>(nrm, red);
-        if (threadIdx.x == 0) partials[blockIdx.x] = s * L.vol;
+        __syncthreads();
     }
 }
 
-// Norm of a whole state (used for ||b||): per-tile partials.
+// Norm of the right-hand side f of each instance (for ||b||): per-tile partials.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restrict__ Lp,
-                                                         const Cell4<R>* __restrict__ s,
+__global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restrict__ lv,
+                                                         WorkList wl, const Ctl* __restrict__ ctls,
                                                          double* __restrict__ partials)
 {
     __shared__ Level<R> L;
     __shared__ double red[kThreads / 32];
-    load_level(L, Lp);
-    __syncthreads();
-    int x0, y0;
-    tile_origin(L, blockIdx.x, x0, y0);
-    const int i = x0 + threadIdx.x % L.tx, j = y0 + threadIdx.x / L.tx;
-    double nrm = 0.0;
-    if (i < L.nx && j < L.ny) {
-        const Cell4<R> r = s[(size_t)j * L.nx + i];
-        const double ic2 = 1.0 / ((double)L.c * (double)L.c);
-        nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
-              (double)r.T * r.T;
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (ctls && !ctls[it.x].active) continue;
+        load_level(L, lv + it.x);
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, it.y, x0, y0);
+        const int i = x0 + threadIdx.x % L.tx, j = y0 + threadIdx.x / L.tx;
+        double nrm = 0.0;
+        if (i < L.nx && j < L.ny) {
+            const Cell4<R> r = L.f[(size_t)j * L.nx + i];
+            const double ic2 = 1.0 / ((double)L.c * (double)L.c);
+            nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
+                  (double)r.T * r.T;
+        }
+        double sum = block_sum(nrm, red);
+        if (threadIdx.x == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncthreads();
     }
-    double sum = block_sum<R>(nrm, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum * L.vol;
 }
 
 // ---------------------------------------------------------------------------
 // Full weighting, coarse cell (ic, jc) <- fine cells 2ic-1..2ic+1 (x) and
-// 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis.
+// 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis.  Items are
+// (instance, 256-cell chunk of the coarse level).
 template <typename R, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restrict__ Lfp,
-                                                       const Level<R>* __restrict__ Lcp,
-                                                       int fine_buf, Ctl* __restrict__ ctl)
+__global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restrict__ lvf,
+                                                       const Level<R>* __restrict__ lvc,
+                                                       WorkList wl, Ctl* __restrict__ ctls,
+                                                       int fine_buf)
 {
-    if (ctl && ctl->done) return;
     __shared__ Level<R> Lf, Lc;
-    load_level(Lf, Lfp);
-    load_level(Lc, Lcp);
-    __syncthreads();
-    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kc >= Lc.n) return;
-    const int ic = kc % Lc.nx, jc = kc / Lc.nx;
-    const R w[3] = { R(0.25), R(0.5), R(0.25) };
-    const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
-    Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
-    const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
-    for (int b = b0; b <= b1; ++b) {
-        const R wy = Lf.dim == 2 ? w[b + 1] : R(1);
-        const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
-        for (int a = -1; a <= 1; ++a) {
-            const R wt = wy * w[a + 1];
-            // correction form: the correction has zero inflow ghosts, the base
-            // carries the prescribed state
-            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
-            const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
-            av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
-            ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
-            if (DELTA) {
-                const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
-                aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+    const int nw = *wl.count;
+    const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        load_level(Lf, lvf + it.x);
+        load_level(Lc, lvc + it.x);
+        __syncthreads();
+        const int kc = it.y * kThreads + threadIdx.x;
+        if (kc < Lc.n) {
+            const int ic = kc % Lc.nx, jc = kc / Lc.nx;
+            const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
+            Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
+            const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+            for (int b = b0; b <= b1; ++b) {
+                const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
+                const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+                for (int a = -1; a <= 1; ++a) {
+                    const R wt = wy * wgt[a + 1];
+                    // correction form: the correction has zero inflow ghosts, the base
+                    // carries the prescribed state
+                    const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
+                    const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
+                    av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
+                    ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+                    if (DELTA) {
+                        const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
+                        aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+                    }
+                }
             }
+            Lc.v[kc] = av;
+            Lc.r[kc] = ar;
+            if (DELTA) Lc.w[kc] = aw;
         }
+        __syncthreads();
     }
-    Lc.v[kc] = av;
-    Lc.r[kc] = ar;
-    if (DELTA) Lc.w[kc] = aw;
 }
 
 template <typename R>
-__global__ void k_restrict_sig(const Level<R>* __restrict__ Lfp, const Level<R>* __restrict__ Lcp)
+__global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>* __restrict__ lvc,
+                               WorkList wl)
 {
     __shared__ Level<R> Lf, Lc;
-    load_level(Lf, Lfp);
-    load_level(Lc, Lcp);
-    __syncthreads();
-    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kc >= Lc.n) return;
-    const int ic = kc % Lc.nx, jc = kc / Lc.nx;
-    const R w[3] = { R(0.25), R(0.5), R(0.25) };
-    Sig2<R> acc = { 0, 0 };
-    const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
-    for (int b = b0; b <= b1; ++b) {
-        const R wy = Lf.dim == 2 ? w[b + 1] : R(1);
-        const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
-        for (int a = -1; a <= 1; ++a) {
-            const Sig2<R> s = fetch_sig(Lf, Lf.sig, 2 * ic + a, jf);
-            acc.sa += wy * w[a + 1] * s.sa;
-            acc.ss += wy * w[a + 1] * s.ss;
+    const int nw = *wl.count;
+    const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        load_level(Lf, lvf + it.x);
+        load_level(Lc, lvc + it.x);
+        __syncthreads();
+        const int kc = it.y * kThreads + threadIdx.x;
+        if (kc < Lc.n) {
+            const int ic = kc % Lc.nx, jc = kc / Lc.nx;
+            Sig2<R> acc = { 0, 0 };
+            const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+            for (int b = b0; b <= b1; ++b) {
+                const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
+                const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+                for (int a = -1; a <= 1; ++a) {
+                    const Sig2<R> s = fetch_sig(Lf, Lf.sig, 2 * ic + a, jf);
+                    acc.sa += wy * wgt[a + 1] * s.sa;
+                    acc.ss += wy * wgt[a + 1] * s.ss;
+                }
+            }
+            Lc.sig[kc] = acc;
         }
+        __syncthreads();
     }
-    Lc.sig[kc] = acc;
 }
 
 // ---------------------------------------------------------------------------
 // u_l += P(u_{l+1} - v_{l+1}) per fine cell (fine 2i <- coarse i, fine 2i+1 <-
 // half of coarse i and i+1; tensor product in 2D); a target outside the
 // admissible set is replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).
+// Items are (instance, 256-cell chunk of the fine level).
 template <typename R, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ Lcp,
-                                                      const Level<R>* __restrict__ Lfp,
-                                                      int coarse_buf, int fine_buf,
-                                                      Ctl* __restrict__ ctl)
+__global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ lvc,
+                                                      const Level<R>* __restrict__ lvf,
+                                                      WorkList wl, Ctl* __restrict__ ctls,
+                                                      int coarse_buf, int fine_buf)
 {
-    if (ctl->done) return;
     __shared__ Level<R> Lf, Lc;
-    load_level(Lf, Lfp);
-    load_level(Lc, Lcp);
-    __syncthreads();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= Lf.n) return;
-    const int i = k % Lf.nx, j = k / Lf.nx;
-    const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
-    const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
-    const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
-    const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
-    Cell4<R> pe = { 0, 0, 0, 0 };
-    for (int b = 0; b <= oy; ++b)
-        for (int a = 0; a <= ox; ++a) {
-            const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
-            const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
-            pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
-            pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        Ctl* ctl = ctls + it.x;
+        load_level(Lf, lvf + it.x);
+        load_level(Lc, lvc + it.x);
+        __syncthreads();
+        const int k = it.y * kThreads + threadIdx.x;
+        if (k < Lf.n) {
+            const int i = k % Lf.nx, j = k / Lf.nx;
+            const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
+            const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
+            const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
+            const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
+            Cell4<R> pe = { 0, 0, 0, 0 };
+            for (int b = 0; b <= oy; ++b)
+                for (int a = 0; a <= ox; ++a) {
+                    const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
+                    const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
+                    pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
+                    pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
+                }
+            Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
+            const Cell4<R> e = uf[k];
+            Cell4<R> u = e;
+            if (DELTA) {   // correction form: the admissible set constrains w + e
+                const Cell4<R> wb = Lf.w[k];
+                u.E += wb.E; u.Fx += wb.Fx; u.Fy += wb.Fy; u.T += wb.T;
+            }
+            const Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
+            R th = R(1);
+            if (!admissible(tg, Lf.c)) {
+                th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
+                atomicAdd(&ctl->damped, 1u);
+            }
+            const Cell4<R> out = { e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy,
+                                   e.T + th * pe.T };
+            uf[k] = out;
         }
-    Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
-    const Cell4<R> e = uf[k];
-    Cell4<R> u = e;
-    if (DELTA) {   // correction form: the admissible set constrains w + e
-        const Cell4<R> w = Lf.w[k];
-        u.E += w.E; u.Fx += w.Fx; u.Fy += w.Fy; u.T += w.T;
+        __syncthreads();
     }
-    Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
-    R th = R(1);
-    if (!admissible(tg, Lf.c)) {
-        th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
-        atomicAdd(&ctl->damped, 1u);
-    }
-    const Cell4<R> out = { e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy, e.T + th * pe.T };
-    uf[k] = out;
 }
 
 // ---------------------------------------------------------------------------
 // b = (E^n, F^n, C_v T^n) of the iterate in buffer `buf` (Algorithm 4).
 template <typename R>
-__global__ void k_make_rhs(const Level<R>* __restrict__ Lp, int buf)
+__global__ void k_make_rhs(const Level<R>* __restrict__ lv, WorkList wl,
+                           const Ctl* __restrict__ ctls, int buf)
 {
     __shared__ Level<R> L;
-    load_level(L, Lp);
-    __syncthreads();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.n) return;
-    Cell4<R> s = L.u[buf][k];
-    s.T *= L.c_v;
-    L.f[k] = s;
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (ctls && !ctls[it.x].active) continue;
+        load_level(L, lv + it.x);
+        __syncthreads();
+        const int k = it.y * kThreads + threadIdx.x;
+        if (k < L.n) {
+            Cell4<R> s = L.u[buf][k];
+            s.T *= L.c_v;
+            L.f[k] = s;
+        }
+        __syncthreads();
+    }
 }
 
-// Deterministic reduction of per-tile partials (fixed order: thread t sums
-// entries t, t+256, ... then a fixed tree), then the control logic.
+// Deterministic reduction of one instance's per-tile partials (fixed order:
+// thread t sums entries t, t+256, ... then a fixed tree), then the control
+// logic of Algorithm 4 for that instance.  One block per instance slot.
 __device__ double block_reduce_fixed(const double* __restrict__ p, int n, double* red)
 {
     double s = 0.0;
@@ -394,16 +481,32 @@ __device__ double block_reduce_fixed(const double* __restrict__ p, int n, double
     return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctl,
-                                                       const double* __restrict__ part, int np,
-                                                       const double* __restrict__ partb, int npb,
-                                                       int mode, int cur)
+__device__ void mark_done(Ctl* ctl, BatchCtl* bctl, int status)
+{
+    ctl->done = 1;
+    ctl->status = status;
+    if (bctl) {
+        const int n = atomicAdd(&bctl->n_done, 1) + 1;
+        if (n >= bctl->n_active) bctl->all_done = 1;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
+                                                       const Level<R>* __restrict__ lv0,
+                                                       const double* __restrict__ part,
+                                                       const double* __restrict__ partb, int mode,
+                                                       int cur, BatchCtl* __restrict__ bctl)
 {
     __shared__ double red[kThreads];
+    Ctl* ctl = ctls + blockIdx.x;
+    if (!ctl->active) return;
     if (mode == FIN_CYCLE && ctl->done) return;
-    const double s = block_reduce_fixed(part, np, red);
+    const Level<R>* L = lv0 + blockIdx.x;
+    const int off = L->part_off, np = L->tiles;
+    const double s = block_reduce_fixed(part + off, np, red);
     double sb = 0.0;
-    if (mode == FIN_INIT) sb = block_reduce_fixed(partb, npb, red);
+    if (mode == FIN_INIT) sb = block_reduce_fixed(partb + off, np, red);
     if (threadIdx.x != 0) return;
     const double res = sqrt(s);
     if (mode == FIN_INIT) {
@@ -413,15 +516,15 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctl,
         ctl->kappa = 0;
         if (ctl->hist_len > 0) ctl->hist[0] = res;
         ctl->result_buf = cur;
-        if (res <= ctl->res0_floor * ctl->bnorm) { ctl->done = 1; ctl->status = CTL_OK; }
-        else { ctl->done = 0; ctl->status = CTL_NOT_CONVERGED; }
+        ctl->status = CTL_NOT_CONVERGED;
+        if (res <= ctl->res0_floor * ctl->bnorm) mark_done(ctl, bctl, CTL_OK);
         return;
     }
     const int kappa = ++ctl->kappa;
     ctl->res = res;
     if (kappa < ctl->hist_len) { ctl->hist[kappa] = res; ctl->dtau_hist[kappa - 1] = ctl->dtau; }
     ctl->result_buf = cur;
-    if (res <= ctl->tol * ctl->res0) { ctl->done = 1; ctl->status = CTL_OK; return; }
+    if (res <= ctl->tol * ctl->res0) { mark_done(ctl, bctl, CTL_OK); return; }
     const double delta = fabs(res - ctl->res_prev) / ctl->res0;
     double dtau = ctl->dtau;
     if (delta > ctl->eps_i) dtau *= ctl->grow;
@@ -429,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctl,
     dtau = dtau < ctl->dtau_min ? ctl->dtau_min : (dtau > ctl->dtau_max ? ctl->dtau_max : dtau);
     ctl->dtau = dtau;
     ctl->res_prev = res;
-    if (kappa >= ctl->max_cycles) { ctl->done = 1; ctl->status = CTL_NOT_CONVERGED; }
+    if (kappa >= ctl->max_cycles) mark_done(ctl, bctl, CTL_NOT_CONVERGED);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,87 +589,193 @@ __global__ void k_check_state(const Cell4<R>* __restrict__ s, const Sig2<R>* __r
 }
 
 // ---------------------------------------------------------------------------
+// Mixed precision: FP32 V-cycles in correction form inside FP64 defect
+// correction.
+//
+// k_defect: per fine cell, r64 = b64 - A64(v64) in FP64 (norm partials for the
+// stop test), and the FP32 fine problem of the next cycle in correction form:
+// base state w = fl32(v64), initial correction e = 0, source g = fl32(r64)
+// (the FP32 cycle solves A32(w + e) - A32(w) = r64 for e).
+__global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __restrict__ lv64,
+                                                     const Level<float>* __restrict__ lv32,
+                                                     WorkList wl, Ctl* __restrict__ ctls,
+                                                     double* __restrict__ partials)
+{
+    __shared__ Level<double> L;
+    __shared__ Level<float> M;
+    __shared__ Tile<double> t;
+    __shared__ double red[kThreads / 32];
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        load_level(L, lv64 + it.x);
+        load_level(M, lv32 + it.x);
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, it.y, x0, y0);
+        load_tile(L, L.u[0], x0, y0, t);
+        __syncthreads();
+        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
+        const int i = x0 + lx, j = y0 + ly;
+        double nrm = 0.0;
+        if (i < L.nx && j < L.ny) {
+            const size_t k = (size_t)j * L.nx + i;
+            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+            double NE, NFx, NFy;
+            neighbour_sum(L, t, ck, NE, NFx, NFy);
+            const Cell4<double> u = L.u[0][k];
+            const Sig2<double> sg = L.sig[k];
+            const double ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+            const double T2 = u.T * u.T, se = ka * (u.E - L.a_r * T2 * T2);
+            const Cell4<double> b = L.f[k];
+            const double rE = b.E - (L.diag * u.E + se - NE);
+            const double rFx = b.Fx - ((L.diag + kt) * u.Fx - NFx);
+            const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
+            const double rT = b.T - (L.c_v * u.T - se);
+            nrm = rE * rE + (rFx * rFx + rFy * rFy) / (L.c * L.c) + rT * rT;
+            const Cell4<float> wb = { (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
+            const Cell4<float> g = { (float)rE, (float)rFx, (float)rFy, (float)rT };
+            const Cell4<float> z = { 0.f, 0.f, 0.f, 0.f };
+            M.w[k] = wb;
+            M.f[k] = g;
+            M.u[0][k] = z;
+        }
+        double sum = block_sum(nrm, red);
+        if (threadIdx.x == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncthreads();
+    }
+}
+
+// k_accumulate: v64 += e in FP64 (e = the FP32 cycle's correction in buffer
+// `buf`); a cell whose update leaves the admissible set takes
+// v64 + theta_c min(1, tau*) e instead (the damping rule of Eq. (34)).
+__global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __restrict__ lv64,
+                                                         const Level<float>* __restrict__ lv32,
+                                                         WorkList wl, Ctl* __restrict__ ctls,
+                                                         int buf)
+{
+    __shared__ Level<double> L;
+    __shared__ Level<float> M;
+    const int nw = *wl.count;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        Ctl* ctl = ctls + it.x;
+        load_level(L, lv64 + it.x);
+        load_level(M, lv32 + it.x);
+        __syncthreads();
+        const int k = it.y * kThreads + threadIdx.x;
+        if (k < L.n) {
+            const Cell4<float> a = M.u[buf][k];
+            Cell4<double> e = { (double)a.E, (double)a.Fx, (double)a.Fy, (double)a.T };
+            if (!(isfinite(e.E) && isfinite(e.Fx) && isfinite(e.Fy) && isfinite(e.T))) {
+                // a correction the FP32 cycle could not form is dropped (counted)
+                e.E = e.Fx = e.Fy = e.T = 0.0;
+                atomicAdd(&ctl->newton_fail, 1u);
+            }
+            const Cell4<double> u = L.u[0][k];
+            Cell4<double> tg = { u.E + e.E, u.Fx + e.Fx, u.Fy + e.Fy, u.T + e.T };
+            if (!admissible(tg, L.c)) {
+                const double th = ctl->theta_c * fmin(1.0, max_admissible_step(u, e, L.c));
+                tg.E = u.E + th * e.E; tg.Fx = u.Fx + th * e.Fx;
+                tg.Fy = u.Fy + th * e.Fy; tg.T = u.T + th * e.T;
+                atomicAdd(&ctl->damped, 1u);
+            }
+            L.u[0][k] = tg;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-template <typename R>
-void launch_sweep(const Level<R>* dL, const Level<R>& hL, bool pseudo, int in_buf, int out_buf,
-                  Ctl* ctl, cudaStream_t s, bool delta)
+static inline int pgrid(const WorkList& wl)
 {
-    if (delta && std::is_same<R, float>::value) {
-        if (pseudo) k_sweep<R, true, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
-        else k_sweep<R, false, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
-        return;
-    }
-    if (pseudo) k_sweep<R, true><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
-    else k_sweep<R, false><<<hL.tiles, kThreads, 0, s>>>(dL, in_buf, out_buf, ctl);
+    return wl.capacity < kPersistentBlocks ? (wl.capacity > 0 ? wl.capacity : 1) : kPersistentBlocks;
 }
 
 template <typename R>
-void launch_apply(const Level<R>* dL, const Level<R>& hL, int mode, int state_buf,
-                  double* partials, int write_r, Ctl* ctl, cudaStream_t s, bool delta)
+void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
+                  int out_buf, cudaStream_t s, bool delta)
 {
+    const int g = pgrid(wl);
+    if (delta && std::is_same<R, float>::value) {
+        if (pseudo) k_sweep<R, true, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        else k_sweep<R, false, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        return;
+    }
+    if (pseudo) k_sweep<R, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+    else k_sweep<R, false><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+}
+
+template <typename R>
+void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int state_buf,
+                  double* partials, int write_r, cudaStream_t s, bool delta)
+{
+    const int g = pgrid(wl);
     if (delta && std::is_same<R, float>::value) {
         if (mode == APPLY_RESID)
-            k_apply<R, APPLY_RESID, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+            k_apply<R, APPLY_RESID, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         else if (mode == APPLY_FAS)
-            k_apply<R, APPLY_FAS, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+            k_apply<R, APPLY_FAS, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         else
-            k_apply<R, APPLY_A, true><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+            k_apply<R, APPLY_A, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         return;
     }
     if (mode == APPLY_RESID)
-        k_apply<R, APPLY_RESID><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        k_apply<R, APPLY_RESID><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
     else if (mode == APPLY_FAS)
-        k_apply<R, APPLY_FAS><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        k_apply<R, APPLY_FAS><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
     else
-        k_apply<R, APPLY_A><<<hL.tiles, kThreads, 0, s>>>(dL, state_buf, partials, write_r, ctl);
+        k_apply<R, APPLY_A><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
 }
 
 template <typename R>
-void launch_norm_state(const Level<R>* dL, const Level<R>& hL, const Cell4<R>* st,
-                       double* partials, cudaStream_t s)
+void launch_norm_state(const Level<R>* lv, WorkList wl, const Ctl* ctls, double* partials,
+                       cudaStream_t s)
 {
-    k_norm_state<R><<<hL.tiles, kThreads, 0, s>>>(dL, st, partials);
+    k_norm_state<R><<<pgrid(wl), kThreads, 0, s>>>(lv, wl, ctls, partials);
 }
 
 template <typename R>
-void launch_restrict(const Level<R>* dLf, const Level<R>* dLc, const Level<R>& hLc, int fine_buf,
-                     Ctl* ctl, cudaStream_t s, bool delta)
+void launch_restrict(const Level<R>* lvf, const Level<R>* lvc, WorkList wl, Ctl* ctls,
+                     int fine_buf, cudaStream_t s, bool delta)
 {
     if (delta && std::is_same<R, float>::value)
-        k_restrict<R, true><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
+        k_restrict<R, true><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl, ctls, fine_buf);
     else
-        k_restrict<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc, fine_buf, ctl);
+        k_restrict<R><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl, ctls, fine_buf);
 }
 
 template <typename R>
-void launch_restrict_sig(const Level<R>* dLf, const Level<R>* dLc, const Level<R>& hLc,
-                         cudaStream_t s)
+void launch_restrict_sig(const Level<R>* lvf, const Level<R>* lvc, WorkList wl, cudaStream_t s)
 {
-    k_restrict_sig<R><<<cdiv(hLc.n, kThreads), kThreads, 0, s>>>(dLf, dLc);
+    k_restrict_sig<R><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl);
 }
 
 template <typename R>
-void launch_prolong(const Level<R>* dLc, const Level<R>* dLf, const Level<R>& hLf, int coarse_buf,
-                    int fine_buf, Ctl* ctl, cudaStream_t s, bool delta)
+void launch_prolong(const Level<R>* lvc, const Level<R>* lvf, WorkList wl, Ctl* ctls,
+                    int coarse_buf, int fine_buf, cudaStream_t s, bool delta)
 {
     if (delta && std::is_same<R, float>::value)
-        k_prolong<R, true><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
+        k_prolong<R, true><<<pgrid(wl), kThreads, 0, s>>>(lvc, lvf, wl, ctls, coarse_buf, fine_buf);
     else
-        k_prolong<R><<<cdiv(hLf.n, kThreads), kThreads, 0, s>>>(dLc, dLf, coarse_buf, fine_buf, ctl);
+        k_prolong<R><<<pgrid(wl), kThreads, 0, s>>>(lvc, lvf, wl, ctls, coarse_buf, fine_buf);
 }
 
 template <typename R>
-void launch_make_rhs(const Level<R>* dL, const Level<R>& hL, int buf, cudaStream_t s)
+void launch_make_rhs(const Level<R>* lv, WorkList wl, const Ctl* ctls, int buf, cudaStream_t s)
 {
-    k_make_rhs<R><<<cdiv(hL.n, kThreads), kThreads, 0, s>>>(dL, buf);
+    k_make_rhs<R><<<pgrid(wl), kThreads, 0, s>>>(lv, wl, ctls, buf);
 }
 
-void launch_finalize(Ctl* ctl, const double* part, int np, const double* partb, int npb, int mode,
-                     int cur, cudaStream_t s)
+template <typename R>
+void launch_finalize(Ctl* ctls, const Level<R>* lv0, int nslots, const double* part,
+                     const double* partb, int mode, int cur, BatchCtl* bctl, cudaStream_t s)
 {
-    k_finalize<<<1, kThreads, 0, s>>>(ctl, part, np, partb, npb, mode, cur);
+    k_finalize<R><<<nslots, kThreads, 0, s>>>(ctls, lv0, part, partb, mode, cur, bctl);
 }
 
 template <typename R>
@@ -596,20 +805,34 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
     k_check_state<R><<<cdiv(n, kThreads), kThreads, 0, s>>>(st, sig, n, (R)c, bad);
 }
 
+void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
+                   double* partials, cudaStream_t s)
+{
+    k_defect<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, partials);
+}
+
+void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,
+                       Ctl* ctls, int buf, cudaStream_t s)
+{
+    k_accumulate<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, buf);
+}
+
 #define M1_INSTANTIATE(R)                                                                          \
-    template void launch_sweep<R>(const Level<R>*, const Level<R>&, bool, int, int, Ctl*,         \
+    template void launch_sweep<R>(const Level<R>*, WorkList, Ctl*, bool, int, int, cudaStream_t,  \
+                                  bool);                                                           \
+    template void launch_apply<R>(const Level<R>*, WorkList, Ctl*, int, int, double*, int,        \
                                   cudaStream_t, bool);                                             \
-    template void launch_apply<R>(const Level<R>*, const Level<R>&, int, int, double*, int, Ctl*, \
-                                  cudaStream_t, bool);                                             \
-    template void launch_norm_state<R>(const Level<R>*, const Level<R>&, const Cell4<R>*,         \
-                                       double*, cudaStream_t);                                     \
-    template void launch_restrict<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, Ctl*,\
+    template void launch_norm_state<R>(const Level<R>*, WorkList, const Ctl*, double*,            \
+                                       cudaStream_t);                                              \
+    template void launch_restrict<R>(const Level<R>*, const Level<R>*, WorkList, Ctl*, int,       \
                                      cudaStream_t, bool);                                          \
-    template void launch_restrict_sig<R>(const Level<R>*, const Level<R>*, const Level<R>&,       \
+    template void launch_restrict_sig<R>(const Level<R>*, const Level<R>*, WorkList,              \
                                          cudaStream_t);                                            \
-    template void launch_prolong<R>(const Level<R>*, const Level<R>*, const Level<R>&, int, int,  \
-                                    Ctl*, cudaStream_t, bool);                                     \
-    template void launch_make_rhs<R>(const Level<R>*, const Level<R>&, int, cudaStream_t);        \
+    template void launch_prolong<R>(const Level<R>*, const Level<R>*, WorkList, Ctl*, int, int,   \
+                                    cudaStream_t, bool);                                           \
+    template void launch_make_rhs<R>(const Level<R>*, WorkList, const Ctl*, int, cudaStream_t);   \
+    template void launch_finalize<R>(Ctl*, const Level<R>*, int, const double*, const double*,    \
+                                     int, int, BatchCtl*, cudaStream_t);                           \
     template void launch_pack_state<R>(const double*, const double*, const double*, const double*,\
                                        double, Cell4<R>*, int, cudaStream_t);                      \
     template void launch_unpack_state<R>(const Cell4<R>*, double*, double*, double*, double*, int,\
@@ -620,98 +843,5 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 
 M1_INSTANTIATE(double)
 M1_INSTANTIATE(float)
-
-// ---------------------------------------------------------------------------
-// Mixed precision: FP32 V-cycles in correction form inside FP64 defect
-// correction.
-//
-// k_defect: per fine cell, r64 = b64 - A64(v64) in FP64 (norm partials for the
-// stop test), and the FP32 fine problem of the next cycle in correction form:
-// base state w = fl32(v64), initial correction e = 0, source g = fl32(r64)
-// (the FP32 cycle solves A32(w + e) - A32(w) = r64 for e).
-__global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __restrict__ L64p,
-                                                     const Level<float>* __restrict__ L32p,
-                                                     double* __restrict__ partials,
-                                                     Ctl* __restrict__ ctl)
-{
-    if (ctl->done) return;
-    __shared__ Level<double> L;
-    __shared__ Level<float> M;
-    __shared__ Tile<double> t;
-    __shared__ double red[kThreads / 32];
-    load_level(L, L64p);
-    load_level(M, L32p);
-    __syncthreads();
-    int x0, y0;
-    tile_origin(L, blockIdx.x, x0, y0);
-    load_tile(L, L.u[0], x0, y0, t);
-    __syncthreads();
-    const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-    const int i = x0 + lx, j = y0 + ly;
-    double nrm = 0.0;
-    if (i < L.nx && j < L.ny) {
-        const size_t k = (size_t)j * L.nx + i;
-        const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
-        double NE, NFx, NFy;
-        neighbour_sum(L, t, ck, NE, NFx, NFy);
-        const Cell4<double> u = L.u[0][k];
-        const Sig2<double> sg = L.sig[k];
-        const double ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-        const double T2 = u.T * u.T, se = ka * (u.E - L.a_r * T2 * T2);
-        const Cell4<double> b = L.f[k];
-        const double rE = b.E - (L.diag * u.E + se - NE);
-        const double rFx = b.Fx - ((L.diag + kt) * u.Fx - NFx);
-        const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
-        const double rT = b.T - (L.c_v * u.T - se);
-        nrm = rE * rE + (rFx * rFx + rFy * rFy) / (L.c * L.c) + rT * rT;
-        const Cell4<float> w = { (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
-        const Cell4<float> g = { (float)rE, (float)rFx, (float)rFy, (float)rT };
-        const Cell4<float> z = { 0.f, 0.f, 0.f, 0.f };
-        M.w[k] = w;
-        M.f[k] = g;
-        M.u[0][k] = z;
-    }
-    double sum = block_sum<double>(nrm, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum * L.vol;
-}
-
-// k_accumulate: v64 += e in FP64 (e = the FP32 cycle's correction in buffer
-// `buf`); a cell whose update leaves the admissible set takes
-// v64 + theta_c min(1, tau*) e instead (the damping rule of Eq. (34)).
-__global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __restrict__ L64p,
-                                                         const Level<float>* __restrict__ L32p,
-                                                         int buf, Ctl* __restrict__ ctl)
-{
-    if (ctl->done) return;
-    __shared__ Level<double> L;
-    __shared__ Level<float> M;
-    load_level(L, L64p);
-    load_level(M, L32p);
-    __syncthreads();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.n) return;
-    const Cell4<float> a = M.u[buf][k];
-    const Cell4<double> e = { (double)a.E, (double)a.Fx, (double)a.Fy, (double)a.T };
-    const Cell4<double> u = L.u[0][k];
-    Cell4<double> t = { u.E + e.E, u.Fx + e.Fx, u.Fy + e.Fy, u.T + e.T };
-    if (!admissible(t, L.c)) {
-        const double th = ctl->theta_c * fmin(1.0, max_admissible_step(u, e, L.c));
-        t.E = u.E + th * e.E; t.Fx = u.Fx + th * e.Fx; t.Fy = u.Fy + th * e.Fy; t.T = u.T + th * e.T;
-        atomicAdd(&ctl->damped, 1u);
-    }
-    L.u[0][k] = t;
-}
-
-void launch_defect(const Level<double>* L64, const Level<double>& h64, const Level<float>* L32,
-                   double* partials, Ctl* ctl, cudaStream_t s)
-{
-    k_defect<<<h64.tiles, kThreads, 0, s>>>(L64, L32, partials, ctl);
-}
-
-void launch_accumulate(const Level<double>* L64, const Level<double>& h64, const Level<float>* L32,
-                       int buf, Ctl* ctl, cudaStream_t s)
-{
-    k_accumulate<<<cdiv(h64.n, kThreads), kThreads, 0, s>>>(L64, L32, buf, ctl);
-}
 
 }  // namespace m1

@@ -33,7 +33,9 @@ OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
            "m1_set_inflow", "m1_get_state", "m1_implicit_step", "m1_residual_norm",
            "m1_step_history", "m1_jacobi", "m1_op_level", "m1_op_restrict", "m1_op_prolong_correct",
-           "m1_residual_norm_noalloc", "m1_last_error"]
+           "m1_residual_norm_noalloc", "m1_last_error", "m1_create_batch", "m1_destroy_batch",
+           "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
+           "m1_batch_implicit_step"]
 
 
 class M1Error(RuntimeError):
@@ -92,6 +94,13 @@ _lib.m1_op_level.argtypes = [ctypes.POINTER(GridDesc), _vp, ctypes.c_double, _vp
                              ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _dp]
 _lib.m1_residual_norm_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_double, _vp, _vp,
                                           _vp, _vp, _vp, _vp]
+_lib.m1_create_batch.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.m1_destroy_batch.argtypes = [_vp]
+_lib.m1_batch_set_state.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.m1_batch_set_inflow.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+_lib.m1_batch_get_state.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.m1_batch_implicit_step.argtypes = [_vp, _dp, ctypes.POINTER(SolveParams),
+                                        ctypes.POINTER(StepStats)]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
@@ -210,17 +219,87 @@ class Grid:
         return hist, dtau
 
 
-def grid_from_case(case, lmax=None, precision=FP64, stream=None) -> Grid:
-    """A grid holding the state, opacities and inflow of an input case."""
-    g = Grid(desc_from_case(case, lmax, precision), stream)
+class Batch:
+    """Owner of one m1_batch_t: independent instances stepped together."""
+
+    def __init__(self, descs, stream=None):
+        arr = (GridDesc * len(descs))(*descs)
+        h = _vp()
+        _check(_lib.m1_create_batch(arr, len(descs), stream, ctypes.byref(h)), "m1_create_batch")
+        self.h = h
+        self.descs = list(descs)
+
+    def close(self):
+        if self.h:
+            _lib.m1_destroy_batch(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __len__(self):
+        return len(self.descs)
+
+    def set_state(self, k, E, Fx, Fy, T, sig_a=None, sig_s=None, on_device=False):
+        if not on_device:
+            E, Fx, Fy, T, sig_a, sig_s = map(_host, (E, Fx, Fy, T, sig_a, sig_s))
+        st = _lib.m1_batch_set_state(self.h, k, _ptr(E), _ptr(Fx), _ptr(Fy), _ptr(T), _ptr(sig_a),
+                                     _ptr(sig_s), int(on_device))
+        return _check(st, "m1_batch_set_state")
+
+    def set_inflow(self, k, side, E, Fx, Fy):
+        E, Fx, Fy = map(_host, (E, Fx, Fy))
+        return _check(_lib.m1_batch_set_inflow(self.h, k, side, _ptr(E), _ptr(Fx), _ptr(Fy)),
+                      "m1_batch_set_inflow")
+
+    def get_state(self, k):
+        d = self.descs[k]
+        out = [np.zeros((d.ny, d.nx)) for _ in range(4)]
+        _check(_lib.m1_batch_get_state(self.h, k, *[_ptr(a) for a in out], 0),
+               "m1_batch_get_state")
+        return out
+
+    def implicit_step(self, dts, params: SolveParams | None = None, allow_not_converged=False):
+        dts = np.ascontiguousarray(dts, dtype=np.float64)
+        stats = (StepStats * len(self.descs))()
+        st = _lib.m1_batch_implicit_step(self.h, dts.ctypes.data_as(_dp),
+                                         ctypes.byref(params) if params else None, stats)
+        _check(st, "m1_batch_implicit_step",
+               allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return list(stats)
+
+
+def load_case(target, case, index=None):
+    """Set the state, opacities and inflow of an input case on a Grid or a
+    Batch slot."""
     s = case["state"]
-    g.set_state(s[0], s[1], s[2], s[3], case["sa"], case["ss"])
+    args = (s[0], s[1], s[2], s[3], case["sa"], case["ss"])
+    if index is None:
+        target.set_state(*args)
+    else:
+        target.set_state(index, *args)
     if case.get("inflow") is not None:
         d = case["desc"]
         for w in range(4):
             if d["bc"][w] == "inflow":
                 n = d["ny"] if w < 2 else d["nx"]
-                g.set_inflow(w, *[case["inflow"][w, f, :n] for f in range(3)])
+                prof = [case["inflow"][w, f, :n] for f in range(3)]
+                if index is None:
+                    target.set_inflow(w, *prof)
+                else:
+                    target.set_inflow(index, w, *prof)
+
+
+def batch_from_cases(cases, lmax=None, precision=FP64, stream=None) -> Batch:
+    b = Batch([desc_from_case(c, lmax, precision) for c in cases], stream)
+    for k, c in enumerate(cases):
+        load_case(b, c, k)
+    return b
+
+
+def grid_from_case(case, lmax=None, precision=FP64, stream=None) -> Grid:
+    """A grid holding the state, opacities and inflow of an input case."""
+    g = Grid(desc_from_case(case, lmax, precision), stream)
+    load_case(g, case)
     return g
 
 
