@@ -62,6 +62,10 @@ DIV_SLOTS = 10.2
 SWEEP_SLOTS = (3 * DIV_SLOTS + 18) + 24 + (2 * DIV_SLOTS + 22) + 3 * (6 + DIV_SLOTS)
 SWEEP_FLOPS = 2 * SWEEP_SLOTS
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (recipe table), 152 SMs x 2 DFMA/clk x 2.07 GHz
+# FP32 fine sweep of the mixed path (correction form), per cell-update: read the
+# correction e, the base state w and the source g (3 x 16 B), (sigma_a, sigma_s)
+# (8 B); write e' (16 B).
+SWEEP32_BYTES = 3 * 16 + 8 + 16
 
 
 class ClockSampler:
@@ -125,6 +129,138 @@ def cpu_sample(case, cycles):
     return cells * st["fine_sweeps"] / dt, dt, st["fine_sweeps"]
 
 
+def sweep_ms(grid, dt, stream, flush, reset, reps=20):
+    """Median time of one fine sweep: 0.5 x (m1_jacobi with 2 sweeps - with 0
+    sweeps), each launch sequence timed with CUDA events on the grid's stream
+    after an L2 flush (state reset before each call, untimed)."""
+    import torch
+
+    def timed(nsw):
+        out = []
+        for _ in range(reps):
+            reset()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            grid.jacobi(dt, nsw)
+            b.record(stream)
+            out.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([x.elapsed_time(y) for x, y in out]))
+
+    return 0.5 * (timed(2) - timed(0))
+
+
+def field_errors(got, ref):
+    """Relative L2 errors per field (E and the flux against ||E||, T against ||T||)."""
+    nE = np.linalg.norm(ref[0])
+    return {"E": float(np.linalg.norm(got[0] - ref[0]) / nE),
+            "Fx": float(np.linalg.norm(got[1] - ref[1]) / nE),
+            "Fy": float(np.linalg.norm(got[2] - ref[2]) / nE),
+            "T": float(np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(ref[3]))}
+
+
+def bench_mixed(m1, case, stream, s0, flush, ref64, steps, hbm_peak):
+    """The same workload through the mixed-precision path (FP32 V-cycles in
+    correction form inside FP64 defect correction)."""
+    import torch
+    grid = m1.grid_from_case(case, precision=m1.MIXED, stream=stream.cuda_stream)
+    params = m1.m1_default_params(tol=case["tol"])
+    dt = case["dt"]
+    cells = case["desc"]["nx"] * case["desc"]["ny"]
+
+    def one():
+        grid.set_state(*s0, on_device=True)
+        return grid.implicit_step(dt, params)
+
+    one()
+    torch.cuda.synchronize()
+    ev, st = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.append(one())
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    got = np.stack(grid.get_state())
+    sms = sweep_ms(grid, dt, stream, flush, lambda: grid.set_state(*s0, on_device=True))
+    grid.close()
+    gbs = SWEEP32_BYTES * cells / (sms * 1e-3) / 1e9
+    units = cells * sum(x.sweeps for x in st)
+    return {"workload": WORKLOAD.replace("fp64", "mixed"), "value": units / (sum(ms) * 1e-3),
+            "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "cycles_per_step": [x.cycles for x in st],
+            "err_vs_fp64_gpu": field_errors(got, ref64),
+            "roofline_fp32_sweep": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                    "unit": "GB/s", "frac": gbs / hbm_peak, "kernel_ms": sms,
+                                    "bytes_per_cell": SWEEP32_BYTES,
+                                    "kernel": "k_sweep<float, correction form>"}}
+
+
+def bench_batched(m1, count, stream):
+    """Independent 2D instances of uneven sizes stepped together, mixed and FP64."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    cases = inputs.batched_instances(count)
+    cells = sum(c["desc"]["nx"] * c["desc"]["ny"] for c in cases)
+    out = {"workload": f"m1-batched-2d-{count}-instances-64..1024-lmax5-tol1e-8",
+           "instances": count, "cells": cells}
+    for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
+        b = m1.batch_from_cases(cases, precision=prec, stream=stream.cuda_stream)
+        params = m1.m1_default_params(tol=1e-8)
+        dts = [c["dt"] for c in cases]
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        st = b.implicit_step(dts, params, allow_not_converged=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        b.close()
+        units = sum(c["desc"]["nx"] * c["desc"]["ny"] * x.sweeps for c, x in zip(cases, st))
+        out[name] = {"ms_per_step": ms, "solves_per_s": count / (ms * 1e-3),
+                     "cell_updates_per_s": units / (ms * 1e-3),
+                     "not_converged": sum(1 for x in st if x.status != 0),
+                     "max_cycles": max(x.cycles for x in st)}
+    out["mixed_over_fp64_solves"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
+def bench_serving(m1, reqs, stream, budget):
+    """A Poisson arrival stream of simulations served with continuous batching,
+    mixed precision against the plain FP64 path (the same stream through an FP64
+    server)."""
+    out = {"requests": len(reqs), "steps": sum(r["nsteps"] for r in reqs),
+           "sizes": sorted({(r["case"]["desc"]["dim"], r["case"]["desc"]["nx"]) for r in reqs}),
+           "arrival_span_s": reqs[-1]["arrival_s"], "budget_bytes": budget}
+    for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
+        grids = [m1.grid_from_case(r["case"], precision=prec) for r in reqs]
+        srv = m1.Server(budget, 64, reqs[0]["case"]["lmax"], prec, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        tickets = []
+        for r, g in zip(reqs, grids):
+            delay = r["arrival_s"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(g, r["nsteps"], r["case"]["dt"],
+                                      m1.m1_default_params(tol=r["case"]["tol"])))
+        status = [srv.wait(t, 3600.0) for t in tickets]
+        wall = time.perf_counter() - t0
+        s = srv.stats()
+        srv.close()
+        for g in grids:
+            g.close()
+        out[name] = {"solves_per_s": s.steps_done / wall, "busy_solves_per_s": s.solves_per_s,
+                     "p50_ms": s.p50_ms, "p99_ms": s.p99_ms, "mean_ms": s.mean_ms,
+                     "wall_s": wall, "cycles": s.cycles, "bytes_peak": s.bytes_peak,
+                     "failed": sum(1 for x in status if x != m1.OK)}
+    out["mixed_over_fp64_solves"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def run_reference(args, case):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -159,6 +295,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed, batched and serving measurements")
+    ap.add_argument("--batch-count", type=int, default=32,
+                    help="instances of the batched sample (512 = the full batched config)")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serve the full stream (64 requests, 10-100 steps, up to 2048^2)")
     args = ap.parse_args()
 
     from paper_2208_14703_gb300 import inputs
@@ -224,31 +366,10 @@ def main():
     ms_total = sum(ms_steps)
 
     # dominant kernel: the fine FP64 Jacobi sweep, timed with CUDA events on the
-    # grid's stream (state reset first; L2 flushed before each timed launch)
-    nsw = 20
-    ks = []
-    grid.set_state(*s0, on_device=True)
-    for k in range(nsw):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        grid.jacobi(dt, 2)
-        b.record(stream)
-        ks.append((a, b))
-    torch.cuda.synchronize()
-    # each m1_jacobi call = rhs build + two sweeps (an even count ends in the
-    # state buffer, no copy); subtract the rhs kernel timed alone (zero sweeps)
-    z = []
-    for k in range(nsw):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        grid.jacobi(dt, 0)
-        b.record(stream)
-        z.append((a, b))
-    torch.cuda.synchronize()
-    sweep_ms = 0.5 * (np.median([a.elapsed_time(b) for a, b in ks])
-                      - np.median([a.elapsed_time(b) for a, b in z]))
+    # grid's stream (each m1_jacobi call = rhs build + the sweeps; an even count
+    # ends in the state buffer, so 0.5 x (2 sweeps - 0 sweeps) is one sweep)
+    ref64 = np.stack(grid.get_state())
+    sweep64_ms = sweep_ms(grid, dt, stream, flush, lambda: grid.set_state(*s0, on_device=True))
     sampler_out = sampler.stop()
 
     sweeps = [s.sweeps for s in stats]
@@ -280,11 +401,11 @@ def main():
         e2e_val = t.item()
 
     pk = peaks()
-    tflops = SWEEP_FLOPS * cells / (sweep_ms * 1e-3) / 1e12
-    gbs = SWEEP_BYTES * cells / (sweep_ms * 1e-3) / 1e9
+    tflops = SWEEP_FLOPS * cells / (sweep64_ms * 1e-3) / 1e12
+    gbs = SWEEP_BYTES * cells / (sweep64_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
             "frac": tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
-            "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep_ms,
+            "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep64_ms,
             "peak_source": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
             "flops_per_cell": SWEEP_FLOPS,
             "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -297,6 +418,23 @@ def main():
         v, secs, fs = cpu_sample(case, 4)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"4 V-cycles of the same 1024^2 workload ({fs} fine sweeps, {secs:.1f} s)"}
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        from paper_2208_14703_gb300 import inputs
+        extras["mixed"] = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps,
+                                      pk["hbm_gbs"])
+        extras["batched"] = bench_batched(m1, args.batch_count, stream)
+        if args.serve_full:
+            reqs = inputs.serving_stream(64)
+        else:
+            reqs = inputs.serving_stream(12, rate_hz=20.0, sizes_2d=(128, 256, 512),
+                                         steps=(10, 20))
+        extras["serving"] = bench_serving(m1, reqs, stream, 32 << 30)
+        extras["serving"]["workload"] = ("poisson-stream-1d-256..65536-2d-128..2048-10..100-steps"
+                                         if args.serve_full else
+                                         "poisson-stream-sample-12-requests-1d-256..65536-"
+                                         "2d-128..512-10..20-steps")
 
     launches = sum(s.launches for s in stats) + 2 * args.steps
     if rank == 0:
@@ -315,7 +453,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
                     "d2h_bytes_per_step": 4 * 8 * cells},
-            "gpu_launches": launches, "clocks": sampler_out,
+            "gpu_launches": launches, "clocks": sampler_out, **extras,
         }))
     grid.close()
     if world > 1:

@@ -136,7 +136,11 @@ m1_status m1_implicit_step(m1_grid_t g, double dt, const m1_solve_params* params
  * Table 1): b = (E, F, C_v T) of the current state, then `sweeps` nonlinear
  * Jacobi sweeps of A(v) = b starting from the current state, which becomes the
  * result.  Asynchronous: the sweeps are queued on the grid's stream and the call
- * returns; synchronise that stream before reading the state from another stream. */
+ * returns; synchronise that stream before reading the state from another stream.
+ * On a MIXED grid the sweeps run in FP32 on the correction equation
+ * A(w + e) - A(w) = r (w = the state rounded to FP32, r = b - A(v) in FP64,
+ * e = 0 at the start), and the state becomes v + e in FP64 (damped like the
+ * prolongation, Eq. (34), where v + e is not admissible). */
 m1_status m1_jacobi(m1_grid_t g, double dt, int sweeps);
 
 /* ||b - A(v)|| (the norm above) of the current state v for a step of length dt,
@@ -171,6 +175,46 @@ m1_status m1_batch_get_state(m1_batch_t b, int index, double* E, double* Fx, dou
  * NOT_CONVERGED if any did). */
 m1_status m1_batch_implicit_step(m1_batch_t b, const double* dt, const m1_solve_params* params,
                                  m1_step_stats* stats);
+
+/* ---- serving: many simulations stepping on one GPU with continuous batching ----
+ * A server owns one engine of max_slots slots (level count lmax, precision FP64
+ * or MIXED; the structural solver parameters nu0, m_pseudo, m_coarse are fixed
+ * at creation, the others are per request).  m1_serve_submit queues a caller's
+ * grid (its state set, same lmax and precision) for nsteps implicit steps of
+ * length dt.  A scheduler thread admits queued requests in arrival order into
+ * free slots while their level hierarchies fit hbm_budget_bytes, copies the
+ * state in on the device (it stays resident for all steps), and launches V-cycle
+ * graphs over every active slot; a slot whose step converged starts its next
+ * step at once, and a finished request's state is copied back into its grid
+ * and its slot and budget are freed, all between V-cycles, so requests arriving
+ * while others run join the running batch.  The caller must not use a
+ * submitted grid until its ticket completes.  Submit, poll, wait and stats are
+ * thread safe.  Step latency is the host time from the start of a step to the
+ * poll (every 2 cycles) that sees it converged. */
+typedef struct m1_server* m1_server_t;
+typedef struct {
+    long long requests_done, steps_done, cycles;
+    double wall_s;          /* from the first admission to the last completed step */
+    double solves_per_s;    /* steps_done / wall_s */
+    double p50_ms, p99_ms, mean_ms;   /* step latency */
+    int active, queued;
+    long long bytes_in_use, bytes_peak;   /* budgeted device bytes of admitted requests */
+} m1_server_stats;
+m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int precision,
+                           const m1_solve_params* structure, void* cuda_stream, m1_server_t* out);
+/* REJECTED: the grid alone exceeds the budget; INVALID_ARG: precision, lmax or
+ * structural parameters differ from the server's. */
+m1_status m1_serve_submit(m1_server_t s, m1_grid_t g, int nsteps, double dt,
+                          const m1_solve_params* params, unsigned long long* ticket);
+/* PENDING while queued or running; then OK, NOT_CONVERGED (a step reached
+ * max_cycles; the request stops there) or the server's error. */
+m1_status m1_serve_poll(m1_server_t s, unsigned long long ticket, int* steps_done,
+                        m1_step_stats* last);
+/* Blocks until the ticket completes or timeout_s passes (TIMEOUT). */
+m1_status m1_serve_wait(m1_server_t s, unsigned long long ticket, double timeout_s);
+m1_status m1_server_get_stats(m1_server_t s, m1_server_stats* out);
+/* Finishes every submitted request, then stops the scheduler and frees the engine. */
+m1_status m1_server_destroy(m1_server_t s);
 
 /* ---- single-kernel entry points (one kernel on caller data, for checks) ----
  * Stateless: each call allocates its own device buffers for `desc` (lmax is

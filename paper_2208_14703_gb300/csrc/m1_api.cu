@@ -857,8 +857,239 @@ m1_status Engine<R>::op_prolong(const double* uc, const double* vc, const double
     return M1_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Serving support: slots joining and leaving a running engine.
+
+// Device bytes a slot of this engine takes for grid `g` (its levels' buffers).
+template <typename R>
+size_t Engine<R>::slot_bytes(const m1_grid_desc& g) const
+{
+    size_t b = 0;
+    long long nx = g.nx, ny = g.dim == 2 ? g.ny : 1;
+    const int states = delta ? 7 : 5;
+    for (int l = 0; l < L; ++l) {
+        const long long n = nx * ny;
+        b += (size_t)n * (states * sizeof(Cell4<R>) + sizeof(Sig2<R>));
+        b += sizeof(R) * 12 * (size_t)std::max(nx, ny) + 8 * 256;
+        nx /= 2; if (g.dim == 2) ny /= 2;
+    }
+    return b;
+}
+
+// Level-0 work lists of the given slots (for the start of their steps).
+template <typename R>
+m1_status Engine<R>::set_init_lists(const std::vector<int>& slots)
+{
+    init_tiles.host.clear();
+    init_chunks.host.clear();
+    for (int i : slots) {
+        for (int t = 0; t < h[i].tiles; ++t) init_tiles.host.push_back(make_int2(i, t));
+        for (int c = 0; c < h[i].chunks; ++c) init_chunks.host.push_back(make_int2(i, c));
+    }
+    M1_TRY(upload_list(init_tiles));
+    M1_TRY(upload_list(init_chunks));
+    if (!slots.empty())
+        M1_CK(cudaMemcpyAsync(init_slots, slots.data(), sizeof(int) * slots.size(),
+                              cudaMemcpyHostToDevice, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    return M1_OK;
+}
+
+// State, opacities (and their coarse restrictions) and inflow profiles of slot 0
+// of `src` (a caller's grid, same precision and level count) into `slot`.
+template <typename R>
+m1_status Engine<R>::copy_slot_in(int slot, Engine<R>& src)
+{
+    M1_CK(cudaStreamSynchronize(src.stream));
+    const Level<R>& q = h[slot];
+    const Level<R>& p = src.h[0];
+    if (q.n != p.n) return M1_ERR_INVALID_ARG;
+    M1_CK(cudaMemcpyAsync(q.u[0], p.u[0], sizeof(Cell4<R>) * q.n, cudaMemcpyDeviceToDevice, stream));
+    M1_CK(cudaMemcpyAsync(q.sig, p.sig, sizeof(Sig2<R>) * q.n, cudaMemcpyDeviceToDevice, stream));
+    for (int l = 1; l < L; ++l) {
+        init_chunks.host.clear();
+        for (int c = 0; c < h[(size_t)l * cap + slot].chunks; ++c)
+            init_chunks.host.push_back(make_int2(slot, c));
+        M1_TRY(upload_list(init_chunks));
+        launch_restrict_sig<R>(d + (size_t)(l - 1) * cap, d + (size_t)l * cap, init_chunks.view(), stream);
+        M1_CK(cudaGetLastError());
+    }
+    for (int l = 0; l < L; ++l) {
+        prof[(size_t)l * cap + slot] = src.prof[(size_t)l * src.cap];
+        std::vector<R> tmp(prof[(size_t)l * cap + slot].begin(), prof[(size_t)l * cap + slot].end());
+        M1_CK(cudaMemcpyAsync(h[(size_t)l * cap + slot].inflow, tmp.data(), sizeof(R) * tmp.size(),
+                              cudaMemcpyHostToDevice, stream));
+        M1_CK(cudaStreamSynchronize(stream));
+    }
+    rhs_valid[slot] = 0;
+    return M1_OK;
+}
+
+template <typename R>
+m1_status Engine<R>::copy_slot_out(int slot, Engine<R>& dst)
+{
+    const Level<R>& q = h[slot];
+    M1_CK(cudaMemcpyAsync(dst.h[0].u[0], q.u[0], sizeof(Cell4<R>) * q.n, cudaMemcpyDeviceToDevice, stream));
+    M1_CK(cudaStreamSynchronize(stream));
+    dst.rhs_valid[0] = 0;
+    return M1_OK;
+}
+
+// Bring a finished slot's result into buffer 0 (where its next step starts).
+template <typename R>
+m1_status Engine<R>::settle(int slot)
+{
+    if (ctl_h[slot].result_buf == 1)
+        M1_CK(cudaMemcpyAsync(h[slot].u[0], h[slot].u[1], sizeof(Cell4<R>) * h[slot].n,
+                              cudaMemcpyDeviceToDevice, stream));
+    return M1_OK;
+}
+
 template struct Engine<double>;
 template struct Engine<float>;
+
+m1_status PlainModel::sv_copy_in(int slot, Model& src)
+{
+    auto* p = dynamic_cast<PlainModel*>(&src);
+    if (!p) return M1_ERR_INVALID_ARG;
+    return e.copy_slot_in(slot, p->e);
+}
+
+m1_status PlainModel::sv_copy_out(int slot, Model& dst)
+{
+    auto* p = dynamic_cast<PlainModel*>(&dst);
+    if (!p) return M1_ERR_INVALID_ARG;
+    return e.copy_slot_out(slot, p->e);
+}
+
+// Start a step on the given slots while the other slots keep cycling.
+m1_status PlainModel::sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
+                               const std::vector<m1_solve_params>& ps)
+{
+    for (size_t k = 0; k < slots.size(); ++k) {
+        const int i = slots[k];
+        M1_TRY(validate_params(ps[k]));
+        M1_TRY(e.set_dt(i, dts[k]));
+        e.ctl_h[i] = make_ctl(ps[k], (double)e.h[i].diag);
+        M1_CK(cudaMemcpyAsync(e.ctl + i, e.ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, e.stream));
+    }
+    M1_TRY(e.set_init_lists(slots));
+    launch_make_rhs<double>(e.d, e.init_chunks.view(), e.ctl, 0, e.stream);
+    launch_apply<double>(e.d, e.init_tiles.view(), e.ctl, APPLY_RESID, 0, e.part, 0, e.stream);
+    launch_norm_state<double>(e.d, e.init_tiles.view(), e.ctl, e.partb, e.stream);
+    launch_finalize<double>(e.ctl, e.d, (int)slots.size(), e.part, e.partb, FIN_INIT, 0, e.bctl,
+                            e.stream, e.init_slots);
+    M1_CK(cudaGetLastError());
+    return M1_OK;
+}
+
+m1_status PlainModel::sv_cycles(const Params& p, int n)
+{
+    M1_TRY(e.build_graph(p));
+    for (int k = 0; k < n; ++k) M1_CK(cudaGraphLaunch(e.graph, e.stream));
+    return M1_OK;
+}
+
+m1_status PlainModel::sv_read(std::vector<Ctl>& out)
+{
+    M1_CK(cudaMemcpyAsync(e.ctl_h, e.ctl, sizeof(Ctl) * e.cap, cudaMemcpyDeviceToHost, e.stream));
+    M1_CK(cudaStreamSynchronize(e.stream));
+    out.assign(e.ctl_h, e.ctl_h + e.cap);
+    return M1_OK;
+}
+
+m1_status MixedModel::sv_init(int cap, int L, cudaStream_t s)
+{
+    M1_TRY(hi.init(cap, 1, false, s, 0));
+    M1_TRY(lo.init(cap, L, true, hi.stream, 0));
+    lo.ctl = hi.ctl;
+    return M1_OK;
+}
+
+size_t MixedModel::sv_bytes(const m1_grid_desc& d) const
+{
+    m1_grid_desc g = d;
+    g.lmax = 1;
+    return hi.slot_bytes(g) + lo.slot_bytes(d);
+}
+
+m1_status MixedModel::sv_add(const m1_grid_desc& d, int* slot)
+{
+    m1_grid_desc g = d;
+    g.lmax = 1;
+    g.precision = M1_FP64;
+    int a, b;
+    M1_TRY(hi.add_slot(g, &a));
+    m1_status st = lo.add_slot(d, &b);
+    if (st != M1_OK) { hi.remove_slot(a); return st; }
+    if (a != b) return M1_ERR_CUDA;
+    *slot = a;
+    return M1_OK;
+}
+
+m1_status MixedModel::sv_remove(int slot)
+{
+    M1_TRY(hi.remove_slot(slot));
+    return lo.remove_slot(slot);   // clears the shared control block of the slot again
+}
+
+m1_status MixedModel::sv_rebuild()
+{
+    M1_TRY(hi.rebuild());
+    return lo.rebuild();
+}
+
+m1_status MixedModel::sv_copy_in(int slot, Model& src)
+{
+    auto* p = dynamic_cast<MixedModel*>(&src);
+    if (!p) return M1_ERR_INVALID_ARG;
+    M1_TRY(hi.copy_slot_in(slot, p->hi));
+    return lo.copy_slot_in(slot, p->lo);
+}
+
+m1_status MixedModel::sv_copy_out(int slot, Model& dst)
+{
+    auto* p = dynamic_cast<MixedModel*>(&dst);
+    if (!p) return M1_ERR_INVALID_ARG;
+    return hi.copy_slot_out(slot, p->hi);
+}
+
+m1_status MixedModel::sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
+                               const std::vector<m1_solve_params>& ps)
+{
+    for (size_t k = 0; k < slots.size(); ++k) {
+        const int i = slots[k];
+        M1_TRY(validate_params(ps[k]));
+        M1_TRY(hi.set_dt(i, dts[k]));
+        M1_TRY(lo.set_dt(i, dts[k]));
+        hi.ctl_h[i] = make_ctl(ps[k], (double)hi.h[i].diag);
+        M1_CK(cudaMemcpyAsync(hi.ctl + i, hi.ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, hi.stream));
+    }
+    M1_TRY(hi.set_init_lists(slots));
+    launch_make_rhs<double>(hi.d, hi.init_chunks.view(), hi.ctl, 0, hi.stream);
+    launch_norm_state<double>(hi.d, hi.init_tiles.view(), hi.ctl, hi.partb, hi.stream);
+    launch_defect(hi.d, lo.d, hi.init_tiles.view(), hi.ctl, hi.part, hi.stream);
+    launch_finalize<double>(hi.ctl, hi.d, (int)slots.size(), hi.part, hi.partb, FIN_INIT, 0, hi.bctl,
+                            hi.stream, hi.init_slots);
+    M1_CK(cudaGetLastError());
+    return M1_OK;
+}
+
+m1_status MixedModel::sv_cycles(const Params& p, int n)
+{
+    M1_TRY(build_graph(p));
+    for (int k = 0; k < n; ++k) M1_CK(cudaGraphLaunch(graph, hi.stream));
+    return M1_OK;
+}
+
+m1_status MixedModel::sv_read(std::vector<Ctl>& out)
+{
+    M1_CK(cudaMemcpyAsync(hi.ctl_h, hi.ctl, sizeof(Ctl) * hi.cap, cudaMemcpyDeviceToHost, hi.stream));
+    M1_CK(cudaStreamSynchronize(hi.stream));
+    out.assign(hi.ctl_h, hi.ctl_h + hi.cap);
+    return M1_OK;
+}
 
 // ---------------------------------------------------------------------------
 m1_status PlainModel::create(const std::vector<m1_grid_desc>& descs, cudaStream_t s)
@@ -986,6 +1217,27 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
     return all_ok ? M1_OK : M1_ERR_NOT_CONVERGED;
 }
 
+// Algorithm 1 in mixed precision: b = (E, F, C_v T) of the current state v, the
+// FP64 defect r = b - A(v), `sweeps` FP32 Jacobi sweeps of the correction
+// equation A32(w + e) - A32(w) = r from e = 0 (w = fl32(v)), then v += e in FP64.
+m1_status MixedModel::jacobi(int i, double dt, int sweeps)
+{
+    if (hi.cap != 1 || i != 0 || !hi.used[0] || !(dt > 0) || sweeps < 0) return M1_ERR_INVALID_ARG;
+    M1_TRY(hi.set_dt(0, dt));
+    M1_TRY(lo.set_dt(0, dt));
+    M1_TRY(hi.set_ctl_simple(0, 0.0, 0.5, 0.5));
+    cudaStream_t s = hi.stream;
+    launch_make_rhs<double>(hi.d, hi.chunks[0].view(), hi.ctl, 0, s);
+    launch_defect(hi.d, lo.d, hi.tiles[0].view(), hi.ctl, hi.part, s);
+    int cur = 0;
+    lo.sweeps_fine(cur, sweeps, s);
+    launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur, s);
+    M1_CK(cudaGetLastError());
+    hi.dt_rhs[0] = dt;
+    hi.rhs_valid[0] = 1;
+    return M1_OK;
+}
+
 MixedModel::~MixedModel()
 {
     if (graph) cudaGraphExecDestroy(graph);
@@ -1037,15 +1289,6 @@ m1_status make_op_engine(const m1_grid_desc* desc, int lmax, const double* inflo
 }  // namespace m1
 
 using m1::Model;
-
-struct m1_grid {
-    std::unique_ptr<Model> model;
-};
-
-struct m1_batch {
-    std::unique_ptr<Model> model;
-    int count = 0;
-};
 
 extern "C" {
 

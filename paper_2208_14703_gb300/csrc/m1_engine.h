@@ -141,6 +141,12 @@ struct Engine {
     m1_status op_restrict(const double* state, const double* resid, double* cs, double* cr);
     m1_status op_prolong(const double* uc, const double* vc, const double* uf, double theta,
                          double* out, int* damped);
+    // serving
+    size_t slot_bytes(const m1_grid_desc& g) const;
+    m1_status set_init_lists(const std::vector<int>& slots);
+    m1_status copy_slot_in(int slot, Engine<R>& src);
+    m1_status copy_slot_out(int slot, Engine<R>& dst);
+    m1_status settle(int slot);
 };
 
 // One or more instances behind the C ABI: the plain FP64 engine, or the mixed
@@ -156,6 +162,22 @@ struct Model {
     virtual m1_status residual_norm(int i, double dt, double* out) = 0;
     virtual m1_status history(int i, double* hist, double* dtau, int len) = 0;
     virtual m1_status jacobi(int i, double dt, int sweeps) = 0;
+    virtual const m1_grid_desc& desc0() const = 0;
+    virtual int precision() const = 0;
+    // serving: slots added and removed between V-cycles of a running engine
+    virtual m1_status sv_init(int cap, int L, cudaStream_t s) = 0;
+    virtual size_t sv_bytes(const m1_grid_desc& d) const = 0;
+    virtual m1_status sv_add(const m1_grid_desc& d, int* slot) = 0;
+    virtual m1_status sv_remove(int slot) = 0;
+    virtual m1_status sv_rebuild() = 0;
+    virtual m1_status sv_copy_in(int slot, Model& src) = 0;
+    virtual m1_status sv_copy_out(int slot, Model& dst) = 0;
+    virtual m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
+                               const std::vector<m1_solve_params>& ps) = 0;
+    virtual m1_status sv_cycles(const Params& p, int n) = 0;
+    virtual m1_status sv_read(std::vector<Ctl>& out) = 0;
+    virtual m1_status sv_settle(int slot) = 0;
+    virtual int sv_graph_cycles() const { return 1; }   // V-cycles per graph launch
 };
 
 struct PlainModel : Model {
@@ -188,6 +210,21 @@ struct PlainModel : Model {
         return e.history(i, hs, dt, len);
     }
     m1_status jacobi(int i, double dt, int sweeps) override { return e.jacobi(i, dt, sweeps); }
+    const m1_grid_desc& desc0() const override { return e.desc[0]; }
+    int precision() const override { return M1_FP64; }
+    m1_status sv_init(int cap, int L, cudaStream_t s) override { return e.init(cap, L, false, s, 0); }
+    size_t sv_bytes(const m1_grid_desc& d) const override { return e.slot_bytes(d); }
+    m1_status sv_add(const m1_grid_desc& d, int* slot) override { return e.add_slot(d, slot); }
+    m1_status sv_remove(int slot) override { return e.remove_slot(slot); }
+    m1_status sv_rebuild() override { return e.rebuild(); }
+    m1_status sv_copy_in(int slot, Model& src) override;
+    m1_status sv_copy_out(int slot, Model& dst) override;
+    m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
+                       const std::vector<m1_solve_params>& ps) override;
+    m1_status sv_cycles(const Params& p, int n) override;
+    m1_status sv_read(std::vector<Ctl>& out) override;
+    m1_status sv_settle(int slot) override { return e.settle(slot); }
+    int sv_graph_cycles() const override { return e.graph_cycles; }
 };
 
 struct MixedModel : Model {
@@ -216,10 +253,34 @@ struct MixedModel : Model {
     {
         return hi.history(i, hs, dt, len);
     }
-    m1_status jacobi(int, double, int) override { return M1_ERR_INVALID_ARG; }
+    m1_status jacobi(int i, double dt, int sweeps) override;
+    const m1_grid_desc& desc0() const override { return lo.desc[0]; }
+    int precision() const override { return M1_MIXED; }
+    m1_status sv_init(int cap, int L, cudaStream_t s) override;
+    size_t sv_bytes(const m1_grid_desc& d) const override;
+    m1_status sv_add(const m1_grid_desc& d, int* slot) override;
+    m1_status sv_remove(int slot) override;
+    m1_status sv_rebuild() override;
+    m1_status sv_copy_in(int slot, Model& src) override;
+    m1_status sv_copy_out(int slot, Model& dst) override;
+    m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
+                       const std::vector<m1_solve_params>& ps) override;
+    m1_status sv_cycles(const Params& p, int n) override;
+    m1_status sv_read(std::vector<Ctl>& out) override;
+    m1_status sv_settle(int) override { return M1_OK; }
 };
 
 m1_status make_model(const std::vector<m1_grid_desc>& descs, cudaStream_t s,
                      std::unique_ptr<Model>& out);
 
 }  // namespace m1
+
+// The opaque handles of the C ABI.
+struct m1_grid {
+    std::unique_ptr<m1::Model> model;
+};
+
+struct m1_batch {
+    std::unique_ptr<m1::Model> model;
+    int count = 0;
+};

@@ -496,13 +496,15 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
                                                        const Level<R>* __restrict__ lv0,
                                                        const double* __restrict__ part,
                                                        const double* __restrict__ partb, int mode,
-                                                       int cur, BatchCtl* __restrict__ bctl)
+                                                       int cur, BatchCtl* __restrict__ bctl,
+                                                       const int* __restrict__ slot_ids)
 {
     __shared__ double red[kThreads];
-    Ctl* ctl = ctls + blockIdx.x;
+    const int slot = slot_ids ? slot_ids[blockIdx.x] : (int)blockIdx.x;
+    Ctl* ctl = ctls + slot;
     if (!ctl->active) return;
     if (mode == FIN_CYCLE && ctl->done) return;
-    const Level<R>* L = lv0 + blockIdx.x;
+    const Level<R>* L = lv0 + slot;
     const int off = L->part_off, np = L->tiles;
     const double s = block_reduce_fixed(part + off, np, red);
     double sb = 0.0;
@@ -773,9 +775,11 @@ void launch_make_rhs(const Level<R>* lv, WorkList wl, const Ctl* ctls, int buf, 
 
 template <typename R>
 void launch_finalize(Ctl* ctls, const Level<R>* lv0, int nslots, const double* part,
-                     const double* partb, int mode, int cur, BatchCtl* bctl, cudaStream_t s)
+                     const double* partb, int mode, int cur, BatchCtl* bctl, cudaStream_t s,
+                     const int* slot_ids)
 {
-    k_finalize<R><<<nslots, kThreads, 0, s>>>(ctls, lv0, part, partb, mode, cur, bctl);
+    if (nslots > 0)
+        k_finalize<R><<<nslots, kThreads, 0, s>>>(ctls, lv0, part, partb, mode, cur, bctl, slot_ids);
 }
 
 template <typename R>
@@ -832,7 +836,7 @@ void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, Work
                                     cudaStream_t, bool);                                           \
     template void launch_make_rhs<R>(const Level<R>*, WorkList, const Ctl*, int, cudaStream_t);   \
     template void launch_finalize<R>(Ctl*, const Level<R>*, int, const double*, const double*,    \
-                                     int, int, BatchCtl*, cudaStream_t);                           \
+                                     int, int, BatchCtl*, cudaStream_t, const int*);               \
     template void launch_pack_state<R>(const double*, const double*, const double*, const double*,\
                                        double, Cell4<R>*, int, cudaStream_t);                      \
     template void launch_unpack_state<R>(const Cell4<R>*, double*, double*, double*, double*, int,\

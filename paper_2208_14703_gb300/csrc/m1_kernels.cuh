@@ -30,7 +30,8 @@ template <typename R>
 void launch_make_rhs(const Level<R>* lv, WorkList wl, const Ctl* ctls, int buf, cudaStream_t s);
 template <typename R>
 void launch_finalize(Ctl* ctls, const Level<R>* lv0, int nslots, const double* part,
-                     const double* partb, int mode, int cur, BatchCtl* bctl, cudaStream_t s);
+                     const double* partb, int mode, int cur, BatchCtl* bctl, cudaStream_t s,
+                     const int* slot_ids = nullptr);
 template <typename R>
 void launch_pack_state(const double* E, const double* Fx, const double* Fy, const double* T,
                        double tscale, Cell4<R>* out, int n, cudaStream_t s);

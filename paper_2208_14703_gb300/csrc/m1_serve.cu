@@ -1,0 +1,350 @@
+// Serving: a request loop that runs implicit M1 steps of many simulations on one
+// GPU with continuous batching.
+//
+// A request is a caller's grid (its state already set) and a number of steps.
+// The scheduler thread admits queued requests in arrival order into free slots
+// of one engine while their level hierarchies fit the HBM budget (the state is
+// copied device to device; it stays resident for all of the request's steps),
+// and launches V-cycle graphs over every active slot.  Every two cycles it reads
+// the slots' control blocks: a slot whose step converged starts its next step
+// at once (or, after its last step, copies the result back into the caller's
+// grid and frees its slot and budget), and queued requests join between cycles.
+// Instances never share arithmetic, so a request's result is the same served
+// alone or in a mix.  Step latency is the host time from the start of a step to
+// the poll that sees it converged.
+#include <m1.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "m1_engine.h"
+
+namespace {
+
+using m1::Ctl;
+using m1::Model;
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    unsigned long long ticket = 0;
+    m1_grid* grid = nullptr;
+    int nsteps = 0;
+    double dt = 0.0;
+    m1_solve_params params{};
+    size_t bytes = 0;
+    int slot = -1;
+    int steps_done = 0;
+    int status = M1_PENDING;
+    bool finished = false;
+    double t_step = 0.0;
+    m1_step_stats last{};
+};
+
+}  // namespace
+
+struct m1_server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<unsigned long long, std::shared_ptr<Request>> reqs;
+    std::vector<std::shared_ptr<Request>> slot_req;
+    std::unique_ptr<Model> model;
+    m1::Params structure{};
+    int precision = 0, L = 0, max_slots = 0, device = 0;
+    size_t budget = 0, used = 0, peak = 0;
+    int poll_cycles = 2;
+    bool stop = false;
+    int error = M1_OK;
+    unsigned long long next_ticket = 1;
+    // statistics
+    std::vector<double> latencies_ms;
+    long long steps_done = 0, requests_done = 0, cycles = 0;
+    double t_first = 0.0, t_last = 0.0;
+    std::thread th;
+
+    void loop();
+    m1_status admit_and_start(std::vector<std::shared_ptr<Request>>& admit);
+    m1_status service_cycles();
+};
+
+m1_status m1_server::admit_and_start(std::vector<std::shared_ptr<Request>>& admit)
+{
+    std::vector<int> slots;
+    std::vector<double> dts;
+    std::vector<m1_solve_params> ps;
+    for (auto& r : admit) {
+        int slot = -1;
+        M1_TRY(model->sv_add(r->grid->model->desc0(), &slot));
+        r->slot = slot;
+        slot_req[slot] = r;
+    }
+    M1_TRY(model->sv_rebuild());
+    for (auto& r : admit) {
+        M1_TRY(model->sv_copy_in(r->slot, *r->grid->model));
+        slots.push_back(r->slot);
+        dts.push_back(r->dt);
+        ps.push_back(r->params);
+    }
+    M1_TRY(model->sv_begin(slots, dts, ps));
+    const double t = now_s();
+    for (auto& r : admit) r->t_step = t;
+    return M1_OK;
+}
+
+// A few V-cycles over every active slot, then the per-slot bookkeeping.
+m1_status m1_server::service_cycles()
+{
+    M1_TRY(model->sv_cycles(structure, poll_cycles));
+    std::vector<Ctl> ctl;
+    M1_TRY(model->sv_read(ctl));
+    const double t = now_s();
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        cycles += (long long)poll_cycles * model->sv_graph_cycles();
+    }
+    std::vector<int> restart;
+    std::vector<double> rdts;
+    std::vector<m1_solve_params> rps;
+    bool removed = false;
+    for (int s = 0; s < max_slots; ++s) {
+        auto r = slot_req[s];
+        if (!r || !ctl[s].active || !ctl[s].done) continue;
+        M1_TRY(model->sv_settle(s));
+        const Ctl& c = ctl[s];
+        m1_step_stats st{};
+        st.cycles = c.kappa;
+        st.res0 = c.res0;
+        st.res = c.kappa > 0 ? c.res : c.res0;
+        st.dtau_final = c.dtau;
+        st.sweeps = (long long)c.kappa * (L == 1 ? structure.nu0 : 2 * structure.nu0);
+        st.ms = 1e3 * (t - r->t_step);
+        st.status = c.status;
+        st.newton_fail = c.newton_fail;
+        st.damped = c.damped;
+        const bool ok = c.status == m1::CTL_OK;
+        bool last;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->last = st;
+            r->steps_done += 1;
+            latencies_ms.push_back(st.ms);
+            steps_done += 1;
+            t_last = t;
+            last = !ok || r->steps_done >= r->nsteps;
+        }
+        if (!last) {
+            restart.push_back(s);
+            rdts.push_back(r->dt);
+            rps.push_back(r->params);
+            continue;
+        }
+        M1_TRY(model->sv_copy_out(s, *r->grid->model));
+        M1_TRY(model->sv_remove(s));
+        removed = true;
+        slot_req[s].reset();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            used -= r->bytes;
+            r->status = ok ? M1_OK : M1_ERR_NOT_CONVERGED;
+            r->finished = true;
+            requests_done += 1;
+        }
+        cv_done.notify_all();
+    }
+    if (removed) M1_TRY(model->sv_rebuild());
+    if (!restart.empty()) {
+        M1_TRY(model->sv_begin(restart, rdts, rps));
+        const double t2 = now_s();
+        for (int s : restart) slot_req[s]->t_step = t2;
+    }
+    return M1_OK;
+}
+
+void m1_server::loop()
+{
+    cudaSetDevice(device);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> admit;
+        bool active = false;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            for (auto& r : slot_req) active = active || (bool)r;
+            if (stop && queue.empty() && !active) break;
+            // admission in arrival order while a slot is free and the budget allows
+            int free_slots = 0;
+            for (auto& r : slot_req) free_slots += r ? 0 : 1;
+            while (!queue.empty() && free_slots > 0 && used + queue.front()->bytes <= budget) {
+                auto r = queue.front();
+                queue.pop_front();
+                used += r->bytes;
+                peak = std::max(peak, used);
+                admit.push_back(r);
+                --free_slots;
+            }
+            if (admit.empty() && !active) {
+                cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+            if (t_first == 0.0) t_first = now_s();
+        }
+        m1_status st = M1_OK;
+        if (!admit.empty()) st = admit_and_start(admit);
+        if (st == M1_OK) st = service_cycles();
+        if (st != M1_OK) {
+            std::lock_guard<std::mutex> lk(mu);
+            error = st;
+            for (auto& kv : reqs)
+                if (!kv.second->finished) { kv.second->status = st; kv.second->finished = true; }
+            queue.clear();
+            stop = true;
+            cv_done.notify_all();
+            break;
+        }
+    }
+}
+
+extern "C" {
+
+m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int precision,
+                           const m1_solve_params* structure, void* cuda_stream, m1_server_t* out)
+{
+    if (!out || max_slots < 1 || lmax < 1 || lmax > 20 || hbm_budget_bytes == 0 ||
+        (precision != M1_FP64 && precision != M1_MIXED))
+        return M1_ERR_INVALID_ARG;
+    *out = nullptr;
+    m1_solve_params p;
+    if (structure) p = *structure; else m1_default_params(&p);
+    M1_TRY(m1::validate_params(p));
+    std::unique_ptr<m1_server> s(new m1_server());
+    if (precision == M1_MIXED) s->model.reset(new m1::MixedModel());
+    else s->model.reset(new m1::PlainModel());
+    M1_TRY(s->model->sv_init(max_slots, lmax, static_cast<cudaStream_t>(cuda_stream)));
+    s->structure = m1::Params{ p.nu0, p.nu_l, p.m_pseudo, p.m_coarse };
+    s->precision = precision;
+    s->L = lmax;
+    s->max_slots = max_slots;
+    s->budget = hbm_budget_bytes;
+    s->slot_req.assign(max_slots, nullptr);
+    cudaGetDevice(&s->device);
+    m1_server* raw = s.release();
+    raw->th = std::thread([raw] { raw->loop(); });
+    *out = raw;
+    return M1_OK;
+}
+
+m1_status m1_serve_submit(m1_server_t s, m1_grid_t g, int nsteps, double dt,
+                          const m1_solve_params* params, unsigned long long* ticket)
+{
+    if (!s || !g || !ticket || nsteps < 1 || !(dt > 0)) return M1_ERR_INVALID_ARG;
+    const m1_grid_desc& d = g->model->desc0();
+    if (g->model->precision() != s->precision || d.lmax != s->L) return M1_ERR_INVALID_ARG;
+    auto r = std::make_shared<Request>();
+    r->grid = g;
+    r->nsteps = nsteps;
+    r->dt = dt;
+    if (params) r->params = *params; else m1_default_params(&r->params);
+    M1_TRY(m1::validate_params(r->params));
+    if (r->params.nu0 != s->structure.nu0 || r->params.m_pseudo != s->structure.m ||
+        r->params.m_coarse != s->structure.mc)
+        return M1_ERR_INVALID_ARG;
+    r->bytes = s->model->sv_bytes(d);
+    if (r->bytes > s->budget) return M1_ERR_REJECTED;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return s->error != M1_OK ? (m1_status)s->error : M1_ERR_REJECTED;
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_all();
+    return M1_OK;
+}
+
+m1_status m1_serve_poll(m1_server_t s, unsigned long long ticket, int* steps_done,
+                        m1_step_stats* last)
+{
+    if (!s) return M1_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return M1_ERR_INVALID_ARG;
+    const Request& r = *it->second;
+    if (steps_done) *steps_done = r.steps_done;
+    if (last) *last = r.last;
+    return r.finished ? (m1_status)r.status : M1_PENDING;
+}
+
+m1_status m1_serve_wait(m1_server_t s, unsigned long long ticket, double timeout_s)
+{
+    if (!s) return M1_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return M1_ERR_INVALID_ARG;
+    auto r = it->second;
+    const bool done = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                          [&] { return r->finished; });
+    if (!done) return M1_ERR_TIMEOUT;
+    return (m1_status)r->status;
+}
+
+m1_status m1_server_get_stats(m1_server_t s, m1_server_stats* out)
+{
+    if (!s || !out) return M1_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    m1_server_stats st{};
+    st.requests_done = s->requests_done;
+    st.steps_done = s->steps_done;
+    st.cycles = s->cycles;
+    st.wall_s = s->t_last > s->t_first ? s->t_last - s->t_first : 0.0;
+    st.solves_per_s = st.wall_s > 0 ? s->steps_done / st.wall_s : 0.0;
+    st.bytes_in_use = (long long)s->used;
+    st.bytes_peak = (long long)s->peak;
+    int active = 0;
+    for (auto& r : s->slot_req) active += r ? 1 : 0;
+    st.active = active;
+    st.queued = (int)s->queue.size();
+    if (!s->latencies_ms.empty()) {
+        std::vector<double> v = s->latencies_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const double x = q * (double)(v.size() - 1);
+            const size_t i = (size_t)x;
+            const double f = x - (double)i;
+            return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+        };
+        st.p50_ms = pct(0.50);
+        st.p99_ms = pct(0.99);
+        double sum = 0.0;
+        for (double x : v) sum += x;
+        st.mean_ms = sum / (double)v.size();
+    }
+    *out = st;
+    return M1_OK;
+}
+
+m1_status m1_server_destroy(m1_server_t s)
+{
+    if (!s) return M1_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->th.joinable()) s->th.join();
+    const m1_status err = (m1_status)s->error;
+    delete s;
+    return err;
+}
+
+}  // extern "C"

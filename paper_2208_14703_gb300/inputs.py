@@ -218,3 +218,50 @@ def crop(case: dict, n: int) -> dict:
     if case.get("inflow") is not None:
         c["inflow"] = np.ascontiguousarray(case["inflow"][:, :, :n])
     return c
+
+
+def bump_case(dim: int, n: int, seed: int, cfl: float, lmax: int, tol: float) -> dict:
+    """One instance: E = 1e-2 + A exp(-|x - x0|^2 / w) with A ~ U[1, 100],
+    x0 ~ U[0.25, 0.75]^d, w ~ U[0.002, 0.02]; T = 1, F = 0; lognormal sigma_a,
+    sigma_s; 1D periodic, 2D reflecting walls; dt = cfl * h / c."""
+    u = uniform(seed, 4)
+    A, w = 1.0 + 99.0 * u[0], 0.002 + 0.018 * u[3]
+    x0, y0 = 0.25 + 0.5 * u[1], 0.25 + 0.5 * u[2]
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    if dim == 1:
+        E = 1e-2 + A * np.exp(-(x - x0) ** 2 / w)
+        return dict(desc=_desc(1, n, 1, 1.0, 1.0, ["periodic"] * 4), dt=cfl * h,
+                    state=_state(n, 1, E[None, :]), sa=lognormal_opacity(n, 1, 2 * seed + 1),
+                    ss=lognormal_opacity(n, 1, 2 * seed + 2), inflow=None, lmax=lmax, tol=tol)
+    X, Y = np.meshgrid(x, x)
+    E = 1e-2 + A * np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / w)
+    return dict(desc=_desc(2, n, n, 1.0, 1.0, ["reflect"] * 4), dt=cfl * h, state=_state(n, n, E),
+                sa=lognormal_opacity(n, n, 2 * seed + 1), ss=lognormal_opacity(n, n, 2 * seed + 2),
+                inflow=None, lmax=lmax, tol=tol)
+
+
+def serving_stream(count: int = 64, seed: int = 11, rate_hz: float = 20.0,
+                   sizes_1d=(256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536),
+                   sizes_2d=(128, 256, 512, 1024, 2048), steps=(10, 100),
+                   cfl_1d: float = 50.0, cfl_2d: float = 100.0, lmax: int = 5,
+                   tol: float = 1e-8) -> list:
+    """Requests of a Poisson arrival stream of simulations: exponential arrival
+    gaps of mean 1 / rate_hz (inverse transform of uniforms), 1D or 2D with
+    probability 1/2, the size uniform over the given set, the number of steps
+    uniform over [steps[0], steps[1]]; each request is a bump_case.  Returns
+    dicts {case, nsteps, arrival_s} in arrival order."""
+    u = uniform(seed, 4 * count).reshape(count, 4)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += -np.log1p(-u[k, 0]) / rate_hz
+        if u[k, 1] < 0.5:
+            n = int(sizes_1d[min(int(u[k, 2] * len(sizes_1d)), len(sizes_1d) - 1)])
+            case = bump_case(1, n, 7000 + k, cfl_1d, lmax, tol)
+        else:
+            n = int(sizes_2d[min(int(u[k, 2] * len(sizes_2d)), len(sizes_2d) - 1)])
+            case = bump_case(2, n, 7000 + k, cfl_2d, lmax, tol)
+        nsteps = steps[0] + min(int(u[k, 3] * (steps[1] - steps[0] + 1)), steps[1] - steps[0])
+        out.append(dict(case=case, nsteps=int(nsteps), arrival_s=t))
+    return out

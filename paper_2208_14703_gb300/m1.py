@@ -35,7 +35,8 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_step_history", "m1_jacobi", "m1_op_level", "m1_op_restrict", "m1_op_prolong_correct",
            "m1_residual_norm_noalloc", "m1_last_error", "m1_create_batch", "m1_destroy_batch",
            "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
-           "m1_batch_implicit_step"]
+           "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
+           "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy"]
 
 
 class M1Error(RuntimeError):
@@ -76,6 +77,18 @@ class StepStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_longlong), ("steps_done", ctypes.c_longlong),
+                ("cycles", ctypes.c_longlong), ("wall_s", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("active", ctypes.c_int), ("queued", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_longlong), ("bytes_peak", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _lib.m1_last_error.restype = ctypes.c_char_p
@@ -101,6 +114,15 @@ _lib.m1_batch_set_inflow.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, 
 _lib.m1_batch_get_state.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
 _lib.m1_batch_implicit_step.argtypes = [_vp, _dp, ctypes.POINTER(SolveParams),
                                         ctypes.POINTER(StepStats)]
+_lib.m1_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(SolveParams), _vp, ctypes.POINTER(_vp)]
+_lib.m1_serve_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_double,
+                                 ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_ulonglong)]
+_lib.m1_serve_poll.argtypes = [_vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(StepStats)]
+_lib.m1_serve_wait.argtypes = [_vp, ctypes.c_ulonglong, ctypes.c_double]
+_lib.m1_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+_lib.m1_server_destroy.argtypes = [_vp]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
@@ -160,7 +182,7 @@ class Grid:
         self.desc = desc
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             _lib.m1_destroy_grid(self.h)
             self.h = None
 
@@ -230,7 +252,7 @@ class Batch:
         self.descs = list(descs)
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             _lib.m1_destroy_batch(self.h)
             self.h = None
 
@@ -266,6 +288,59 @@ class Batch:
         _check(st, "m1_batch_implicit_step",
                allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return list(stats)
+
+
+class Server:
+    """Owner of one m1_server_t (continuous-batching request loop)."""
+
+    def __init__(self, budget_bytes, max_slots, lmax, precision=FP64, structure=None,
+                 stream=None):
+        h = _vp()
+        st = _lib.m1_server_create(int(budget_bytes), max_slots, lmax, precision,
+                                   ctypes.byref(structure) if structure else None, stream,
+                                   ctypes.byref(h))
+        _check(st, "m1_server_create")
+        self.h = h
+        self._held = {}   # grids in flight, kept alive until their tickets complete
+
+    def submit(self, grid: Grid, nsteps, dt, params: SolveParams | None = None):
+        t = ctypes.c_ulonglong()
+        st = _lib.m1_serve_submit(self.h, grid.h, nsteps, dt,
+                                  ctypes.byref(params) if params else None, ctypes.byref(t))
+        _check(st, "m1_serve_submit")
+        self._held[t.value] = grid
+        return t.value
+
+    def poll(self, ticket):
+        """(status, steps done, last step's StepStats); status PENDING while running."""
+        n = ctypes.c_int()
+        last = StepStats()
+        st = _lib.m1_serve_poll(self.h, ticket, ctypes.byref(n), ctypes.byref(last))
+        if st != PENDING:
+            self._held.pop(ticket, None)
+        return st, n.value, last
+
+    def wait(self, ticket, timeout_s=600.0):
+        st = _lib.m1_serve_wait(self.h, ticket, timeout_s)
+        if st != ERR_TIMEOUT:
+            self._held.pop(ticket, None)
+        return st
+
+    def stats(self):
+        out = ServerStats()
+        _check(_lib.m1_server_get_stats(self.h, ctypes.byref(out)), "m1_server_get_stats")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            st = _lib.m1_server_destroy(self.h)
+            self.h = None
+            _check(st, "m1_server_destroy")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.m1_server_destroy(self.h)
+            self.h = None
 
 
 def load_case(target, case, index=None):

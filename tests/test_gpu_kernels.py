@@ -147,6 +147,21 @@ def test_fp32_kernels_close_to_fp64_oracle(name, kw):
     _close(got, ref, 2e-5)
 
 
+@pytest.mark.parametrize("name,kw", CASES[:2] + CASES[4:5])
+def test_mixed_grid_jacobi_close_to_fp64_oracle(name, kw):
+    """Two Jacobi sweeps on a MIXED grid (FP32 sweeps of the correction equation
+    around the FP64 state, accumulated in FP64) against two FP64 oracle sweeps."""
+    case, g, desc, sig = _setup(kw, precision=m1.MIXED)
+    b = O.rhs_of(g, case["state"])
+    v1, _ = O.jacobi_sweep(g, case["dt"], case["sa"], case["ss"], b, case["state"])
+    ref, _ = O.jacobi_sweep(g, case["dt"], case["sa"], case["ss"], b, v1)
+    grid = m1.grid_from_case(case, lmax=1, precision=m1.MIXED)
+    grid.jacobi(case["dt"], 2)
+    got = np.stack(grid.get_state())
+    grid.close()
+    _close(got, ref, 2e-5)
+
+
 def test_full_size_sweep_matches_oracle():
     # the 1024^2 workload (lognormal opacities, hot square, reflecting walls):
     # one Jacobi sweep and one operator application over the whole grid
