@@ -235,7 +235,8 @@ def bench_serving(m1, reqs, stream, budget):
     server)."""
     out = {"requests": len(reqs), "steps": sum(r["nsteps"] for r in reqs),
            "sizes": sorted({(r["case"]["desc"]["dim"], r["case"]["desc"]["nx"]) for r in reqs}),
-           "arrival_span_s": reqs[-1]["arrival_s"], "budget_bytes": budget}
+           "arrival_span_s": reqs[-1]["arrival_s"], "budget_bytes": budget,
+           "dtau_rule": "signed (decrease of the residual norm)"}
     for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
         grids = [m1.grid_from_case(r["case"], precision=prec) for r in reqs]
         srv = m1.Server(budget, 64, reqs[0]["case"]["lmax"], prec, stream=stream.cuda_stream)
@@ -246,7 +247,8 @@ def bench_serving(m1, reqs, stream, budget):
             if delay > 0:
                 time.sleep(delay)
             tickets.append(srv.submit(g, r["nsteps"], r["case"]["dt"],
-                                      m1.m1_default_params(tol=r["case"]["tol"])))
+                                      m1.m1_default_params(tol=r["case"]["tol"],
+                                                           dtau_rule=m1.DTAU_SIGNED)))
         status = [srv.wait(t, 3600.0) for t in tickets]
         wall = time.perf_counter() - t0
         s = srv.stats()

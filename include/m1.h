@@ -77,11 +77,21 @@ typedef struct {
  * shrink 0.5 (Algorithm 4), eps_i = 1e-2, eps_d = 1e-4, tol = 1e-8 (relative to
  * the initial residual), dtau clamped to [1e-12, 1e6], theta_ex = 0.5 (fraction
  * of the admissible explicit pseudo-time step), theta_c = 0.5 (damping of an
- * inadmissible prolongated cell), max_cycles = 20000. */
+ * inadmissible prolongated cell), max_cycles = 20000, dtau_rule = M1_DTAU_ABS.
+ * dtau_rule selects the residual change that drives dtau after each cycle:
+ *   M1_DTAU_ABS     delta = | ||r_k|| - ||r_{k-1}|| | / ||r_0|| (as Algorithm 4
+ *                   prints it): a fast-growing residual also grows dtau;
+ *   M1_DTAU_SIGNED  delta = (||r_{k-1}|| - ||r_k||) / ||r_0||, the decrease (as
+ *                   Section 4 words the rule: increase dtau when the residual
+ *                   decreases fast enough, decrease it when it decreases slowly),
+ *                   so a growing residual halves dtau.
+ * Then dtau *= grow if delta > eps_i, dtau *= shrink if delta < eps_d. */
+enum { M1_DTAU_ABS = 0, M1_DTAU_SIGNED = 1 };
 typedef struct {
     int nu0, nu_l, m_pseudo, m_coarse;
     double dtau0, grow, shrink, eps_i, eps_d, tol, dtau_min, dtau_max, theta_ex, theta_c;
     int max_cycles;
+    int dtau_rule;
 } m1_solve_params;
 
 /* Statistics of one implicit step.  res0/res: ||r|| before the first and after

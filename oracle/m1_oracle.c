@@ -696,7 +696,8 @@ static int fine_jacobi(level_t* q, double dt, const double* b, double* u, int nu
 /* Appendix A, Algorithm 4: one implicit time step, v^n -> v^{n+1}.
  *
  * Parameters (ip / dp arrays, Section 5 defaults in parentheses):
- *   ip = { L_max, nu0 (3), nu_l (1), m (3), m_coarse (3), max_cycles, literal_fas }
+ *   ip = { L_max, nu0 (3), nu_l (1), m (3), m_coarse (3), max_cycles, literal_fas,
+ *          dtau_rule }
  *   dp = { dtau0 (1e-3), grow (1.1), shrink (0.5), eps_i, eps_d, tol,
  *          dtau_min, dtau_max, theta_ex (1/2), theta_c (1/2) }
  * The state v (4 planes) holds v^n on entry, v^{n+1} on return; b = (E^n, F^n,
@@ -711,6 +712,10 @@ static int fine_jacobi(level_t* q, double dt, const double* b, double* u, int nu
  *  - after the cycle r_kappa = b - A(v); stop when ||r_kappa|| <= tol ||r_0||;
  *    delta = | ||r_kappa|| - ||r_{kappa-1}|| | / ||r_0||; dtau *= grow if
  *    delta > eps_i, dtau *= shrink if delta < eps_d; clamp to [dtau_min, dtau_max].
+ *    dtau_rule = 1 takes the signed decrease delta = (||r_{kappa-1}|| - ||r_kappa||)
+ *    / ||r_0|| instead, the reading of the prose of Section 4 (increase when the
+ *    residual decreases fast enough, decrease when it decreases slowly), so that
+ *    a growing residual shrinks dtau; Algorithm 4 prints the absolute change.
  *  - literal_fas = 1 restricts and corrects the unsmoothed v_l instead (the
  *    letter of Algorithm 4), kept only for comparison.
  * Outputs: stats = { cycles, res0, res, dtau, fine_sweeps, status, newton_fail,
@@ -723,6 +728,7 @@ int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflo
 {
     grid_t g0; grid_from_desc(&g0, idesc, ddesc, inflow);
     int L = ip[0], nu0 = ip[1], nul = ip[2], m = ip[3], mc = ip[4], maxc = ip[5], literal = ip[6];
+    int signed_rule = ip[7];
     double dtau = dp[0], grow = dp[1], shrink = dp[2], eps_i = dp[3], eps_d = dp[4], tol = dp[5];
     double dtau_min = dp[6], dtau_max = dp[7], th_ex = dp[8], th_c = dp[9];
     size_t n0 = (size_t)g0.nx * g0.ny;
@@ -806,7 +812,7 @@ int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflo
             res_hist[kappa] = res;
             dtau_hist[kappa - 1] = dtau;
             if (res <= tol * res0) { status = 0; break; }
-            double delta = fabs(res - res_prev) / res0;
+            double delta = (signed_rule ? res_prev - res : fabs(res - res_prev)) / res0;
             if (delta > eps_i) dtau *= grow;
             if (delta < eps_d) dtau *= shrink;
             if (dtau < dtau_min) dtau = dtau_min;

@@ -233,6 +233,7 @@ class SolveParams:
     m_coarse: int = 3
     max_cycles: int = 20000
     literal_fas: int = 0
+    dtau_rule: int = 0
     dtau0: float = 1e-3
     grow: float = 1.1
     shrink: float = 0.5
@@ -246,7 +247,7 @@ class SolveParams:
 
     def arrays(self):
         ip = np.array([self.lmax, self.nu0, self.nu_l, self.m, self.m_coarse, self.max_cycles,
-                       self.literal_fas], dtype=np.int32)
+                       self.literal_fas, self.dtau_rule], dtype=np.int32)
         dp = np.array([self.dtau0, self.grow, self.shrink, self.eps_i, self.eps_d, self.tol,
                        self.dtau_min, self.dtau_max, self.theta_ex, self.theta_c])
         return ip, dp

@@ -93,7 +93,8 @@ m1_status validate_desc(const m1_grid_desc* d)
 m1_status validate_params(const m1_solve_params& sp)
 {
     if (sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 || sp.max_cycles < 1 ||
-        !(sp.tol >= 0) || !(sp.dtau0 > 0) || !(sp.theta_ex > 0) || !(sp.theta_c > 0))
+        !(sp.tol >= 0) || !(sp.dtau0 > 0) || !(sp.theta_ex > 0) || !(sp.theta_c > 0) ||
+        (sp.dtau_rule != M1_DTAU_ABS && sp.dtau_rule != M1_DTAU_SIGNED))
         return M1_ERR_INVALID_ARG;
     return M1_OK;
 }
@@ -104,6 +105,7 @@ Ctl make_ctl(const m1_solve_params& sp, double diag0)
     c.tol = sp.tol; c.grow = sp.grow; c.shrink = sp.shrink; c.eps_i = sp.eps_i;
     c.eps_d = sp.eps_d; c.dtau0 = sp.dtau0; c.dtau_min = sp.dtau_min; c.dtau_max = sp.dtau_max;
     c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
+    c.dtau_rule = sp.dtau_rule;
     c.res0_floor = 1e-14 * diag0;   // rounding floor of evaluating A
     c.active = 1;
     return c;
@@ -1301,6 +1303,7 @@ m1_status m1_default_params(m1_solve_params* p)
     p->dtau0 = 1e-3; p->grow = 1.1; p->shrink = 0.5; p->eps_i = 1e-2; p->eps_d = 1e-4;
     p->tol = 1e-8; p->dtau_min = 1e-12; p->dtau_max = 1e6; p->theta_ex = 0.5; p->theta_c = 0.5;
     p->max_cycles = 20000;
+    p->dtau_rule = M1_DTAU_ABS;
     return M1_OK;
 }
 

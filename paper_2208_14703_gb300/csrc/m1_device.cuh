@@ -65,6 +65,7 @@ struct Ctl {
     double tol, grow, shrink, eps_i, eps_d, dtau0, dtau_min, dtau_max, theta_ex, theta_c;
     double res0_floor;            // stop at once if ||r_0|| <= res0_floor ||b||
     int max_cycles, hist_len;
+    int dtau_rule;                // 0: |change| of the residual norm; 1: its decrease
     int active;                   // the instance takes part in the batch
     // state
     double res0, res, res_prev, bnorm, dtau;

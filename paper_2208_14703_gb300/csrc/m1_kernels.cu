@@ -527,7 +527,8 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
     if (kappa < ctl->hist_len) { ctl->hist[kappa] = res; ctl->dtau_hist[kappa - 1] = ctl->dtau; }
     ctl->result_buf = cur;
     if (res <= ctl->tol * ctl->res0) { mark_done(ctl, bctl, CTL_OK); return; }
-    const double delta = fabs(res - ctl->res_prev) / ctl->res0;
+    const double delta =
+        (ctl->dtau_rule ? ctl->res_prev - res : fabs(res - ctl->res_prev)) / ctl->res0;
     double dtau = ctl->dtau;
     if (delta > ctl->eps_i) dtau *= ctl->grow;
     if (delta < ctl->eps_d) dtau *= ctl->shrink;

@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "NONADMISSIBLE_INP
                 -4: "NOT_CONVERGED", -5: "CUDA", -6: "TIMEOUT", -7: "REJECTED"}
 BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
 FP64, MIXED = 0, 1
+DTAU_ABS, DTAU_SIGNED = 0, 1
 OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 
 EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
@@ -63,7 +64,8 @@ class SolveParams(ctypes.Structure):
                 ("eps_i", ctypes.c_double), ("eps_d", ctypes.c_double),
                 ("tol", ctypes.c_double), ("dtau_min", ctypes.c_double),
                 ("dtau_max", ctypes.c_double), ("theta_ex", ctypes.c_double),
-                ("theta_c", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+                ("theta_c", ctypes.c_double), ("max_cycles", ctypes.c_int),
+                ("dtau_rule", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):

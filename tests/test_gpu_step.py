@@ -139,6 +139,28 @@ def test_consecutive_steps_match_oracle():
     g.close()
 
 
+@pytest.mark.parametrize("rule", [0, 1])
+def test_dtau_rules_match_oracle_over_steps(rule):
+    """Five steps of the 1D bump whose fifth step runs away under the printed
+    dtau rule: per step the same cycle count and status as the oracle under
+    either rule (the printed rule's run-away step ends at max_cycles on both),
+    and the same state after the step the oracle converges."""
+    case = inputs.bump_case(1, 1024, 7001, 50.0, 4, 1e-8)
+    og = O.Grid.from_case(case)
+    g = m1.grid_from_case(case)
+    v = case["state"]
+    p = m1.m1_default_params(tol=1e-8, max_cycles=400, dtau_rule=rule)
+    for k in range(5):
+        v, ost, _, _ = O.implicit_step(og, case["dt"], case["sa"], case["ss"], v,
+                                       O.SolveParams(lmax=4, tol=1e-8, max_cycles=400,
+                                                     dtau_rule=rule))
+        st = g.implicit_step(case["dt"], p, allow_not_converged=True)
+        assert st.cycles == ost["cycles"] and st.status == ost["status"], k
+        if ost["status"] == 0:
+            assert max(rel_l2(np.stack(g.get_state()), v).values()) <= PARITY, k
+    g.close()
+
+
 def test_full_size_step_properties():
     # the 1024^2 FP64 workload with L_max = 8, tol 1e-8
     case = inputs.hot_square_2d(1024)

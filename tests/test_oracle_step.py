@@ -235,3 +235,47 @@ def test_inadmissible_input_is_rejected():
     _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], v,
                                   O.SolveParams(lmax=2))
     assert st["status"] == -2
+
+
+def _bump_steps(rule, nsteps=5):
+    """Five steps of a 1D bump (1024 cells, lognormal opacities, CFL 50, L_max 4)
+    whose fifth step makes the residual grow for many cycles under the printed
+    rule; returns the per-step stats and the last step's histories."""
+    case = inputs.bump_case(1, 1024, 7001, 50.0, 4, 1e-8)
+    g = O.Grid.from_case(case)
+    p = O.SolveParams(lmax=4, tol=1e-8, max_cycles=400, dtau_rule=rule)
+    v, out = case["state"], []
+    for _ in range(nsteps):
+        v, st, rh, dh = O.implicit_step(g, case["dt"], case["sa"], case["ss"], v, p)
+        out.append(st)
+    return out, np.asarray(rh), np.asarray(dh), p
+
+
+def test_dtau_rules_follow_their_wording():
+    """Algorithm 4 prints delta = |change of ||r|||; Section 4 words the rule as
+    the decrease (grow dtau when the residual decreases fast enough, shrink it
+    when it decreases slowly).  Pins on the recorded histories: under the
+    printed rule a cycle whose residual grew by more than eps_i ||r_0|| grows
+    dtau by 1.1 (up to the clamp); under the worded rule every cycle whose
+    residual grew halves dtau (down to the clamp).  With the printed rule the
+    fifth step runs away (the growth feeds itself) and reaches max_cycles; with
+    the worded rule every step converges."""
+    st0, rh, dh, p = _bump_steps(0)
+    assert [s["status"] for s in st0[:4]] == [0] * 4 and st0[4]["status"] == -4
+    k_last = int(st0[4]["cycles"])
+    fed = 0
+    for k in range(1, k_last):
+        if (rh[k] - rh[k - 1]) / rh[0] > p.eps_i:
+            assert dh[k] == pytest.approx(min(p.dtau_max, dh[k - 1] * p.grow), rel=1e-15)
+            fed += 1
+    assert fed > 10
+    st1, rh, dh, p = _bump_steps(1)
+    assert all(s["status"] == 0 for s in st1)
+    k_last = int(st1[4]["cycles"])
+    grew = 0
+    for k in range(1, k_last):
+        if rh[k] > rh[k - 1]:
+            assert dh[k] == pytest.approx(max(p.dtau_min, dh[k - 1] * p.shrink), rel=1e-15)
+            grew += 1
+    assert grew >= 1
+    assert st1[0]["cycles"] == st0[0]["cycles"]   # the rules agree while the residual falls
