@@ -142,6 +142,7 @@ std::vector<DevList*> Engine<R>::all_lists()
     std::vector<DevList*> v;
     for (auto& l : tiles) v.push_back(&l);
     for (auto& l : chunks) v.push_back(&l);
+    for (auto& l : strips) v.push_back(&l);
     v.push_back(&init_tiles);
     v.push_back(&init_chunks);
     return v;
@@ -180,6 +181,7 @@ m1_status Engine<R>::init(int capacity, int levels, bool correction_form, cudaSt
     last_cycles.assign(cap, 0);
     tiles.assign(L, DevList{});
     chunks.assign(L, DevList{});
+    strips.assign(L, DevList{});
     M1_TRY(calloc_common((void**)&d, sizeof(Level<R>) * L * cap));
     M1_TRY(calloc_common((void**)&ctl, sizeof(Ctl) * cap));
     M1_TRY(calloc_common((void**)&bctl, sizeof(BatchCtl)));
@@ -233,7 +235,13 @@ m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
         q.tiles = q.tiles_x * ((ny + q.ty - 1) / q.ty);
         q.chunks = (q.n + kThreads - 1) / kThreads;
         q.prof_len = std::max(nx, ny);
+        // strips of up to kStripH rows, shorter on small levels so that a
+        // level still spreads over enough warps (ny / 64 rows, at least one)
+        q.sh = g.dim == 2 ? std::max(1, std::min(kStripH, ny / 64)) : 1;
+        q.sx = (nx + kStripW - 1) / kStripW;
+        q.strips = q.sx * ((ny + q.sh - 1) / q.sh);
         q.c = (R)g.c; q.a_r = (R)g.a_r; q.c_v = (R)g.c_v;
+        q.ic2 = (R)(1.0 / (g.c * g.c));
         q.vol = g.dim == 2 ? hx * hy : hx;
         const size_t c4 = sizeof(Cell4<R>) * q.n;
         M1_TRY(slot_alloc(i, (void**)&q.v, c4));
@@ -355,13 +363,16 @@ m1_status Engine<R>::rebuild()
     for (int l = 0; l < L; ++l) {
         tiles[l].host.clear();
         chunks[l].host.clear();
+        strips[l].host.clear();
         for (int i = 0; i < cap; ++i) {
             if (!used[i]) continue;
             const Level<R>& q = h[(size_t)l * cap + i];
             for (int t = 0; t < q.tiles; ++t) tiles[l].host.push_back(make_int2(i, t));
+            for (int t = 0; t < q.strips; ++t) strips[l].host.push_back(make_int2(i, t));
             for (int c = 0; c < q.chunks; ++c) chunks[l].host.push_back(make_int2(i, c));
         }
         M1_TRY(upload_list(tiles[l]));
+        M1_TRY(upload_list(strips[l]));
         M1_TRY(upload_list(chunks[l]));
     }
     M1_CK(cudaMemcpyAsync(d, h.data(), sizeof(Level<R>) * h.size(), cudaMemcpyHostToDevice, stream));
@@ -518,7 +529,7 @@ template <typename R>
 void Engine<R>::sweeps_fine(int& cur, int count, cudaStream_t s)
 {
     for (int k = 0; k < count; ++k) {
-        launch_sweep<R>(d, tiles[0].view(), ctl, false, cur, 1 - cur, s, delta);
+        launch_sweep<R>(d, strips[0].view(), ctl, false, cur, 1 - cur, s, delta);
         cur = 1 - cur;
     }
 }
@@ -531,10 +542,10 @@ void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
     Level<R>* dl = d + (size_t)l * cap;
     for (int k = 0; k < m; ++k) {
         if (k == 0 && from_v) {
-            launch_sweep<R>(dl, tiles[l].view(), ctl, true, -1, 0, s, delta);
+            launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta);
             cur = 0;
         } else {
-            launch_sweep<R>(dl, tiles[l].view(), ctl, true, cur, 1 - cur, s, delta);
+            launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta);
             cur = 1 - cur;
         }
     }
@@ -821,7 +832,7 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
     case M1_OP_PSEUDO:
         M1_TRY(pack_planar(q.u[0], n, state));
         M1_TRY(pack_planar(q.f, n, rhs));
-        launch_sweep<R>(d, t0, ctl, mode == M1_OP_PSEUDO, 0, 1, stream);
+        launch_sweep<R>(d, strips[0].view(), ctl, mode == M1_OP_PSEUDO, 0, 1, stream);
         M1_CK(cudaGetLastError());
         return unpack_planar(q.u[1], n, out);
     default:

@@ -29,6 +29,12 @@ template <typename R> struct alignas(2 * sizeof(R)) Sig2 { R sa, ss; };
 // Tile shape of the stencil kernels: 256 threads, 32 x 8 cells in 2D, 256 x 1 in 1D.
 constexpr int kThreads = 256;
 constexpr int kTx2 = 32, kTy2 = 8, kTx1 = 256;
+// Warp strips of the Jacobi sweep: a warp's 32 lanes own 32 consecutive columns
+// (kStripW = 30 output columns and one halo column on each side) and march up
+// to kStripH rows (2D; one row in 1D).
+constexpr int kStripW = 30, kStripH = 16, kStripWarps = 2;
+// Blocks of a persistent strip launch: up to 16 resident 2-warp blocks per SM.
+constexpr int kStripBlocks = 152 * 16;
 constexpr int kHalo = (kTx2 + 2) * (kTy2 + 2) > (kTx1 + 2) ? (kTx2 + 2) * (kTy2 + 2) : (kTx1 + 2);
 
 // One grid level as the kernels see it.  Constants that depend on the time
@@ -41,7 +47,9 @@ struct Level {
     int chunks;                   // 256-cell chunks (cell-parallel kernels)
     int part_off;                 // first norm partial of this instance (level 0)
     int prof_len;                 // stride of the inflow profile table
+    int sx, sh, strips;           // warp strips: count along x, rows each, total
     R c, a_r, c_v;
+    R ic2;                        // 1 / c^2
     R ax, ay, bx, by;             // c dt / h and dt / (2 h) per axis (y: 0 in 1D)
     R diag;                       // 1 + ax + ay
     R cdt;                        // c dt
@@ -96,6 +104,54 @@ struct WorkList {
 constexpr int kPersistentBlocks = 152 * 4;
 
 // ---------------------------------------------------------------------------
+// Reciprocal and square root of the per-cell arithmetic.
+// FP64: a hardware estimate (PTX rcp.approx.ftz.f64, rsqrt.approx.ftz.f64;
+// relative error near 2^-22 or better) refined by Newton-Raphson iteration, the
+// textbook method for these functions: for r ~ 1/a, r <- r + r (1 - a r); for
+// y ~ 1/sqrt(a), y <- y + (y/2)(1 - a y^2); each step squares the relative
+// error, so two steps reach FP64 rounding (the result can differ from the
+// correctly rounded one in the last bit).  The square root is s = a y with one
+// correction s <- s + (y/2)(a - s^2).  Arguments are positive normal numbers.
+// FP32: the approximate hardware operations (rcp.approx.ftz.f32,
+// sqrt.approx.ftz.f32; about 1 ulp), the correction form keeping their error
+// relative to the correction.
+template <typename R> struct Fm;
+template <> struct Fm<double> {
+    __device__ static __forceinline__ double rcp(double a)
+    {
+        double r;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+        double e = fma(-a, r, 1.0);
+        r = fma(r, e, r);
+        e = fma(-a, r, 1.0);
+        return fma(r, e, r);
+    }
+    __device__ static __forceinline__ double sqrt(double a)
+    {
+        double y;
+        asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+        const double h = 0.5 * y;
+        y = fma(h, fma(-a * y, y, 1.0), y);
+        const double s = a * y;
+        return fma(0.5 * y, fma(-s, s, a), s);
+    }
+};
+template <> struct Fm<float> {
+    __device__ static __forceinline__ float rcp(float a)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+    __device__ static __forceinline__ float sqrt(float a)
+    {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Per-cell arithmetic.
 
 // M1 closure (Section 2.1, Eq. (5)) in the algebraically equivalent form
@@ -105,13 +161,13 @@ constexpr int kPersistentBlocks = 152 * 4;
 template <typename R>
 __device__ __forceinline__ void closure(R E, R Fx, R Fy, R inv_c2, R& Pxx, R& Pxy, R& Pyy)
 {
-    R iE = R(1) / E;
+    R iE = Fm<R>::rcp(E);
     R fx = Fx * iE, fy = Fy * iE;
     R f2 = (fx * fx + fy * fy) * inv_c2;
     f2 = f2 < R(1) ? f2 : R(1);
-    R s = sqrt(R(4) - R(3) * f2);
+    R s = Fm<R>::sqrt(R(4) - R(3) * f2);
     R iso = (s - R(1)) * (R(1) / R(3));
-    R q = R(3) / (R(2) + s) * inv_c2;
+    R q = R(3) * Fm<R>::rcp(R(2) + s) * inv_c2;
     Pxx = E * (iso + q * fx * fx);
     Pxy = E * (q * fx * fy);
     Pyy = E * (iso + q * fy * fy);
@@ -165,7 +221,7 @@ __device__ __forceinline__ float newton_quartic_f32(float C, float K, float Rr, 
         float T3 = T * T * T;
         float g = fmaf(K, T3 * T, C * T) - Rr;
         float dg = fmaf(4.0f * K, T3, C);
-        float dT = g / dg;
+        float dT = g * Fm<float>::rcp(dg);
         T -= dT;
         if (fabsf(dT) <= 4e-7f * T) { ok = true; break; }
     }
@@ -189,7 +245,7 @@ template <> struct Quartic<double> {
             double T3 = T * T * T;
             double g = fma(K, T3 * T, C * T) - Rr;
             double dg = fma(4.0 * K, T3, C);
-            dT = g * (double)(1.0f / (float)dg);
+            dT = g * (double)Fm<float>::rcp((float)dg);
             T -= dT;
             if (it >= 1 && fabs(dT) <= 1e-15 * T) break;
         }
@@ -212,7 +268,7 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
     Cell4<R> o;
     R A = w0 + w1 * diag;
     R k = w1 * ka;
-    R iF = R(1) / (w0 + w1 * (diag + kt));
+    R iF = Fm<R>::rcp(w0 + w1 * (diag + kt));
     o.Fx = bFx * iF;
     o.Fy = bFy * iF;
     R C = w0 + w1 * c_v;
@@ -222,7 +278,7 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
         o.E = bE / A;
         return o;
     }
-    R iAk = R(1) / (A + k);
+    R iAk = Fm<R>::rcp(A + k);
     R K = k * A * a_r * iAk;
     R Rr = bT + k * bE * iAk;
     R T = Quartic<R>::solve(C, K, Rr, ok);
@@ -250,7 +306,7 @@ __device__ __forceinline__ void closure_delta(R wE, R wFx, R wFy, R eE, R eFx, R
                                               R& dPxx, R& dPxy, R& dPyy)
 {
     const R E1 = wE + eE;
-    const R iE0 = R(1) / wE, iE1 = R(1) / E1;
+    const R iE0 = Fm<R>::rcp(wE), iE1 = Fm<R>::rcp(E1);
     const R px0 = wFx * iE0, py0 = wFy * iE0;
     const R dpx = (eFx - px0 * eE) * iE1, dpy = (eFy - py0 * eE) * iE1;
     const R px1 = px0 + dpx, py1 = py0 + dpy;
@@ -259,11 +315,12 @@ __device__ __forceinline__ void closure_delta(R wE, R wFx, R wFy, R eE, R eFx, R
     const R f21 = f20 + df2;
     const R c0 = f20 < R(1) ? f20 : R(1), c1 = f21 < R(1) ? f21 : R(1);
     const R dc = (f20 <= R(1) && f21 <= R(1)) ? df2 : c1 - c0;
-    const R s0 = sqrt(R(4) - R(3) * c0), s1 = sqrt(R(4) - R(3) * c1);
-    const R ds = R(-3) * dc / (s0 + s1);
+    const R s0 = Fm<R>::sqrt(R(4) - R(3) * c0), s1 = Fm<R>::sqrt(R(4) - R(3) * c1);
+    const R ds = R(-3) * dc * Fm<R>::rcp(s0 + s1);
     const R a1 = (s1 - R(1)) * (R(1) / R(3)), da = ds * (R(1) / R(3));
-    const R q0 = R(3) / (R(2) + s0);
-    const R dq = R(-3) * ds / ((R(2) + s0) * (R(2) + s1));
+    const R i20 = Fm<R>::rcp(R(2) + s0), i21 = Fm<R>::rcp(R(2) + s1);
+    const R q0 = R(3) * i20;
+    const R dq = R(-3) * ds * i20 * i21;
     const R iso = eE * a1 + wE * da;
     dPxx = iso + inv_c2 * (dq * E1 * px1 * px1 + q0 * (eE * px1 * px1 + wE * dpx * (px0 + px1)));
     dPyy = iso + inv_c2 * (dq * E1 * py1 * py1 + q0 * (eE * py1 * py1 + wE * dpy * (py0 + py1)));
@@ -293,7 +350,7 @@ __device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, 
     Cell4<R> o;
     const R A = w0 + w1 * diag;
     const R k = w1 * ka;
-    const R iF = R(1) / (w0 + w1 * (diag + kt));
+    const R iF = Fm<R>::rcp(w0 + w1 * (diag + kt));
     o.Fx = bFx * iF;
     o.Fy = bFy * iF;
     const R C = w0 + w1 * c_v;
@@ -303,7 +360,7 @@ __device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, 
         o.E = bE / A;
         return o;
     }
-    const R iAk = R(1) / (A + k);
+    const R iAk = Fm<R>::rcp(A + k);
     const R K = k * A * a_r * iAk;
     const R Rr = bT + k * bE * iAk;
     R x = R(0);
@@ -312,7 +369,7 @@ __device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, 
         const R Tx = T + x;
         const R h = C * x + K * quartic_delta(T, x) - Rr;
         const R dh = C + R(4) * K * Tx * Tx * Tx;
-        const R dx = h / dh;
+        const R dx = h * Fm<R>::rcp(dh);
         x -= dx;
         if (fabs(dx) <= R(1e-6) * fabs(x) || dx == R(0)) { ok = true; break; }
     }

@@ -76,6 +76,7 @@ struct Engine {
     Level<R>* d = nullptr;                  // device descriptors
     std::vector<std::vector<double>> prof;  // inflow profiles [level * cap + slot]
     std::vector<DevList> tiles, chunks;     // work lists per level
+    std::vector<DevList> strips;            // warp-strip lists per level (sweeps)
     DevList init_tiles, init_chunks;        // scratch lists for one slot
     int* init_slots = nullptr;
     Ctl* ctl = nullptr;                     // device control blocks [cap]

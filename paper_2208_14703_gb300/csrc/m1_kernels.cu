@@ -47,7 +47,7 @@ __device__ __forceinline__ void load_tile(const Level<R>& L, const Cell4<R>* __r
                                           int x0, int y0, Tile<R>& t)
 {
     const int hw = L.tx + 2, hh = L.dim == 2 ? L.ty + 2 : 1, oy = L.dim == 2 ? 1 : 0;
-    const R inv_c2 = R(1) / (L.c * L.c);
+    const R inv_c2 = L.ic2;
     for (int k = threadIdx.x; k < hw * hh; k += blockDim.x) {
         int hi = k % hw, hj = k / hw;
         int gi = x0 + hi - 1, gj = y0 + hj - oy;
@@ -115,76 +115,186 @@ __device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
 }
 
 // ---------------------------------------------------------------------------
-template <typename R, bool PSEUDO, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_sweep(const Level<R>* __restrict__ lv, WorkList wl,
-                                                    Ctl* __restrict__ ctls, int in_buf, int out_buf)
+// One cell of a warp strip as its neighbours need it: the state (or, in the
+// correction form, the correction e) and its closure P (or P(w + e) - P(w)),
+// plus the temperature the cell's own update needs (u.T; correction form: the
+// base w.T).
+template <typename R>
+struct Staged {
+    R E, Fx, Fy, Pxx, Pxy, Pyy, T;
+};
+
+// The loads behind a staged cell (issued one row ahead of their use).
+template <typename R>
+struct Raw {
+    Cell4<R> c, w;
+};
+
+template <typename R>
+__device__ __forceinline__ Staged<R> shfl_staged(const Staged<R>& v, int from)
 {
-    __shared__ Level<R> L;
-    __shared__ Tile<R> t;
+    Staged<R> o;
+    o.E = __shfl_sync(0xffffffffu, v.E, from);
+    o.Fx = __shfl_sync(0xffffffffu, v.Fx, from);
+    o.Fy = __shfl_sync(0xffffffffu, v.Fy, from);
+    o.Pxx = __shfl_sync(0xffffffffu, v.Pxx, from);
+    o.Pxy = __shfl_sync(0xffffffffu, v.Pxy, from);
+    o.Pyy = __shfl_sync(0xffffffffu, v.Pyy, from);
+    o.T = v.T;
+    return o;
+}
+
+// Cell (i, j) of state s (ghost rules of `fetch` outside the grid; `fast`:
+// the whole row of the warp lies inside, plain loads).
+template <typename R, bool DELTA>
+__device__ __forceinline__ Raw<R> load_raw(const Level<R>& L, const Cell4<R>* __restrict__ s, int i,
+                                           int j, bool fast)
+{
+    Raw<R> r;
+    const size_t k = (size_t)j * L.nx + i;
+    if (!DELTA) {
+        r.c = fast ? s[k] : fetch(L, s, i, j, KIND_STATE);
+    } else {
+        r.w = fast ? L.w[k] : fetch(L, L.w, i, j, KIND_STATE);
+        r.c = fast ? s[k] : fetch(L, s, i, j, KIND_DIFF);
+    }
+    return r;
+}
+
+template <typename R, bool DELTA>
+__device__ __forceinline__ Staged<R> stage_raw(const Level<R>& L, const Raw<R>& r)
+{
+    Staged<R> o;
+    o.E = r.c.E; o.Fx = r.c.Fx; o.Fy = r.c.Fy;
+    if (!DELTA) {
+        closure(r.c.E, r.c.Fx, r.c.Fy, L.ic2, o.Pxx, o.Pxy, o.Pyy);
+        o.T = r.c.T;
+    } else {
+        closure_delta(r.w.E, r.w.Fx, r.w.Fy, r.c.E, r.c.Fx, r.c.Fy, L.ic2, o.Pxx, o.Pxy, o.Pyy);
+        o.T = r.w.T;
+    }
+    return o;
+}
+
+// One Jacobi sweep (Algorithm 1) or one fused pseudo-time step (Eq. (30),
+// Algorithm 3) at one level for every listed (instance, strip).
+//
+// Each warp takes a strip of 30 columns x L.sh rows (1D: 30 cells): lane l owns
+// column x0 - 1 + l, and the warp marches up the rows keeping the staged rows
+// j - 1, j, j + 1 in registers (the loads of row j + 2 and of the next own
+// cells are issued before row j is updated); the west and east neighbours of a
+// lane are its neighbour lanes (warp shuffles), so every staged cell's closure
+// is evaluated once per strip (32/30 x (sh + 2)/sh evaluations per updated
+// cell) with no shared-memory tile and no block barrier.  Lanes 1..30 update
+// their cell.
+template <typename R, bool PSEUDO, bool DELTA = false>
+__global__ void __launch_bounds__(kStripWarps * 32) k_sweep(const Level<R>* __restrict__ lv,
+                                                            WorkList wl, Ctl* __restrict__ ctls,
+                                                            int in_buf, int out_buf)
+{
+    __shared__ Level<R> Ls[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<R>& L = Ls[wib];
     const int nw = *wl.count;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
         Ctl* ctl = ctls + it.x;
-        load_level(L, lv + it.x);
-        __syncthreads();
-        int x0, y0;
-        tile_origin(L, it.y, x0, y0);
-        const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-        load_tile<R, DELTA>(L, src, x0, y0, t);
-        __syncthreads();
-        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-        const int i = x0 + lx, j = y0 + ly;
-        if (i < L.nx && j < L.ny) {
-            const size_t k = (size_t)j * L.nx + i;
-            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
-            R NE, NFx, NFy;
-            neighbour_sum(L, t, ck, NE, NFx, NFy);
-            const Cell4<R> b = L.f[k];
-            const Sig2<R> sg = L.sig[k];
-            const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-            bool ok;
-            Cell4<R> out;
-            if (!PSEUDO) {
-                if (!DELTA)
-                    out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE,
-                                         b.Fx + NFx, b.Fy + NFy, b.T, ok);
-                else
-                    out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, L.w[k].T,
-                                               b.E + NE, b.Fx + NFx, b.Fy + NFy, b.T, ok);
-            } else {
-                // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit
-                // half: one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
-                // DELTA: u = w + e and the sweep updates the correction e.
-                const R dtau = (R)ctl->dtau;
-                const R theta = (R)ctl->theta_ex;
-                const Cell4<R> u = src[k];
-                if (!DELTA) {
-                    const R tau = limited_step(u, b, dtau, theta, L.c);
-                    out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
-                                         u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
-                                         u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
-                } else {
-                    // u = w + e and f = A(w) + g: the full-form step
-                    // u' + dtau A(u') = u + tau f reads, for the correction,
-                    // e' + dtau (A(w+e') - A(w)) = e + tau g + (tau - dtau) A(w);
-                    // the last term is zero wherever the step is not limited
-                    const Cell4<R> wb = L.w[k], aw = L.aw[k];
-                    const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
-                    const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
-                    const R tau = limited_step(full, ff, dtau, theta, L.c);
-                    const R lim = tau - dtau;
-                    out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
-                                               u.E + tau * b.E + lim * aw.E + dtau * NE,
-                                               u.Fx + tau * b.Fx + lim * aw.Fx + dtau * NFx,
-                                               u.Fy + tau * b.Fy + lim * aw.Fy + dtau * NFy,
-                                               u.T + tau * b.T + lim * aw.T, ok);
-                }
-            }
-            if (!ok) atomicAdd(&ctl->newton_fail, 1u);
-            L.u[out_buf][k] = out;
+        {
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(lv + it.x);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(&L);
+            for (int q = lane; q < (int)(sizeof(Level<R>) / 8); q += 32) dst[q] = src[q];
         }
-        __syncthreads();
+        __syncwarp();
+        const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
+        const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+        const int i = min(x0 - 1 + lane, nx);       // lanes past the east ghost repeat it
+        const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+        const bool own = lane >= 1 && lane <= kStripW && i < nx;
+        const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
+        const R c = L.c, bx = L.bx, by = L.by;
+        const int rows = min(L.sh, ny - y0);
+        Staged<R> prev{}, cur, next{};
+        Raw<R> rn{};
+        if (two_d) {
+            prev = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0 - 1, colfast && y0 >= 1));
+            rn = load_raw<R, DELTA>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
+        }
+        cur = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0, colfast));
+        size_t k = (size_t)y0 * nx + i;
+        Cell4<R> bn{};
+        Sig2<R> sn{};
+        if (own) { bn = L.f[k]; sn = L.sig[k]; }
+        for (int r = 0; r < rows; ++r, k += nx) {
+            const int j = y0 + r;
+            if (two_d) {
+                next = stage_raw<R, DELTA>(L, rn);
+                if (r + 1 < rows) rn = load_raw<R, DELTA>(L, src, i, j + 2, colfast && j + 2 < ny);
+            }
+            const Cell4<R> b = bn;
+            const Sig2<R> sg = sn;
+            if (own && r + 1 < rows) { bn = L.f[k + nx]; sn = L.sig[k + nx]; }
+            const Staged<R> wv = shfl_staged(cur, (lane + 31) & 31);
+            const Staged<R> ev = shfl_staged(cur, (lane + 1) & 31);
+            if (own) {
+                // neighbour operators L and R of Eq. (9): x faces, then y faces
+                R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
+                R NFx = c * bx * ((wv.Fx + ev.Fx) + c * (wv.Pxx - ev.Pxx));
+                R NFy = c * bx * ((wv.Fy + ev.Fy) + c * (wv.Pxy - ev.Pxy));
+                if (two_d) {
+                    NE += by * (c * (prev.E + next.E) + (prev.Fy - next.Fy));
+                    NFx += c * by * ((prev.Fx + next.Fx) + c * (prev.Pxy - next.Pxy));
+                    NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
+                }
+                const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+                bool ok;
+                Cell4<R> out;
+                if (!PSEUDO) {
+                    if (!DELTA)
+                        out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE,
+                                             b.Fx + NFx, b.Fy + NFy, b.T, ok);
+                    else
+                        out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r,
+                                                   cur.T, b.E + NE, b.Fx + NFx, b.Fy + NFy,
+                                                   b.T, ok);
+                } else {
+                    // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit
+                    // half: one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
+                    // DELTA: u = w + e and the sweep updates the correction e.
+                    const R dtau = (R)ctl->dtau;
+                    const R theta = (R)ctl->theta_ex;
+                    if (!DELTA) {
+                        const Cell4<R> u = { cur.E, cur.Fx, cur.Fy, cur.T };
+                        const R tau = limited_step(u, b, dtau, theta, c);
+                        out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
+                                             u.E + tau * b.E + dtau * NE,
+                                             u.Fx + tau * b.Fx + dtau * NFx,
+                                             u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+                    } else {
+                        // u = w + e and f = A(w) + g: the full-form step
+                        // u' + dtau A(u') = u + tau f reads, for the correction,
+                        // e' + dtau (A(w+e') - A(w)) = e + tau g + (tau - dtau) A(w);
+                        // the last term is zero wherever the step is not limited
+                        const Cell4<R> u = src[k];
+                        const Cell4<R> wb = L.w[k], aw = L.aw[k];
+                        const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
+                        const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
+                        const R tau = limited_step(full, ff, dtau, theta, c);
+                        const R lim = tau - dtau;
+                        out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
+                                                   u.E + tau * b.E + lim * aw.E + dtau * NE,
+                                                   u.Fx + tau * b.Fx + lim * aw.Fx + dtau * NFx,
+                                                   u.Fy + tau * b.Fy + lim * aw.Fy + dtau * NFy,
+                                                   u.T + tau * b.T + lim * aw.T, ok);
+                    }
+                }
+                if (!ok) atomicAdd(&ctl->newton_fail, 1u);
+                L.u[out_buf][k] = out;
+            }
+            prev = cur;
+            cur = next;
+        }
+        __syncwarp();
     }
 }
 
@@ -251,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
                 const Cell4<R> f = L.f[k];
                 Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
                 if (write_r) L.r[k] = r;
-                const double ic2 = 1.0 / ((double)L.c * (double)L.c);
+                const double ic2 = (double)L.ic2;
                 nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
                       (double)r.T * r.T;
             } else if (MODE == APPLY_FAS) {
@@ -636,7 +746,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __rest
             const double rFx = b.Fx - ((L.diag + kt) * u.Fx - NFx);
             const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
             const double rT = b.T - (L.c_v * u.T - se);
-            nrm = rE * rE + (rFx * rFx + rFy * rFy) / (L.c * L.c) + rT * rT;
+            nrm = rE * rE + (rFx * rFx + rFy * rFy) * L.ic2 + rT * rT;
             const Cell4<float> wb = { (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
             const Cell4<float> g = { (float)rE, (float)rFx, (float)rFy, (float)rT };
             const Cell4<float> z = { 0.f, 0.f, 0.f, 0.f };
@@ -699,18 +809,25 @@ static inline int pgrid(const WorkList& wl)
     return wl.capacity < kPersistentBlocks ? (wl.capacity > 0 ? wl.capacity : 1) : kPersistentBlocks;
 }
 
+// Blocks of a persistent launch over a list of warp items.
+static inline int pgrid_warps(const WorkList& wl)
+{
+    const int b = (wl.capacity + kStripWarps - 1) / kStripWarps;
+    return b < kStripBlocks ? (b > 0 ? b : 1) : kStripBlocks;
+}
+
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
                   int out_buf, cudaStream_t s, bool delta)
 {
-    const int g = pgrid(wl);
+    const int g = pgrid_warps(wl), t = kStripWarps * 32;
     if (delta && std::is_same<R, float>::value) {
-        if (pseudo) k_sweep<R, true, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
-        else k_sweep<R, false, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        if (pseudo) k_sweep<R, true, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        else k_sweep<R, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
         return;
     }
-    if (pseudo) k_sweep<R, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
-    else k_sweep<R, false><<<g, kThreads, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+    if (pseudo) k_sweep<R, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+    else k_sweep<R, false><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
 }
 
 template <typename R>

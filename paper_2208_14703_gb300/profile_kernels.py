@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--case", required=True, choices=["sweep64", "sweep32", "step64", "stepmixed"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--lmax", type=int, default=6)
+    ap.add_argument("--cycles", type=int, default=50, help="max_cycles of the step cases")
     args = ap.parse_args()
 
     from paper_2208_14703_gb300 import inputs, m1
@@ -34,7 +35,7 @@ def main():
     g = m1.grid_from_case(case, precision=m1.MIXED if mixed else m1.FP64)
     state = [np.ascontiguousarray(case["state"][k]) for k in range(4)]
     dt = case["dt"]
-    params = m1.m1_default_params(tol=case["tol"], max_cycles=50)
+    params = m1.m1_default_params(tol=case["tol"], max_cycles=args.cycles)
     for _ in range(2):                       # warm-up, then the profiled pass
         g.set_state(*state)
         if args.case.startswith("sweep"):
