@@ -263,6 +263,20 @@ def bench_serving(m1, reqs, stream, budget):
     return out
 
 
+def reduce_over_ranks(ms, units, device, world):
+    """Whole-job throughput of replicas: the slowest rank's time and the units
+    of all ranks (MAX and SUM all-reduces when world > 1).  Returns
+    (ms_max, units_sum, units_sum / seconds)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item(), u.item() / (t.item() * 1e-3)
+
+
 def run_reference(args, case):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -331,6 +345,8 @@ def main():
     # a dedicated (non-default) stream shared by the grid and the CUDA events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    # strip heights of the sweep kernels, tuned on this GPU (untimed)
+    tuning = m1.autotune(stream.cuda_stream)
     grid = m1.grid_from_case(case, stream=stream.cuda_stream)
     dev = torch.device("cuda", local)
     s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).to(dev) for k in range(4)]
@@ -377,12 +393,7 @@ def main():
     sweeps = [s.sweeps for s in stats]
     cycles = [s.cycles for s in stats]
     units = cells * sum(sweeps)
-    tmax = torch.tensor([ms_total], device=dev)
-    utot = torch.tensor([float(units)], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(utot, op=torch.distributed.ReduceOp.SUM)
-    value = utot.item() / (tmax.item() * 1e-3)
+    ms_max, _, value = reduce_over_ranks(ms_total, units, dev, world)
 
     # end to end through the C ABI with host buffers
     pin = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).pin_memory() for k in range(4)]
@@ -397,10 +408,7 @@ def main():
         grid.get_state([o.numpy() for o in outp])
         e2e_units += cells * st.sweeps
     te = time.perf_counter() - te
-    e2e_val = e2e_units / te
-    if world > 1:
-        t = torch.tensor([e2e_val * world], device=dev)
-        e2e_val = t.item()
+    _, _, e2e_val = reduce_over_ranks(1e3 * te, e2e_units, dev, world)
 
     pk = peaks()
     tflops = SWEEP_FLOPS * cells / (sweep64_ms * 1e-3) / 1e12
@@ -442,15 +450,17 @@ def main():
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tmax.item() / args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": cells, "lmax": case["lmax"],
                        "tol": case["tol"], "cfl": 100, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)",
-                       "reset": "v^n restored on the device before every step (timed)"},
+                       "reset": "v^n restored on the device before every step (timed)",
+                       "strip_rows": {f"{'fp64' if t['kind'] == 0 else 'fp32'}-{t['n']}": t["strip_rows"]
+                                      for t in tuning}},
             "cycles_per_step": cycles, "fine_sweeps_per_step": sweeps,
-            "steps_cells_per_s": cells * args.steps / (tmax.item() * 1e-3) * world,
+            "steps_cells_per_s": cells * args.steps / (ms_max * 1e-3) * world,
             "wall_s": wall,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,

@@ -226,6 +226,33 @@ m1_status m1_server_get_stats(m1_server_t s, m1_server_stats* out);
 /* Finishes every submitted request, then stops the scheduler and frees the engine. */
 m1_status m1_server_destroy(m1_server_t s);
 
+/* ---- autotuning of the sweep kernels' strip shape ----
+ * The Jacobi and pseudo-time sweeps (Algorithm 1, Algorithm 3) of a 2D level
+ * give each warp a strip of 30 columns and `strip_rows` rows.  m1_autotune
+ * times one sweep of a synthetic admissible n x n level (n = 16 .. 2048) for
+ * strip heights 1, 2, 4, 8, 16, 32, for FP64 (kind 0) and for the FP32
+ * correction form of the mixed path (kind 1), and keeps the fastest height per
+ * size class (grids of about the same cell count) in a process-wide table that
+ * grids, batches and servers created afterwards use.  Before any tuning the
+ * height is ny / 64 (between 1 and 16).  The height does not change any
+ * arithmetic: results are identical for every table.  Runs on `cuda_stream`
+ * (NULL: a stream of its own) and blocks; takes well under a second.  Writes up
+ * to max_entries entries (one per kind and size) to `out` and their count to
+ * *n_entries. */
+typedef struct {
+    int kind;            /* 0: FP64, 1: FP32 correction form */
+    int n;               /* level size n x n */
+    int strip_rows;      /* chosen height */
+    double ms;           /* time of one sweep at that height */
+    double ms_default;   /* time at the untuned height (NAN if not a candidate) */
+} m1_tune_entry;
+m1_status m1_autotune(void* cuda_stream, m1_tune_entry* out, int max_entries, int* n_entries);
+/* Installs entries (e.g. restored from an earlier m1_autotune); strip_rows = 0
+ * restores the default for that kind and size class. */
+m1_status m1_set_tuning(const m1_tune_entry* in, int n);
+/* The strip height a new nx x ny level of the given kind would take. */
+m1_status m1_strip_rows(int kind, int nx, int ny, int* rows);
+
 /* ---- single-kernel entry points (one kernel on caller data, for checks) ----
  * Stateless: each call allocates its own device buffers for `desc` (lmax is
  * ignored; precision selects FP64 or FP32 arithmetic), runs one kernel on the

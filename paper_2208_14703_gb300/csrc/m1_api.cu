@@ -235,9 +235,8 @@ m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
         q.tiles = q.tiles_x * ((ny + q.ty - 1) / q.ty);
         q.chunks = (q.n + kThreads - 1) / kThreads;
         q.prof_len = std::max(nx, ny);
-        // strips of up to kStripH rows, shorter on small levels so that a
-        // level still spreads over enough warps (ny / 64 rows, at least one)
-        q.sh = g.dim == 2 ? std::max(1, std::min(kStripH, ny / 64)) : 1;
+        // strip height: the autotuned value for this level size and precision
+        q.sh = g.dim == 2 ? strip_rows(sizeof(R) == 4 ? 1 : 0, nx, ny) : 1;
         q.sx = (nx + kStripW - 1) / kStripW;
         q.strips = q.sx * ((ny + q.sh - 1) / q.sh);
         q.c = (R)g.c; q.a_r = (R)g.a_r; q.c_v = (R)g.c_v;

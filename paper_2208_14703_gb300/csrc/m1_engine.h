@@ -54,6 +54,9 @@ struct DevList {
 };
 
 m1_status validate_desc(const m1_grid_desc* d);
+// Rows of a sweep strip for a 2D level (kind 0: FP64, 1: FP32), from the
+// autotuner's table (m1_tune.cu) or the default rule.
+int strip_rows(int kind, int nx, int ny);
 m1_status validate_params(const m1_solve_params& sp);
 Ctl make_ctl(const m1_solve_params& sp, double diag0);
 m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles,

@@ -37,7 +37,8 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_residual_norm_noalloc", "m1_last_error", "m1_create_batch", "m1_destroy_batch",
            "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
            "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
-           "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy"]
+           "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy", "m1_autotune",
+           "m1_set_tuning", "m1_strip_rows"]
 
 
 class M1Error(RuntimeError):
@@ -91,6 +92,14 @@ class ServerStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("strip_rows", ctypes.c_int),
+                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _lib.m1_last_error.restype = ctypes.c_char_p
@@ -125,6 +134,11 @@ _lib.m1_serve_poll.argtypes = [_vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_
 _lib.m1_serve_wait.argtypes = [_vp, ctypes.c_ulonglong, ctypes.c_double]
 _lib.m1_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
 _lib.m1_server_destroy.argtypes = [_vp]
+_lib.m1_autotune.argtypes = [_vp, ctypes.POINTER(TuneEntry), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)]
+_lib.m1_set_tuning.argtypes = [ctypes.POINTER(TuneEntry), ctypes.c_int]
+_lib.m1_strip_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int)]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
@@ -343,6 +357,29 @@ class Server:
         if getattr(self, "h", None):
             _lib.m1_server_destroy(self.h)
             self.h = None
+
+
+def autotune(stream=None):
+    """Run the strip-height autotuner; returns its entries as dicts."""
+    buf = (TuneEntry * 64)()
+    n = ctypes.c_int()
+    _check(_lib.m1_autotune(stream, buf, 64, ctypes.byref(n)), "m1_autotune")
+    return [buf[k].as_dict() for k in range(min(n.value, 64))]
+
+
+def set_tuning(entries):
+    """Install tuner entries (dicts with kind, n, strip_rows)."""
+    arr = (TuneEntry * max(1, len(entries)))()
+    for k, e in enumerate(entries):
+        arr[k] = TuneEntry(e["kind"], e["n"], e["strip_rows"], e.get("ms", 0.0),
+                           e.get("ms_default", 0.0))
+    _check(_lib.m1_set_tuning(arr, len(entries)), "m1_set_tuning")
+
+
+def strip_rows(kind, nx, ny):
+    r = ctypes.c_int()
+    _check(_lib.m1_strip_rows(kind, nx, ny, ctypes.byref(r)), "m1_strip_rows")
+    return r.value
 
 
 def load_case(target, case, index=None):
