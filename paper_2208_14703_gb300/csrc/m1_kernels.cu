@@ -114,18 +114,6 @@ __device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
     return ctls && (ctls[inst].done || !ctls[inst].active);
 }
 
-// Programmatic dependent launch: the V-cycle kernels are launched so that the
-// next kernel in the stream may be scheduled before this one ends.  Each waits
-// at its start until its predecessor has completed and its writes are visible
-// (griddepcontrol.wait) and only then lets its own successor be scheduled, so at
-// most one launch is in flight ahead of the running kernel and only launch
-// latency overlaps with work.
-__device__ __forceinline__ void dep_enter()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // ---------------------------------------------------------------------------
 // One cell of a warp strip as its neighbours need it: the state (or, in the
 // correction form, the correction e) and its closure P (or P(w + e) - P(w)),
@@ -204,7 +192,6 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep(const Level<R>* __re
                                                             WorkList wl, Ctl* __restrict__ ctls,
                                                             int in_buf, int out_buf)
 {
-    dep_enter();
     __shared__ Level<R> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<R>& L = Ls[wib];
@@ -330,7 +317,6 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
                                                     Ctl* __restrict__ ctls, int state_buf,
                                                     double* __restrict__ partials, int write_r)
 {
-    dep_enter();
     __shared__ Level<R> L;
     __shared__ Tile<R> t;
     __shared__ double red[kThreads / 32];
@@ -402,7 +388,6 @@ __global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restr
                                                          WorkList wl, const Ctl* __restrict__ ctls,
                                                          double* __restrict__ partials)
 {
-    dep_enter();
     __shared__ Level<R> L;
     __shared__ double red[kThreads / 32];
     const int nw = *wl.count;
@@ -437,7 +422,6 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
                                                        WorkList wl, Ctl* __restrict__ ctls,
                                                        int fine_buf)
 {
-    dep_enter();
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
     const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
@@ -482,7 +466,6 @@ template <typename R>
 __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>* __restrict__ lvc,
                                WorkList wl)
 {
-    dep_enter();
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
     const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
@@ -522,7 +505,6 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
                                                       WorkList wl, Ctl* __restrict__ ctls,
                                                       int coarse_buf, int fine_buf)
 {
-    dep_enter();
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
@@ -574,7 +556,6 @@ template <typename R>
 __global__ void k_make_rhs(const Level<R>* __restrict__ lv, WorkList wl,
                            const Ctl* __restrict__ ctls, int buf)
 {
-    dep_enter();
     __shared__ Level<R> L;
     const int nw = *wl.count;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
@@ -628,7 +609,6 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
                                                        int cur, BatchCtl* __restrict__ bctl,
                                                        const int* __restrict__ slot_ids)
 {
-    dep_enter();
     __shared__ double red[kThreads];
     const int slot = slot_ids ? slot_ids[blockIdx.x] : (int)blockIdx.x;
     Ctl* ctl = ctls + slot;
@@ -734,7 +714,6 @@ __global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __rest
                                                      WorkList wl, Ctl* __restrict__ ctls,
                                                      double* __restrict__ partials)
 {
-    dep_enter();
     __shared__ Level<double> L;
     __shared__ Level<float> M;
     __shared__ Tile<double> t;
@@ -789,7 +768,6 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
                                                          WorkList wl, Ctl* __restrict__ ctls,
                                                          int buf)
 {
-    dep_enter();
     __shared__ Level<double> L;
     __shared__ Level<float> M;
     const int nw = *wl.count;
@@ -831,23 +809,6 @@ static inline int pgrid(const WorkList& wl)
     return wl.capacity < kPersistentBlocks ? (wl.capacity > 0 ? wl.capacity : 1) : kPersistentBlocks;
 }
 
-// Launch with the programmatic-stream-serialization attribute (see dep_enter).
-template <typename... KArgs, typename... Args>
-static void launch_dep(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args)
-{
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 // Blocks of a persistent launch over a list of warp items.
 static inline int pgrid_warps(const WorkList& wl)
 {
@@ -861,12 +822,12 @@ void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int i
 {
     const int g = pgrid_warps(wl), t = kStripWarps * 32;
     if (delta && std::is_same<R, float>::value) {
-        if (pseudo) launch_dep(k_sweep<R, true, true>, g, t, s, lv, wl, ctls, in_buf, out_buf);
-        else launch_dep(k_sweep<R, false, true>, g, t, s, lv, wl, ctls, in_buf, out_buf);
+        if (pseudo) k_sweep<R, true, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        else k_sweep<R, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
         return;
     }
-    if (pseudo) launch_dep(k_sweep<R, true>, g, t, s, lv, wl, ctls, in_buf, out_buf);
-    else launch_dep(k_sweep<R, false>, g, t, s, lv, wl, ctls, in_buf, out_buf);
+    if (pseudo) k_sweep<R, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+    else k_sweep<R, false><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
 }
 
 template <typename R>
@@ -876,26 +837,26 @@ void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int stat
     const int g = pgrid(wl);
     if (delta && std::is_same<R, float>::value) {
         if (mode == APPLY_RESID)
-            launch_dep(k_apply<R, APPLY_RESID, true>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+            k_apply<R, APPLY_RESID, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         else if (mode == APPLY_FAS)
-            launch_dep(k_apply<R, APPLY_FAS, true>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+            k_apply<R, APPLY_FAS, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         else
-            launch_dep(k_apply<R, APPLY_A, true>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+            k_apply<R, APPLY_A, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
         return;
     }
     if (mode == APPLY_RESID)
-        launch_dep(k_apply<R, APPLY_RESID>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+        k_apply<R, APPLY_RESID><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
     else if (mode == APPLY_FAS)
-        launch_dep(k_apply<R, APPLY_FAS>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+        k_apply<R, APPLY_FAS><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
     else
-        launch_dep(k_apply<R, APPLY_A>, g, kThreads, s, lv, wl, ctls, state_buf, partials, write_r);
+        k_apply<R, APPLY_A><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
 }
 
 template <typename R>
 void launch_norm_state(const Level<R>* lv, WorkList wl, const Ctl* ctls, double* partials,
                        cudaStream_t s)
 {
-    launch_dep(k_norm_state<R>, pgrid(wl), kThreads, s, lv, wl, ctls, partials);
+    k_norm_state<R><<<pgrid(wl), kThreads, 0, s>>>(lv, wl, ctls, partials);
 }
 
 template <typename R>
@@ -903,15 +864,15 @@ void launch_restrict(const Level<R>* lvf, const Level<R>* lvc, WorkList wl, Ctl*
                      int fine_buf, cudaStream_t s, bool delta)
 {
     if (delta && std::is_same<R, float>::value)
-        launch_dep(k_restrict<R, true>, pgrid(wl), kThreads, s, lvf, lvc, wl, ctls, fine_buf);
+        k_restrict<R, true><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl, ctls, fine_buf);
     else
-        launch_dep(k_restrict<R>, pgrid(wl), kThreads, s, lvf, lvc, wl, ctls, fine_buf);
+        k_restrict<R><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl, ctls, fine_buf);
 }
 
 template <typename R>
 void launch_restrict_sig(const Level<R>* lvf, const Level<R>* lvc, WorkList wl, cudaStream_t s)
 {
-    launch_dep(k_restrict_sig<R>, pgrid(wl), kThreads, s, lvf, lvc, wl);
+    k_restrict_sig<R><<<pgrid(wl), kThreads, 0, s>>>(lvf, lvc, wl);
 }
 
 template <typename R>
@@ -919,15 +880,15 @@ void launch_prolong(const Level<R>* lvc, const Level<R>* lvf, WorkList wl, Ctl* 
                     int coarse_buf, int fine_buf, cudaStream_t s, bool delta)
 {
     if (delta && std::is_same<R, float>::value)
-        launch_dep(k_prolong<R, true>, pgrid(wl), kThreads, s, lvc, lvf, wl, ctls, coarse_buf, fine_buf);
+        k_prolong<R, true><<<pgrid(wl), kThreads, 0, s>>>(lvc, lvf, wl, ctls, coarse_buf, fine_buf);
     else
-        launch_dep(k_prolong<R>, pgrid(wl), kThreads, s, lvc, lvf, wl, ctls, coarse_buf, fine_buf);
+        k_prolong<R><<<pgrid(wl), kThreads, 0, s>>>(lvc, lvf, wl, ctls, coarse_buf, fine_buf);
 }
 
 template <typename R>
 void launch_make_rhs(const Level<R>* lv, WorkList wl, const Ctl* ctls, int buf, cudaStream_t s)
 {
-    launch_dep(k_make_rhs<R>, pgrid(wl), kThreads, s, lv, wl, ctls, buf);
+    k_make_rhs<R><<<pgrid(wl), kThreads, 0, s>>>(lv, wl, ctls, buf);
 }
 
 template <typename R>
@@ -936,7 +897,7 @@ void launch_finalize(Ctl* ctls, const Level<R>* lv0, int nslots, const double* p
                      const int* slot_ids)
 {
     if (nslots > 0)
-        launch_dep(k_finalize<R>, nslots, kThreads, s, ctls, lv0, part, partb, mode, cur, bctl, slot_ids);
+        k_finalize<R><<<nslots, kThreads, 0, s>>>(ctls, lv0, part, partb, mode, cur, bctl, slot_ids);
 }
 
 template <typename R>
@@ -969,13 +930,13 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
                    double* partials, cudaStream_t s)
 {
-    launch_dep(k_defect, pgrid(wl), kThreads, s, lv64, lv32, wl, ctls, partials);
+    k_defect<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, partials);
 }
 
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,
                        Ctl* ctls, int buf, cudaStream_t s)
 {
-    launch_dep(k_accumulate, pgrid(wl), kThreads, s, lv64, lv32, wl, ctls, buf);
+    k_accumulate<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, buf);
 }
 
 #define M1_INSTANTIATE(R)                                                                          \
