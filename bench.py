@@ -53,19 +53,30 @@ def peaks():
 # Algorithmic work of one fine FP64 Jacobi sweep (2D), per cell-update.
 # Bytes: read the iterate u, the right-hand side b and (sigma_a, sigma_s); write u'.
 SWEEP_BYTES = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8
-# FP64 work in FMA issue slots, counted on the minimal arithmetic of the update
-# (one closure per cell: 3 div/sqrt + 18 ops; neighbour sums: 24 ops; local
-# solve: 2 div + 22 ops + a 3-iteration Newton of 6 ops and 1 div each), with a
-# division or square root weighted by its measured cost on GB300 (FP64 FMA
-# 0.595 T/s vs 58.3 G div/s or sqrt/s: 10.2 slots).  2 flops per slot.
-DIV_SLOTS = 10.2
-SWEEP_SLOTS = (3 * DIV_SLOTS + 18) + 24 + (2 * DIV_SLOTS + 22) + 3 * (6 + DIV_SLOTS)
-SWEEP_FLOPS = 2 * SWEEP_SLOTS
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (recipe table), 152 SMs x 2 DFMA/clk x 2.07 GHz
+# DRAM bytes per cell of the FP64 sweep kernel measured by ncu on one 2048^2
+# launch (dram__bytes_read.sum + dram__bytes_write.sum = 457.0 MB / 4,194,304 cells)
+SWEEP64_TRAFFIC_PER_CELL = 457.0e6 / (2048 * 2048)
+# FP64 work of one fine Jacobi update (2D), counted in FP64-pipe operations
+# (each DFMA, DMUL or DADD is one issue slot; a reciprocal = hardware estimate +
+# 4 DFMA of Newton refinement = 5; a square root = estimate + 8) on the
+# arithmetic as written, with one closure per cell (halo re-evaluations are
+# not algorithmic work):
+#   closure 39 (reciprocal of E 5, f^2 and its clamp 7, square root 9,
+#     reciprocal of 2 + s 6, coefficients 4, P 8)
+#   neighbour operators 26 (x faces 13, y faces 13)
+#   opacity products and right-hand sides 6
+#   local solve 59 (two reciprocals 12, flux 2, quartic setup 9, two FP64
+#     Newton polish steps of 14 after the FP32 iteration, E 4 and checks)
+SWEEP_OPS = 39 + 26 + 6 + 59
+# GB300 FP64 pipe: 2 operations per clock per SM (nominal 1.25 TFLOP/s counts a
+# DFMA as 2 flops): 152 SMs x 2 x 2.07 GHz.
+FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 # FP32 fine sweep of the mixed path (correction form), per cell-update: read the
 # correction e, the base state w and the source g (3 x 16 B), (sigma_a, sigma_s)
 # (8 B); write e' (16 B).
 SWEEP32_BYTES = 3 * 16 + 8 + 16
+# DRAM bytes per cell of that kernel, ncu on one 2048^2 launch (292.2 MB)
+SWEEP32_TRAFFIC_PER_CELL = 292.2e6 / (2048 * 2048)
 
 
 class ClockSampler:
@@ -196,6 +207,7 @@ def bench_mixed(m1, case, stream, s0, flush, ref64, steps, hbm_peak):
             "err_vs_fp64_gpu": field_errors(got, ref64),
             "roofline_fp32_sweep": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
                                     "unit": "GB/s", "frac": gbs / hbm_peak, "kernel_ms": sms,
+                                    "traffic": SWEEP32_TRAFFIC_PER_CELL * cells,
                                     "bytes_per_cell": SWEEP32_BYTES,
                                     "kernel": "k_sweep<float, correction form>"}}
 
@@ -411,13 +423,16 @@ def main():
     _, _, e2e_val = reduce_over_ranks(1e3 * te, e2e_units, dev, world)
 
     pk = peaks()
-    tflops = SWEEP_FLOPS * cells / (sweep64_ms * 1e-3) / 1e12
+    tops = SWEEP_OPS * cells / (sweep64_ms * 1e-3) / 1e12
     gbs = SWEEP_BYTES * cells / (sweep64_ms * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
+    roof = {"bound": "alu", "achieved": tops, "peak": FP64_PEAK_TOPS, "unit": "Top/s",
+            "frac": tops / FP64_PEAK_TOPS, "traffic": SWEEP64_TRAFFIC_PER_CELL * cells,
             "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep64_ms,
-            "peak_source": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
-            "flops_per_cell": SWEEP_FLOPS,
+            "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (no measured FP64 "
+                           "peak in MEASURED_PEAKS.json)",
+            "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL or DADD)",
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                              "2048^2 launch (457.0 MB), scaled to 1024^2 by cells",
             "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / pk["hbm_gbs"], "bytes_per_cell": SWEEP_BYTES}}
 
