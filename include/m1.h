@@ -231,11 +231,13 @@ m1_status m1_server_destroy(m1_server_t s);
  * give each warp a strip of 30 columns and `strip_rows` rows.  m1_autotune
  * times one sweep of a synthetic admissible n x n level (n = 16 .. 2048) for
  * strip heights 1, 2, 4, 8, 16, 32, for FP64 (kind 0) and for the FP32
- * correction form of the mixed path (kind 1), and keeps the fastest height per
- * size class (grids of about the same cell count) in a process-wide table that
- * grids, batches and servers created afterwards use.  Before any tuning the
- * height is ny / 64 (between 1 and 16).  The height does not change any
- * arithmetic: results are identical for every table.  Runs on `cuda_stream`
+ * correction form of the mixed path (kind 1, also both row stagings), and keeps
+ * the fastest shape per size class (grids of about the same cell count) in a
+ * process-wide table that grids, batches and servers created afterwards use.
+ * Before any tuning the height is ny / 64 (between 1 and 16), registers.  The height does not change any
+ * arithmetic (results are bitwise identical for every height); the two FP32
+ * stagings are two kernels whose FP32 roundings may differ in the last bit, so
+ * mixed-precision results agree to rounding.  Runs on `cuda_stream`
  * (NULL: a stream of its own) and blocks; takes well under a second.  Writes up
  * to max_entries entries (one per kind and size) to `out` and their count to
  * *n_entries. */
@@ -243,8 +245,11 @@ typedef struct {
     int kind;            /* 0: FP64, 1: FP32 correction form */
     int n;               /* level size n x n */
     int strip_rows;      /* chosen height */
-    double ms;           /* time of one sweep at that height */
-    double ms_default;   /* time at the untuned height (NAN if not a candidate) */
+    int staging;         /* kind 1: 0 = rows loaded into registers one row ahead,
+                            1 = rows copied asynchronously into a shared-memory ring
+                            three rows ahead (fine-level sweeps); kind 0: 0 */
+    double ms;           /* time of one sweep with the chosen shape */
+    double ms_default;   /* time with the untuned shape (NAN if not a candidate) */
 } m1_tune_entry;
 m1_status m1_autotune(void* cuda_stream, m1_tune_entry* out, int max_entries, int* n_entries);
 /* Installs entries (e.g. restored from an earlier m1_autotune); strip_rows = 0

@@ -237,6 +237,7 @@ m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
         q.prof_len = std::max(nx, ny);
         // strip height: the autotuned value for this level size and precision
         q.sh = g.dim == 2 ? strip_rows(sizeof(R) == 4 ? 1 : 0, nx, ny) : 1;
+        q.ring = (sizeof(R) == 4 && delta && g.dim == 2) ? strip_ring(nx, ny) : 0;
         q.sx = (nx + kStripW - 1) / kStripW;
         q.strips = q.sx * ((ny + q.sh - 1) / q.sh);
         q.c = (R)g.c; q.a_r = (R)g.a_r; q.c_v = (R)g.c_v;
@@ -374,6 +375,13 @@ m1_status Engine<R>::rebuild()
         M1_TRY(upload_list(strips[l]));
         M1_TRY(upload_list(chunks[l]));
     }
+    // level-0 sweeps of all slots share one launch: the cp.async kernel when
+    // the slots holding most level-0 cells chose it
+    long long with = 0, without = 0;
+    for (int i = 0; i < cap; ++i)
+        if (used[i]) (h[i].ring ? with : without) += h[i].n;
+    const bool r0 = with > without;
+    if (r0 != ring0) { ring0 = r0; graph_dirty = true; }
     M1_CK(cudaMemcpyAsync(d, h.data(), sizeof(Level<R>) * h.size(), cudaMemcpyHostToDevice, stream));
     M1_CK(cudaStreamSynchronize(stream));
     return M1_OK;
@@ -528,7 +536,7 @@ template <typename R>
 void Engine<R>::sweeps_fine(int& cur, int count, cudaStream_t s)
 {
     for (int k = 0; k < count; ++k) {
-        launch_sweep<R>(d, strips[0].view(), ctl, false, cur, 1 - cur, s, delta);
+        launch_sweep<R>(d, strips[0].view(), ctl, false, cur, 1 - cur, s, delta, ring0);
         cur = 1 - cur;
     }
 }

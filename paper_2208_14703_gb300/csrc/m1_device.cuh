@@ -48,6 +48,7 @@ struct Level {
     int part_off;                 // first norm partial of this instance (level 0)
     int prof_len;                 // stride of the inflow profile table
     int sx, sh, strips;           // warp strips: count along x, rows each, total
+    int ring;                     // FP32 correction form: stage strip rows by cp.async
     R c, a_r, c_v;
     R ic2;                        // 1 / c^2
     R ax, ay, bx, by;             // c dt / h and dt / (2 h) per axis (y: 0 in 1D)

@@ -57,6 +57,9 @@ m1_status validate_desc(const m1_grid_desc* d);
 // Rows of a sweep strip for a 2D level (kind 0: FP64, 1: FP32), from the
 // autotuner's table (m1_tune.cu) or the default rule.
 int strip_rows(int kind, int nx, int ny);
+// Whether an FP32 correction-form level of this size stages its strip rows
+// through shared memory by asynchronous copies (autotuned; default: no).
+int strip_ring(int nx, int ny);
 m1_status validate_params(const m1_solve_params& sp);
 Ctl make_ctl(const m1_solve_params& sp, double diag0);
 m1_status run_until_done(cudaGraphExec_t graph, int graph_cycles, int max_cycles,
@@ -107,6 +110,7 @@ struct Engine {
     Params gparams{};
     int graph_cycles = 1;
     bool graph_dirty = true;
+    bool ring0 = false;                     // level-0 sweeps take the cp.async kernel
 
     ~Engine();
     std::vector<DevList*> all_lists();

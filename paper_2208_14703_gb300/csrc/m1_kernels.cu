@@ -176,17 +176,137 @@ __device__ __forceinline__ Staged<R> stage_raw(const Level<R>& L, const Raw<R>& 
     return o;
 }
 
+// The update of one strip cell (lanes 1..30): neighbour operators of Eq. (9)
+// from the staged west/east (shuffled) and south/north rows, then the local
+// solve of a Jacobi sweep (Algorithm 1) or of the fused pseudo-time step
+// (Eq. (30), Algorithm 3).  `u` is the cell's own iterate (the correction e in
+// the correction form) and `wb` its base state (correction form only).
+template <typename R, bool PSEUDO, bool DELTA>
+__device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const Staged<R>& wv,
+                                            const Staged<R>& ev, const Staged<R>& prev,
+                                            const Staged<R>& next, const Staged<R>& cur,
+                                            const Cell4<R>& b, const Sig2<R>& sg, size_t k,
+                                            int out_buf, bool two_d, const Cell4<R>& u,
+                                            const Cell4<R>& wb)
+{
+    const R c = L.c, bx = L.bx, by = L.by;
+    R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
+    R NFx = c * bx * ((wv.Fx + ev.Fx) + c * (wv.Pxx - ev.Pxx));
+    R NFy = c * bx * ((wv.Fy + ev.Fy) + c * (wv.Pxy - ev.Pxy));
+    if (two_d) {
+        NE += by * (c * (prev.E + next.E) + (prev.Fy - next.Fy));
+        NFx += c * by * ((prev.Fx + next.Fx) + c * (prev.Pxy - next.Pxy));
+        NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
+    }
+    const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+    bool ok;
+    Cell4<R> out;
+    if (!PSEUDO) {
+        if (!DELTA)
+            out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE, b.Fx + NFx,
+                                 b.Fy + NFy, b.T, ok);
+        else
+            out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, cur.T, b.E + NE,
+                                       b.Fx + NFx, b.Fy + NFy, b.T, ok);
+    } else {
+        // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit half:
+        // one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
+        const R dtau = (R)ctl->dtau;
+        const R theta = (R)ctl->theta_ex;
+        if (!DELTA) {
+            const R tau = limited_step(u, b, dtau, theta, c);
+            out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
+                                 u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
+                                 u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
+        } else {
+            // u = w + e and f = A(w) + g: the full-form step u' + dtau A(u') = u + tau f
+            // reads, for the correction,
+            // e' + dtau (A(w+e') - A(w)) = e + tau g + (tau - dtau) A(w);
+            // the last term is zero wherever the step is not limited
+            const Cell4<R> aw = L.aw[k];
+            const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
+            const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
+            const R tau = limited_step(full, ff, dtau, theta, c);
+            const R lim = tau - dtau;
+            out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
+                                       u.E + tau * b.E + lim * aw.E + dtau * NE,
+                                       u.Fx + tau * b.Fx + lim * aw.Fx + dtau * NFx,
+                                       u.Fy + tau * b.Fy + lim * aw.Fy + dtau * NFy,
+                                       u.T + tau * b.T + lim * aw.T, ok);
+        }
+    }
+    if (!ok) atomicAdd(&ctl->newton_fail, 1u);
+    L.u[out_buf][k] = out;
+}
+
 // One Jacobi sweep (Algorithm 1) or one fused pseudo-time step (Eq. (30),
-// Algorithm 3) at one level for every listed (instance, strip).
+// Algorithm 3) of one (instance, strip) item by one warp, loads into registers.
 //
-// Each warp takes a strip of 30 columns x L.sh rows (1D: 30 cells): lane l owns
+// The warp takes a strip of 30 columns x L.sh rows (1D: 30 cells): lane l owns
 // column x0 - 1 + l, and the warp marches up the rows keeping the staged rows
 // j - 1, j, j + 1 in registers (the loads of row j + 2 and of the next own
 // cells are issued before row j is updated); the west and east neighbours of a
 // lane are its neighbour lanes (warp shuffles), so every staged cell's closure
 // is evaluated once per strip (32/30 x (sh + 2)/sh evaluations per updated
 // cell) with no shared-memory tile and no block barrier.  Lanes 1..30 update
-// their cell.
+// their cell.  Ghost rows and columns follow the rules of `fetch`.
+template <typename R, bool PSEUDO, bool DELTA>
+__device__ __forceinline__ void strip_regs(const Level<R>& L, Ctl* ctl, int2 it, int lane,
+                                           const Cell4<R>* __restrict__ src, int out_buf)
+{
+    const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
+    const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+    const int i = min(x0 - 1 + lane, nx);       // lanes past the east ghost repeat it
+    const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const int rows = min(L.sh, ny - y0);
+    Staged<R> prev{}, cur, next{};
+    Raw<R> rn{};
+    if (two_d) {
+        prev = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0 - 1, colfast && y0 >= 1));
+        rn = load_raw<R, DELTA>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
+    }
+    cur = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0, colfast));
+    size_t k = (size_t)y0 * nx + i;
+    Cell4<R> bn{};
+    Sig2<R> sn{};
+    if (own) { bn = L.f[k]; sn = L.sig[k]; }
+    for (int r = 0; r < rows; ++r, k += nx) {
+        const int j = y0 + r;
+        if (two_d) {
+            next = stage_raw<R, DELTA>(L, rn);
+            if (r + 1 < rows) rn = load_raw<R, DELTA>(L, src, i, j + 2, colfast && j + 2 < ny);
+        }
+        const Cell4<R> b = bn;
+        const Sig2<R> sg = sn;
+        if (own && r + 1 < rows) { bn = L.f[k + nx]; sn = L.sig[k + nx]; }
+        const Staged<R> wv = shfl_staged(cur, (lane + 31) & 31);
+        const Staged<R> ev = shfl_staged(cur, (lane + 1) & 31);
+        if (own) {
+            Cell4<R> u{}, wb{};
+            if (PSEUDO) {
+                if (!DELTA) { u = Cell4<R>{ cur.E, cur.Fx, cur.Fy, cur.T }; }
+                else { u = src[k]; wb = L.w[k]; }
+            }
+            update_cell<R, PSEUDO, DELTA>(L, ctl, wv, ev, prev, next, cur, b, sg, k, out_buf,
+                                          two_d, u, wb);
+        }
+        prev = cur;
+        cur = next;
+    }
+}
+
+// Copy the per-warp Level descriptor of item `inst` into shared memory.
+template <typename R>
+__device__ __forceinline__ void load_level_warp(Level<R>& L, const Level<R>* src, int lane)
+{
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&L);
+    for (int q = lane; q < (int)(sizeof(Level<R>) / 8); q += 32) d[q] = s[q];
+    __syncwarp();
+}
+
+// Persistent sweep over every listed (instance, strip): one warp per item.
 template <typename R, bool PSEUDO, bool DELTA = false>
 __global__ void __launch_bounds__(kStripWarps * 32) k_sweep(const Level<R>* __restrict__ lv,
                                                             WorkList wl, Ctl* __restrict__ ctls,
@@ -199,101 +319,158 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep(const Level<R>* __re
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        Ctl* ctl = ctls + it.x;
-        {
-            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(lv + it.x);
-            unsigned long long* dst = reinterpret_cast<unsigned long long*>(&L);
-            for (int q = lane; q < (int)(sizeof(Level<R>) / 8); q += 32) dst[q] = src[q];
-        }
-        __syncwarp();
-        const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
-        const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
-        const int i = min(x0 - 1 + lane, nx);       // lanes past the east ghost repeat it
-        const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
-        const bool own = lane >= 1 && lane <= kStripW && i < nx;
+        load_level_warp(L, lv + it.x, lane);
         const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-        const R c = L.c, bx = L.bx, by = L.by;
-        const int rows = min(L.sh, ny - y0);
-        Staged<R> prev{}, cur, next{};
-        Raw<R> rn{};
-        if (two_d) {
-            prev = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0 - 1, colfast && y0 >= 1));
-            rn = load_raw<R, DELTA>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
-        }
-        cur = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0, colfast));
-        size_t k = (size_t)y0 * nx + i;
-        Cell4<R> bn{};
-        Sig2<R> sn{};
-        if (own) { bn = L.f[k]; sn = L.sig[k]; }
-        for (int r = 0; r < rows; ++r, k += nx) {
-            const int j = y0 + r;
-            if (two_d) {
-                next = stage_raw<R, DELTA>(L, rn);
-                if (r + 1 < rows) rn = load_raw<R, DELTA>(L, src, i, j + 2, colfast && j + 2 < ny);
-            }
-            const Cell4<R> b = bn;
-            const Sig2<R> sg = sn;
-            if (own && r + 1 < rows) { bn = L.f[k + nx]; sn = L.sig[k + nx]; }
-            const Staged<R> wv = shfl_staged(cur, (lane + 31) & 31);
-            const Staged<R> ev = shfl_staged(cur, (lane + 1) & 31);
+        strip_regs<R, PSEUDO, DELTA>(L, ctls + it.x, it, lane, src, out_buf);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 correction-form sweep with the strip rows staged through shared memory
+// by asynchronous copies (cp.async), kRing - 1 rows ahead of their use, so that
+// the loads of three rows are in flight per warp without holding registers.
+// Cells outside the grid (ghost rows and columns) are filled by `fetch` with
+// the wall rules and stored into the ring directly.
+constexpr int kRing = 4;
+
+struct RowSlot32 {
+    Cell4<float> w[32], e[32], f[32];
+    Sig2<float> sig[32];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Row q of the strip (lane's column i) into a ring slot: asynchronous copies of
+// w, e and, for the lane's own cell, f and sigma; a cell outside the grid is
+// fetched with the wall rules and stored directly.  Rows past `last` are not
+// needed and leave an empty copy group.
+__device__ __forceinline__ void issue_row32(const Level<float>& L,
+                                            const Cell4<float>* __restrict__ src, RowSlot32& S,
+                                            int i, int q, int last, int lane, bool own)
+{
+    if (q <= last) {
+        if (q >= 0 && q < L.ny && i >= 0 && i < L.nx) {
+            const size_t k = (size_t)q * L.nx + i;
+            cp_async16(&S.w[lane], L.w + k);
+            cp_async16(&S.e[lane], src + k);
             if (own) {
-                // neighbour operators L and R of Eq. (9): x faces, then y faces
-                R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
-                R NFx = c * bx * ((wv.Fx + ev.Fx) + c * (wv.Pxx - ev.Pxx));
-                R NFy = c * bx * ((wv.Fy + ev.Fy) + c * (wv.Pxy - ev.Pxy));
-                if (two_d) {
-                    NE += by * (c * (prev.E + next.E) + (prev.Fy - next.Fy));
-                    NFx += c * by * ((prev.Fx + next.Fx) + c * (prev.Pxy - next.Pxy));
-                    NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
-                }
-                const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-                bool ok;
-                Cell4<R> out;
-                if (!PSEUDO) {
-                    if (!DELTA)
-                        out = local_solve<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r, b.E + NE,
-                                             b.Fx + NFx, b.Fy + NFy, b.T, ok);
-                    else
-                        out = local_solve_delta<R>(R(0), R(1), L.diag, ka, kt, L.c_v, L.a_r,
-                                                   cur.T, b.E + NE, b.Fx + NFx, b.Fy + NFy,
-                                                   b.T, ok);
-                } else {
-                    // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit
-                    // half: one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
-                    // DELTA: u = w + e and the sweep updates the correction e.
-                    const R dtau = (R)ctl->dtau;
-                    const R theta = (R)ctl->theta_ex;
-                    if (!DELTA) {
-                        const Cell4<R> u = { cur.E, cur.Fx, cur.Fy, cur.T };
-                        const R tau = limited_step(u, b, dtau, theta, c);
-                        out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
-                                             u.E + tau * b.E + dtau * NE,
-                                             u.Fx + tau * b.Fx + dtau * NFx,
-                                             u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
-                    } else {
-                        // u = w + e and f = A(w) + g: the full-form step
-                        // u' + dtau A(u') = u + tau f reads, for the correction,
-                        // e' + dtau (A(w+e') - A(w)) = e + tau g + (tau - dtau) A(w);
-                        // the last term is zero wherever the step is not limited
-                        const Cell4<R> u = src[k];
-                        const Cell4<R> wb = L.w[k], aw = L.aw[k];
-                        const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
-                        const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
-                        const R tau = limited_step(full, ff, dtau, theta, c);
-                        const R lim = tau - dtau;
-                        out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
-                                                   u.E + tau * b.E + lim * aw.E + dtau * NE,
-                                                   u.Fx + tau * b.Fx + lim * aw.Fx + dtau * NFx,
-                                                   u.Fy + tau * b.Fy + lim * aw.Fy + dtau * NFy,
-                                                   u.T + tau * b.T + lim * aw.T, ok);
-                    }
-                }
-                if (!ok) atomicAdd(&ctl->newton_fail, 1u);
-                L.u[out_buf][k] = out;
+                cp_async16(&S.f[lane], L.f + k);
+                cp_async8(&S.sig[lane], L.sig + k);
             }
-            prev = cur;
-            cur = next;
+        } else {
+            S.w[lane] = fetch(L, L.w, i, q, KIND_STATE);
+            S.e[lane] = fetch(L, src, i, q, KIND_DIFF);
         }
+    }
+    cp_commit();
+}
+
+// The 1D form of a strip (one row of 30 updated cells, no y neighbours).
+template <bool PSEUDO>
+__device__ __forceinline__ void row_1d32(const Level<float>& L, Ctl* ctl, int2 it, int lane,
+                                         const Cell4<float>* __restrict__ src, int out_buf)
+{
+    const int nx = L.nx;
+    const int x0 = it.y * kStripW;
+    const int i = min(x0 - 1 + lane, nx);
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const bool fast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const Staged<float> cur = stage_raw<float, true>(L, load_raw<float, true>(L, src, i, 0, fast));
+    const Staged<float> wv = shfl_staged(cur, (lane + 31) & 31);
+    const Staged<float> ev = shfl_staged(cur, (lane + 1) & 31);
+    if (own) {
+        const size_t k = (size_t)i;
+        Cell4<float> u{}, wb{};
+        if (PSEUDO) { u = src[k]; wb = L.w[k]; }
+        update_cell<float, PSEUDO, true>(L, ctl, wv, ev, cur, cur, cur, L.f[k], L.sig[k], k,
+                                         out_buf, false, u, wb);
+    }
+}
+
+template <bool PSEUDO>
+__device__ __forceinline__ void strip_ring32(const Level<float>& L, Ctl* ctl, int2 it, int lane,
+                                             const Cell4<float>* __restrict__ src, int out_buf,
+                                             RowSlot32* ring)
+{
+    const int nx = L.nx, ny = L.ny;
+    const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+    const int i = min(x0 - 1 + lane, nx);       // lanes past the east ghost repeat it
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const int rows = min(L.sh, ny - y0);
+    const int last = y0 + rows;               // the last row the strip reads
+    // ring slot of row q: (q - y0 + 1) mod kRing
+    for (int q = y0 - 1; q <= y0 + 2; ++q) issue_row32(L, src, ring[(q - y0 + 1) & 3], i, q, last,
+                                                       lane, own);
+    cp_wait<2>();                             // rows y0 - 1 and y0
+    auto stage = [&](const RowSlot32& S) {
+        Raw<float> r;
+        r.w = S.w[lane];
+        r.c = S.e[lane];
+        return stage_raw<float, true>(L, r);
+    };
+    Staged<float> prev = stage(ring[0]), cur = stage(ring[1]), next{};
+    size_t k = (size_t)y0 * nx + i;
+    for (int r = 0; r < rows; ++r, k += nx) {
+        cp_wait<1>();                         // row j + 1
+        next = stage(ring[(r + 2) & 3]);
+        issue_row32(L, src, ring[r & 3], i, y0 + r + 3, last, lane, own);
+        const Staged<float> wv = shfl_staged(cur, (lane + 31) & 31);
+        const Staged<float> ev = shfl_staged(cur, (lane + 1) & 31);
+        if (own) {
+            const RowSlot32& S = ring[(r + 1) & 3];
+            const Cell4<float> b = S.f[lane];
+            const Sig2<float> sg = S.sig[lane];
+            Cell4<float> u{}, wb{};
+            if (PSEUDO) { u = S.e[lane]; wb = S.w[lane]; }
+            update_cell<float, PSEUDO, true>(L, ctl, wv, ev, prev, next, cur, b, sg, k, out_buf,
+                                             true, u, wb);
+        }
+        prev = cur;
+        cur = next;
+    }
+    cp_wait<0>();                             // no copy outlives the item
+}
+
+template <bool PSEUDO>
+__global__ void __launch_bounds__(kStripWarps * 32) k_sweep_ring32(const Level<float>* __restrict__ lv,
+                                                                   WorkList wl,
+                                                                   Ctl* __restrict__ ctls,
+                                                                   int in_buf, int out_buf)
+{
+    __shared__ Level<float> Ls[kStripWarps];
+    __shared__ RowSlot32 ring[kStripWarps][kRing];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<float>& L = Ls[wib];
+    const int nw = *wl.count;
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        load_level_warp(L, lv + it.x, lane);
+        const Cell4<float>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
+        if (L.dim == 2) strip_ring32<PSEUDO>(L, ctls + it.x, it, lane, src, out_buf, ring[wib]);
+        else row_1d32<PSEUDO>(L, ctls + it.x, it, lane, src, out_buf);
         __syncwarp();
     }
 }
@@ -818,10 +995,17 @@ static inline int pgrid_warps(const WorkList& wl)
 
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
-                  int out_buf, cudaStream_t s, bool delta)
+                  int out_buf, cudaStream_t s, bool delta, bool ring)
 {
     const int g = pgrid_warps(wl), t = kStripWarps * 32;
-    if (delta && std::is_same<R, float>::value) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (delta && ring) {
+            if (pseudo) k_sweep_ring32<true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+            else k_sweep_ring32<false><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+            return;
+        }
+    }
+    if (delta) {
         if (pseudo) k_sweep<R, true, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
         else k_sweep<R, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
         return;
@@ -941,7 +1125,7 @@ void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, Work
 
 #define M1_INSTANTIATE(R)                                                                          \
     template void launch_sweep<R>(const Level<R>*, WorkList, Ctl*, bool, int, int, cudaStream_t,  \
-                                  bool);                                                           \
+                                  bool, bool);                                                     \
     template void launch_apply<R>(const Level<R>*, WorkList, Ctl*, int, int, double*, int,        \
                                   cudaStream_t, bool);                                             \
     template void launch_norm_state<R>(const Level<R>*, WorkList, const Ctl*, double*,            \

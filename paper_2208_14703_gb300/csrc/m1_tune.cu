@@ -5,10 +5,15 @@
 // ((sh + 2) / sh) but leave fewer strips, hence fewer warps, per level; the
 // best height depends on the level size, the precision and the GPU.  The tuner
 // times one sweep of a synthetic admissible 2D level for every candidate height
-// and size class and keeps the fastest; levels created afterwards take their
-// height from the table (before any tuning: ny / 64 rows, between 1 and 16).
+// and size class and keeps the fastest; for the FP32 correction form it also
+// chooses how strip rows are staged (loads into registers one row ahead, or
+// asynchronous copies into a shared-memory ring three rows ahead).  Levels
+// created afterwards take both from the table (before any tuning: ny / 64
+// rows, between 1 and 16, staged through registers).
 // The height changes no arithmetic: every cell's update is the same whatever
-// strip it falls in, so tuned and untuned grids give identical results.
+// strip it falls in, so grids of any height give identical results.  The two
+// stagings are separate kernels; their FP32 roundings may differ in the last
+// bit (the mixed path's FP64 defect correction makes results agree to rounding).
 #include <m1.h>
 
 #include <cmath>
@@ -27,6 +32,7 @@ constexpr int kCandidates[] = { 1, 2, 4, 8, 16, 32 };
 
 std::mutex g_tune_mu;
 int g_rows[2][kClasses] = {};                // [kind][class], 0 = untuned
+int g_ring[kClasses] = {};                   // FP32 correction form: 1 = cp.async staging
 
 int size_class(int nx, int ny)
 {
@@ -58,7 +64,8 @@ void synth(int n, std::vector<Cell4<R>>& u, std::vector<Cell4<R>>& f, std::vecto
 }
 
 // Milliseconds per sweep of an n x n level for every candidate strip height
-// (`out` in the order of kCandidates; NAN where the height exceeds n).
+// and staging (`out[s * ncand + c]`, s = 0 registers, 1 cp.async ring (FP32
+// correction form only); NAN where not applicable).
 template <typename R>
 m1_status time_level(int n, bool delta, cudaStream_t stream, std::vector<double>& out)
 {
@@ -87,13 +94,16 @@ m1_status time_level(int n, bool delta, cudaStream_t stream, std::vector<double>
                           e.stream));
     M1_TRY(e.set_dt(0, 100.0 / n));
     M1_TRY(e.set_ctl_simple(0, 0.0, 0.5, 0.5));
-    out.assign(sizeof(kCandidates) / sizeof(int), NAN);
+    const int ncand = (int)(sizeof(kCandidates) / sizeof(int));
+    out.assign(2 * ncand, NAN);
     const int reps = n >= 1024 ? 4 : 10;
-    for (size_t c = 0; c < out.size(); ++c) {
+    for (int idx = 0; idx < 2 * ncand; ++idx) {
+        const int c = idx % ncand, ring = idx / ncand;
         const int sh = kCandidates[c];
-        if (sh > n) continue;
+        if (sh > n || (ring && !delta)) continue;
         e.h[0].sh = sh;
         e.h[0].strips = e.h[0].sx * ((n + sh - 1) / sh);
+        e.h[0].ring = ring;
         M1_TRY(e.rebuild());
         int cur = 0;
         e.sweeps_fine(cur, 2, e.stream);              // warm-up
@@ -104,7 +114,7 @@ m1_status time_level(int n, bool delta, cudaStream_t stream, std::vector<double>
         M1_CK(cudaEventSynchronize(e.ev1));
         float ms = 0.f;
         M1_CK(cudaEventElapsedTime(&ms, e.ev0, e.ev1));
-        out[c] = ms / reps;
+        out[idx] = ms / reps;
     }
     return M1_OK;
 }
@@ -120,6 +130,12 @@ int strip_rows(int kind, int nx, int ny)
     }
     if (r <= 0) r = std::max(1, std::min(kStripH, ny / 64));
     return std::max(1, std::min(r, ny));
+}
+
+int strip_ring(int nx, int ny)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_ring[size_class(nx, ny)];
 }
 
 }  // namespace m1
@@ -140,24 +156,29 @@ m1_status m1_autotune(void* cuda_stream, m1_tune_entry* out, int max_entries, in
             m1_status st = kind == 0 ? m1::time_level<double>(n, false, s, ms)
                                      : m1::time_level<float>(n, true, s, ms);
             if (st != M1_OK) return st;
+            const int ncand = (int)(sizeof(m1::kCandidates) / sizeof(int));
             int best = -1;
-            for (size_t c = 0; c < ms.size(); ++c)
-                if (!std::isnan(ms[c]) && (best < 0 || ms[c] < ms[best])) best = (int)c;
+            for (int c = 0; c < (int)ms.size(); ++c)
+                if (!std::isnan(ms[c]) && (best < 0 || ms[c] < ms[best])) best = c;
             if (best < 0) continue;
             m1_tune_entry t{};
             t.kind = kind;
             t.n = n;
-            t.strip_rows = m1::kCandidates[best];
+            t.strip_rows = m1::kCandidates[best % ncand];
+            t.staging = best / ncand;
             t.ms = ms[best];
             t.ms_default = NAN;
             const int def = std::max(1, std::min(m1::kStripH, n / 64));
-            for (size_t c = 0; c < ms.size(); ++c)
+            for (int c = 0; c < ncand; ++c)
                 if (m1::kCandidates[c] == def) t.ms_default = ms[c];
             found.push_back(t);
         }
     {
         std::lock_guard<std::mutex> lk(m1::g_tune_mu);
-        for (const auto& t : found) m1::g_rows[t.kind][m1::size_class(t.n, t.n)] = t.strip_rows;
+        for (const auto& t : found) {
+            m1::g_rows[t.kind][m1::size_class(t.n, t.n)] = t.strip_rows;
+            if (t.kind == 1) m1::g_ring[m1::size_class(t.n, t.n)] = t.staging;
+        }
     }
     if (n_entries) *n_entries = (int)found.size();
     for (int k = 0; k < (int)found.size() && k < max_entries; ++k) out[k] = found[k];
@@ -169,10 +190,14 @@ m1_status m1_set_tuning(const m1_tune_entry* in, int n)
     if (n < 0 || (n > 0 && !in)) return M1_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k)
         if ((in[k].kind != 0 && in[k].kind != 1) || in[k].n < 1 || in[k].strip_rows < 0 ||
-            in[k].strip_rows > 64)
+            in[k].strip_rows > 64 || in[k].staging < 0 || in[k].staging > 1 ||
+            (in[k].kind == 0 && in[k].staging != 0))
             return M1_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(m1::g_tune_mu);
-    for (int k = 0; k < n; ++k) m1::g_rows[in[k].kind][m1::size_class(in[k].n, in[k].n)] = in[k].strip_rows;
+    for (int k = 0; k < n; ++k) {
+        m1::g_rows[in[k].kind][m1::size_class(in[k].n, in[k].n)] = in[k].strip_rows;
+        if (in[k].kind == 1) m1::g_ring[m1::size_class(in[k].n, in[k].n)] = in[k].staging;
+    }
     return M1_OK;
 }
 

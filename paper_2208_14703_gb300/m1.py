@@ -94,7 +94,8 @@ class ServerStats(ctypes.Structure):
 
 class TuneEntry(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("strip_rows", ctypes.c_int),
-                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double)]
+                ("staging", ctypes.c_int), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -371,8 +372,8 @@ def set_tuning(entries):
     """Install tuner entries (dicts with kind, n, strip_rows)."""
     arr = (TuneEntry * max(1, len(entries)))()
     for k, e in enumerate(entries):
-        arr[k] = TuneEntry(e["kind"], e["n"], e["strip_rows"], e.get("ms", 0.0),
-                           e.get("ms_default", 0.0))
+        arr[k] = TuneEntry(e["kind"], e["n"], e["strip_rows"], e.get("staging", 0),
+                           e.get("ms", 0.0), e.get("ms_default", 0.0))
     _check(_lib.m1_set_tuning(arr, len(entries)), "m1_set_tuning")
 
 

@@ -1,6 +1,7 @@
-"""The strip-height table of the sweep kernels: defaults and installed entries
-(host logic, no GPU needed); on the GPU, the autotuner's output and the fact
-that the strip height changes no arithmetic (bitwise equal steps)."""
+"""The strip-shape table of the sweep kernels: defaults and installed entries
+(host logic, no GPU needed); on the GPU, the autotuner's output, the fact that
+the strip height changes no arithmetic (bitwise equal steps) and that the two
+row stagings of the FP32 correction form agree to rounding."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,8 @@ m1 = pytest.importorskip("paper_2208_14703_gb300.m1")
 @pytest.fixture
 def restore_tuning():
     yield
-    m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": 0} for k in (0, 1) for c in range(16)])
+    m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": 0, "staging": 0} for k in (0, 1)
+                   for c in range(16)])
 
 
 def test_default_strip_rows(restore_tuning):
@@ -34,6 +36,8 @@ def test_installed_entries_and_reset(restore_tuning):
     assert m1.strip_rows(1, 256, 256) == 4
     with pytest.raises(m1.M1Error):
         m1.set_tuning([{"kind": 2, "n": 256, "strip_rows": 8}])
+    with pytest.raises(m1.M1Error):
+        m1.set_tuning([{"kind": 0, "n": 256, "strip_rows": 8, "staging": 1}])
 
 
 @pytest.mark.gpu
@@ -42,21 +46,41 @@ def test_autotune_entries(restore_tuning):
     assert {(e["kind"], e["n"]) for e in ent} == {(k, 1 << c) for k in (0, 1) for c in range(4, 12)}
     for e in ent:
         assert e["strip_rows"] in (1, 2, 4, 8, 16, 32) and e["strip_rows"] <= e["n"]
+        assert e["staging"] in ((0,) if e["kind"] == 0 else (0, 1))
         assert e["ms"] > 0 and (np.isnan(e["ms_default"]) or e["ms"] <= e["ms_default"])
         assert m1.strip_rows(e["kind"], e["n"], e["n"]) == e["strip_rows"]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [0, 1])
-def test_strip_height_changes_no_arithmetic(precision, restore_tuning):
-    case = inputs.hot_square_2d(128, lmax=5)
-    outs = []
-    for rows in (1, 32):
-        m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": rows} for k in (0, 1)
-                       for c in range(16)])
-        g = m1.grid_from_case(case, precision=precision)
-        st = g.implicit_step(case["dt"], m1.m1_default_params(tol=1e-8))
-        outs.append((st.cycles, np.stack(g.get_state())))
-        g.close()
-    assert outs[0][0] == outs[1][0]
-    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+def test_strip_shape_changes_no_arithmetic(precision, restore_tuning):
+    """Strip heights 1 and 32 give bitwise equal steps (the same kernel, every
+    cell's update the same whatever strip it falls in).  The two row stagings of
+    the FP32 correction form are two kernels whose FP32 contractions may round
+    differently, so their steps agree to rounding: same cycle count, results
+    within 1e-10 relative.  Checked on a square hot-square grid and on a ragged
+    periodic grid."""
+    cases = [inputs.hot_square_2d(128, lmax=5),
+             inputs.random_admissible_2d(80, 48, seed=9, fmax=0.95, cfl=20,
+                                         bc=("periodic",) * 4, lmax=3)]
+    cases[1]["tol"] = 1e-8
+    for case in cases:
+        outs = {}
+        for rows, staging in ((1, 0), (32, 0), (1, 1), (32, 1)):
+            if staging and precision == 0:
+                continue
+            m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": rows,
+                            "staging": staging if k == 1 else 0}
+                           for k in (0, 1) for c in range(16)])
+            g = m1.grid_from_case(case, precision=precision)
+            st = g.implicit_step(case["dt"], m1.m1_default_params(tol=case["tol"]))
+            outs[rows, staging] = (st.cycles, np.stack(g.get_state()))
+            g.close()
+        for staging in (0, 1) if precision else (0,):
+            assert outs[32, staging][0] == outs[1, staging][0]
+            np.testing.assert_array_equal(outs[32, staging][1], outs[1, staging][1])
+        if precision:
+            a, b = outs[1, 0], outs[1, 1]
+            assert a[0] == b[0]
+            for f in range(4):
+                assert np.linalg.norm(a[1][f] - b[1][f]) <= 1e-10 * np.linalg.norm(a[1][0])
