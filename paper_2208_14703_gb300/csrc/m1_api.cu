@@ -140,10 +140,9 @@ template <typename R>
 std::vector<DevList*> Engine<R>::all_lists()
 {
     std::vector<DevList*> v;
-    for (auto& l : tiles) v.push_back(&l);
     for (auto& l : chunks) v.push_back(&l);
     for (auto& l : strips) v.push_back(&l);
-    v.push_back(&init_tiles);
+    v.push_back(&init_strips);
     v.push_back(&init_chunks);
     return v;
 }
@@ -179,7 +178,6 @@ m1_status Engine<R>::init(int capacity, int levels, bool correction_form, cudaSt
     dt_rhs.assign(cap, NAN);
     rhs_valid.assign(cap, 0);
     last_cycles.assign(cap, 0);
-    tiles.assign(L, DevList{});
     chunks.assign(L, DevList{});
     strips.assign(L, DevList{});
     M1_TRY(calloc_common((void**)&d, sizeof(Level<R>) * L * cap));
@@ -343,7 +341,7 @@ m1_status Engine<R>::rebuild()
 {
     int off = 0;
     for (int i = 0; i < cap; ++i)
-        if (used[i]) { h[i].part_off = off; off += h[i].tiles; }
+        if (used[i]) { h[i].part_off = off; off += h[i].strips; }
     if (off > part_cap || !part) {
         int capn = 1;
         while (capn < off) capn <<= 1;
@@ -361,17 +359,14 @@ m1_status Engine<R>::rebuild()
         graph_dirty = true;
     }
     for (int l = 0; l < L; ++l) {
-        tiles[l].host.clear();
         chunks[l].host.clear();
         strips[l].host.clear();
         for (int i = 0; i < cap; ++i) {
             if (!used[i]) continue;
             const Level<R>& q = h[(size_t)l * cap + i];
-            for (int t = 0; t < q.tiles; ++t) tiles[l].host.push_back(make_int2(i, t));
             for (int t = 0; t < q.strips; ++t) strips[l].host.push_back(make_int2(i, t));
             for (int c = 0; c < q.chunks; ++c) chunks[l].host.push_back(make_int2(i, c));
         }
-        M1_TRY(upload_list(tiles[l]));
         M1_TRY(upload_list(strips[l]));
         M1_TRY(upload_list(chunks[l]));
     }
@@ -569,12 +564,12 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         Level<R>* dl = d + (size_t)l * cap;
         if (l == 0) {
             sweeps_fine(cur[0], p.nu0, s);
-            launch_apply<R>(dl, tiles[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
+            launch_apply<R>(dl, strips[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
         } else {
-            if (delta) launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
-            launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+            if (delta) launch_apply<R>(dl, strips[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
+            launch_apply<R>(dl, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
             pseudo(l, cur[l], p.m, true, s);
-            launch_apply<R>(dl, tiles[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
+            launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
         }
         launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
     }
@@ -583,8 +578,8 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
     } else {
         const int l = L - 1;
         if (delta)
-            launch_apply<R>(d + (size_t)l * cap, tiles[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
-        launch_apply<R>(d + (size_t)l * cap, tiles[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+            launch_apply<R>(d + (size_t)l * cap, strips[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
+        launch_apply<R>(d + (size_t)l * cap, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
         pseudo(l, cur[l], p.mc, true, s);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -594,7 +589,7 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         else pseudo(l, cur[l], p.m, false, s);
     }
     if (tail) {
-        launch_apply<R>(d, tiles[0].view(), ctl, APPLY_RESID, cur[0], part, 0, s, delta);
+        launch_apply<R>(d, strips[0].view(), ctl, APPLY_RESID, cur[0], part, 0, s, delta);
         launch_finalize<R>(ctl, d, cap, part, nullptr, FIN_CYCLE, cur[0], bctl, s);
     }
     cur0 = cur[0];
@@ -668,7 +663,7 @@ m1_status Engine<R>::step(const double* dts, const m1_solve_params& sp, m1_step_
     M1_TRY(build_graph(p));
     M1_TRY(begin_step(dts, sp));
     M1_CK(cudaEventRecord(ev0, stream));
-    const WorkList t0 = tiles[0].view(), c0 = chunks[0].view();
+    const WorkList t0 = strips[0].view(), c0 = chunks[0].view();
     launch_make_rhs<R>(d, c0, ctl, 0, stream);
     launch_apply<R>(d, t0, ctl, APPLY_RESID, 0, part, 0, stream);
     launch_norm_state<R>(d, t0, ctl, partb, stream);
@@ -718,17 +713,17 @@ m1_status Engine<R>::residual_norm(int i, double dt, double* out)
 {
     if (i < 0 || i >= cap || !used[i] || !out || !(dt > 0)) return M1_ERR_INVALID_ARG;
     M1_TRY(set_dt(i, dt));
-    init_tiles.host.clear();
+    init_strips.host.clear();
     init_chunks.host.clear();
-    for (int t = 0; t < h[i].tiles; ++t) init_tiles.host.push_back(make_int2(i, t));
+    for (int t = 0; t < h[i].strips; ++t) init_strips.host.push_back(make_int2(i, t));
     for (int c = 0; c < h[i].chunks; ++c) init_chunks.host.push_back(make_int2(i, c));
-    M1_TRY(upload_list(init_tiles));
+    M1_TRY(upload_list(init_strips));
     M1_TRY(upload_list(init_chunks));
     if (!(rhs_valid[i] && dt == dt_rhs[i]))
         launch_make_rhs<R>(d, init_chunks.view(), nullptr, 0, stream);
-    launch_apply<R>(d, init_tiles.view(), nullptr, APPLY_RESID, 0, part, 0, stream);
+    launch_apply<R>(d, init_strips.view(), nullptr, APPLY_RESID, 0, part, 0, stream);
     M1_CK(cudaGetLastError());
-    std::vector<double> p(h[i].tiles);
+    std::vector<double> p(h[i].strips);
     M1_CK(cudaMemcpyAsync(p.data(), part + h[i].part_off, sizeof(double) * p.size(),
                           cudaMemcpyDeviceToHost, stream));
     M1_CK(cudaStreamSynchronize(stream));
@@ -807,7 +802,7 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
                           stream));
     launch_pack_sig<R>(stage + 4 * (size_t)n, stage + 5 * (size_t)n, q.sig, n, stream);
     M1_TRY(set_ctl_simple(0, dtau, theta, 0.5));
-    const WorkList t0 = tiles[0].view();
+    const WorkList t0 = strips[0].view();
     switch (mode) {
     case M1_OP_APPLY:
         M1_TRY(pack_planar(q.u[0], n, state));
@@ -821,7 +816,7 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
         M1_CK(cudaGetLastError());
         M1_TRY(unpack_planar(q.r, n, out));
         if (norm) {
-            std::vector<double> p(q.tiles);
+            std::vector<double> p(q.strips);
             M1_CK(cudaMemcpy(p.data(), part, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
             double s = 0.0;
             for (double x : p) s += x;
@@ -901,13 +896,13 @@ size_t Engine<R>::slot_bytes(const m1_grid_desc& g) const
 template <typename R>
 m1_status Engine<R>::set_init_lists(const std::vector<int>& slots)
 {
-    init_tiles.host.clear();
+    init_strips.host.clear();
     init_chunks.host.clear();
     for (int i : slots) {
-        for (int t = 0; t < h[i].tiles; ++t) init_tiles.host.push_back(make_int2(i, t));
+        for (int t = 0; t < h[i].strips; ++t) init_strips.host.push_back(make_int2(i, t));
         for (int c = 0; c < h[i].chunks; ++c) init_chunks.host.push_back(make_int2(i, c));
     }
-    M1_TRY(upload_list(init_tiles));
+    M1_TRY(upload_list(init_strips));
     M1_TRY(upload_list(init_chunks));
     if (!slots.empty())
         M1_CK(cudaMemcpyAsync(init_slots, slots.data(), sizeof(int) * slots.size(),
@@ -996,8 +991,8 @@ m1_status PlainModel::sv_begin(const std::vector<int>& slots, const std::vector<
     }
     M1_TRY(e.set_init_lists(slots));
     launch_make_rhs<double>(e.d, e.init_chunks.view(), e.ctl, 0, e.stream);
-    launch_apply<double>(e.d, e.init_tiles.view(), e.ctl, APPLY_RESID, 0, e.part, 0, e.stream);
-    launch_norm_state<double>(e.d, e.init_tiles.view(), e.ctl, e.partb, e.stream);
+    launch_apply<double>(e.d, e.init_strips.view(), e.ctl, APPLY_RESID, 0, e.part, 0, e.stream);
+    launch_norm_state<double>(e.d, e.init_strips.view(), e.ctl, e.partb, e.stream);
     launch_finalize<double>(e.ctl, e.d, (int)slots.size(), e.part, e.partb, FIN_INIT, 0, e.bctl,
                             e.stream, e.init_slots);
     M1_CK(cudaGetLastError());
@@ -1088,8 +1083,8 @@ m1_status MixedModel::sv_begin(const std::vector<int>& slots, const std::vector<
     }
     M1_TRY(hi.set_init_lists(slots));
     launch_make_rhs<double>(hi.d, hi.init_chunks.view(), hi.ctl, 0, hi.stream);
-    launch_norm_state<double>(hi.d, hi.init_tiles.view(), hi.ctl, hi.partb, hi.stream);
-    launch_defect(hi.d, lo.d, hi.init_tiles.view(), hi.ctl, hi.part, hi.stream);
+    launch_norm_state<double>(hi.d, hi.init_strips.view(), hi.ctl, hi.partb, hi.stream);
+    launch_defect(hi.d, lo.d, hi.init_strips.view(), hi.ctl, hi.part, hi.stream);
     launch_finalize<double>(hi.ctl, hi.d, (int)slots.size(), hi.part, hi.partb, FIN_INIT, 0, hi.bctl,
                             hi.stream, hi.init_slots);
     M1_CK(cudaGetLastError());
@@ -1164,7 +1159,7 @@ void MixedModel::record_cycle(const Params& p, cudaStream_t s)
     int cur0 = 0;
     lo.record_cycle(p, cur0, s, false);
     launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s);
-    launch_defect(hi.d, lo.d, hi.tiles[0].view(), hi.ctl, hi.part, s);
+    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, nullptr, FIN_CYCLE, 0, hi.bctl, s);
 }
 
@@ -1197,7 +1192,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
     M1_TRY(hi.begin_step(dts, sp));
     cudaStream_t s = hi.stream;
     M1_CK(cudaEventRecord(hi.ev0, s));
-    const WorkList t0 = hi.tiles[0].view(), c0 = hi.chunks[0].view();
+    const WorkList t0 = hi.strips[0].view(), c0 = hi.chunks[0].view();
     launch_make_rhs<double>(hi.d, c0, hi.ctl, 0, s);
     launch_norm_state<double>(hi.d, t0, hi.ctl, hi.partb, s);
     launch_defect(hi.d, lo.d, t0, hi.ctl, hi.part, s);
@@ -1248,7 +1243,7 @@ m1_status MixedModel::jacobi(int i, double dt, int sweeps)
     M1_TRY(hi.set_ctl_simple(0, 0.0, 0.5, 0.5));
     cudaStream_t s = hi.stream;
     launch_make_rhs<double>(hi.d, hi.chunks[0].view(), hi.ctl, 0, s);
-    launch_defect(hi.d, lo.d, hi.tiles[0].view(), hi.ctl, hi.part, s);
+    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
     int cur = 0;
     lo.sweeps_fine(cur, sweeps, s);
     launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur, s);

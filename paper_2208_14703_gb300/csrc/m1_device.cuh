@@ -211,9 +211,8 @@ __device__ __forceinline__ bool admissible(const Cell4<R>& s, R c)
 
 // Newton on g(T) = C T + K T^4 - R (increasing, convex for T > 0) started at
 // T0 = min(R/C, (R/K)^(1/4)), which lies at or right of the root.
-// FP32 iterations reach about 1e-7; the FP64 variant then takes two Newton
-// steps in FP64 with the FP32 reciprocal of g' (each step squares the relative
-// error up to the 1e-7 error of that reciprocal), reaching FP64 rounding.
+// FP32 iterations reach about 1e-7; the FP64 variant then takes one Halley
+// step in FP64, reaching FP64 rounding.
 __device__ __forceinline__ float newton_quartic_f32(float C, float K, float Rr, bool& ok)
 {
     float T = fminf(Rr / C, sqrtf(sqrtf(Rr / K)));
@@ -241,16 +240,34 @@ template <> struct Quartic<double> {
     {
         bool ok32;
         double T = (double)newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
-        double dT = 0.0;
-        for (int it = 0; it < 3; ++it) {
-            double T3 = T * T * T;
-            double g = fma(K, T3 * T, C * T) - Rr;
-            double dg = fma(4.0 * K, T3, C);
-            dT = g * (double)Fm<float>::rcp((float)dg);
-            T -= dT;
-            if (it >= 1 && fabs(dT) <= 1e-15 * T) break;
+        // One step of Halley's method (cubically convergent):
+        // T <- T - 2 g g' / (2 g'^2 - g g''), g' = C + 4 K T^3, g'' = 12 K T^2.
+        // From the FP32 root (relative error near 1e-7) it lands at FP64
+        // rounding.  The quotient needs only ~1e-14 relative accuracy (it
+        // multiplies a correction of ~1e-7 T): FP32 reciprocal estimate of the
+        // denominator plus one FP64 Newton step.
+        const double T2 = T * T;
+        const double g = fma(K, T2 * T2, C * T) - Rr;
+        const double d1 = fma(4.0 * K, T2 * T, C);
+        const double den = fma(2.0 * d1, d1, -g * (12.0 * K * T2));
+        double r = (double)Fm<float>::rcp((float)den);
+        r = fma(r, fma(-den, r, 1.0), r);
+        double dT = 2.0 * g * d1 * r;
+        T -= dT;
+        if (fabs(dT) > 1e-6 * T) {
+            // the FP32 start was not close enough for one cubic step: Newton
+            for (int it = 0; it < 8; ++it) {
+                const double T3 = T * T * T;
+                const double gn = fma(K, T3 * T, C * T) - Rr;
+                const double dg = fma(4.0 * K, T3, C);
+                dT = gn * (double)Fm<float>::rcp((float)dg);
+                T -= dT;
+                if (fabs(dT) <= 1e-15 * T) break;
+            }
+            ok = fabs(dT) <= 1e-12 * T;
+        } else {
+            ok = true;
         }
-        ok = fabs(dT) <= 1e-12 * T;
         return T;
     }
 };

@@ -81,9 +81,8 @@ struct Engine {
     std::vector<Level<R>> h;                // host descriptors [level * cap + slot]
     Level<R>* d = nullptr;                  // device descriptors
     std::vector<std::vector<double>> prof;  // inflow profiles [level * cap + slot]
-    std::vector<DevList> tiles, chunks;     // work lists per level
-    std::vector<DevList> strips;            // warp-strip lists per level (sweeps)
-    DevList init_tiles, init_chunks;        // scratch lists for one slot
+    std::vector<DevList> strips, chunks;    // work lists per level: warp strips, 256-cell chunks
+    DevList init_strips, init_chunks;       // scratch lists for one slot
     int* init_slots = nullptr;
     Ctl* ctl = nullptr;                     // device control blocks [cap]
     Ctl* ctl_h = nullptr;                   // pinned mirror
@@ -95,7 +94,7 @@ struct Engine {
     double* hist = nullptr;
     double* dtau_hist = nullptr;
     int hist_len = 0;
-    double* part = nullptr;                 // per-tile norm partials (level 0, all slots)
+    double* part = nullptr;                 // per-strip norm partials (level 0, all slots)
     double* partb = nullptr;
     int part_cap = 0;
     double* stage = nullptr;                // planar FP64 staging, 6 * stage_n

@@ -3,7 +3,7 @@
 //   k_sweep     one Jacobi sweep (Algorithm 1 / Eq. (10)); PSEUDO = true fuses
 //               the explicit and implicit halves of the pseudo-time step
 //               (Eq. (30), Algorithm 3) into the same sweep
-//   k_apply     A(u) for the residual r = f - A(u) (Eq. (13)) with per-tile norm
+//   k_apply     A(u) for the residual r = f - A(u) (Eq. (13)) with per-strip norm
 //               partials, or the FAS right-hand side f = A(v) + r (Eq. (24))
 //   k_restrict  full-weighting restriction of the iterate and residual (Eq. (21)/(22))
 //   k_prolong   prolongation of the coarse correction (Eq. (14)/(18)) with the
@@ -12,21 +12,17 @@
 //               adaptive implicit pseudo-time step (Algorithm 4), per instance
 //   k_defect, k_accumulate   FP64 ends of the mixed-precision cycle
 //
-// Every kernel walks a work list of (instance, tile) or (instance, 256-cell
+// Every kernel walks a work list of (instance, strip) or (instance, 256-cell
 // chunk) items with a fixed persistent grid, so one launch serves every
 // instance of a batch at one level; an instance whose control block says done
-// skips its items.  The stencil kernels stage a tile plus a one-cell halo in
-// shared memory and evaluate each cell's closure once per pass.
+// skips its items.  The stencil kernels give each warp a strip of 30 columns
+// and march it up the rows with the staged rows (state and closure) in
+// registers, so each staged cell's closure is evaluated once per strip.
 #include <type_traits>
 
 #include "m1_kernels.cuh"
 
 namespace m1 {
-
-template <typename R>
-struct Tile {
-    R E[kHalo], Fx[kHalo], Fy[kHalo], Pxx[kHalo], Pxy[kHalo], Pyy[kHalo];
-};
 
 template <typename R>
 __device__ __forceinline__ void load_level(Level<R>& dst, const Level<R>* src)
@@ -37,62 +33,6 @@ __device__ __forceinline__ void load_level(Level<R>& dst, const Level<R>* src)
     for (int k = threadIdx.x; k < (int)(sizeof(Level<R>) / 8); k += blockDim.x) d[k] = s[k];
 }
 
-// Stage the tile [x0, x0+tx) x [y0, y0+ty) of state `s` with its one-cell halo
-// (no corners) and each staged cell's closure.  DELTA (correction form): `s`
-// is the correction e, the base state is L.w, and the tile holds e and the
-// closure difference P(w + e) - P(w); the neighbour operators are linear in
-// (E, F, P), so the same neighbour sum then gives N(w + e) - N(w).
-template <typename R, bool DELTA = false>
-__device__ __forceinline__ void load_tile(const Level<R>& L, const Cell4<R>* __restrict__ s,
-                                          int x0, int y0, Tile<R>& t)
-{
-    const int hw = L.tx + 2, hh = L.dim == 2 ? L.ty + 2 : 1, oy = L.dim == 2 ? 1 : 0;
-    const R inv_c2 = L.ic2;
-    for (int k = threadIdx.x; k < hw * hh; k += blockDim.x) {
-        int hi = k % hw, hj = k / hw;
-        int gi = x0 + hi - 1, gj = y0 + hj - oy;
-        bool edge_x = hi == 0 || hi == hw - 1, edge_y = oy && (hj == 0 || hj == hh - 1);
-        if ((edge_x && edge_y) || gi > L.nx || gj > L.ny) continue;
-        R pxx, pxy, pyy;
-        Cell4<R> c;
-        if (!DELTA) {
-            c = fetch(L, s, gi, gj, KIND_STATE);
-            closure(c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
-        } else {
-            const Cell4<R> w = fetch(L, L.w, gi, gj, KIND_STATE);
-            c = fetch(L, s, gi, gj, KIND_DIFF);
-            closure_delta(w.E, w.Fx, w.Fy, c.E, c.Fx, c.Fy, inv_c2, pxx, pxy, pyy);
-        }
-        t.E[k] = c.E; t.Fx[k] = c.Fx; t.Fy[k] = c.Fy;
-        t.Pxx[k] = pxx; t.Pxy[k] = pxy; t.Pyy[k] = pyy;
-    }
-}
-
-// Sum of the neighbour operators L and R of Eq. (9) around staged cell `ck`
-// (2D: the x pair and the y pair of faces).
-template <typename R>
-__device__ __forceinline__ void neighbour_sum(const Level<R>& L, const Tile<R>& t, int ck,
-                                              R& NE, R& NFx, R& NFy)
-{
-    const R c = L.c;
-    const int w = ck - 1, e = ck + 1;
-    NE = L.bx * (c * (t.E[w] + t.E[e]) + (t.Fx[w] - t.Fx[e]));
-    NFx = c * L.bx * ((t.Fx[w] + t.Fx[e]) + c * (t.Pxx[w] - t.Pxx[e]));
-    NFy = c * L.bx * ((t.Fy[w] + t.Fy[e]) + c * (t.Pxy[w] - t.Pxy[e]));
-    if (L.dim == 2) {
-        const int hw = L.tx + 2, sth = ck - hw, nth = ck + hw;
-        NE += L.by * (c * (t.E[sth] + t.E[nth]) + (t.Fy[sth] - t.Fy[nth]));
-        NFx += c * L.by * ((t.Fx[sth] + t.Fx[nth]) + c * (t.Pxy[sth] - t.Pxy[nth]));
-        NFy += c * L.by * ((t.Fy[sth] + t.Fy[nth]) + c * (t.Pyy[sth] - t.Pyy[nth]));
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void tile_origin(const Level<R>& L, int tile, int& x0, int& y0)
-{
-    x0 = (tile % L.tiles_x) * L.tx;
-    y0 = (tile / L.tiles_x) * L.ty;
-}
 
 // The explicit pseudo-time step length min(dtau, theta tau*) of Algorithm 3
 // (tau* = the largest admissible step from u along f).  The admissible set is
@@ -475,49 +415,101 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep_ring32(const Level<f
     }
 }
 
-// ---------------------------------------------------------------------------
-// Block sum of one double per thread (result valid in thread 0).
-__device__ __forceinline__ double block_sum(double v, double* red)
+
+// Sum of one double over the lanes of a warp in a fixed order (lane 0 holds it).
+__device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    return s;
+    return v;
 }
 
-template <typename R, int MODE, bool DELTA = false>
-__global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__ lv, WorkList wl,
-                                                    Ctl* __restrict__ ctls, int state_buf,
-                                                    double* __restrict__ partials, int write_r)
+// Neighbour operators L and R of Eq. (9) of a strip cell from its staged west /
+// east (shuffled) and south / north rows.
+template <typename R>
+__device__ __forceinline__ void strip_neighbours(const Level<R>& L, const Staged<R>& wv,
+                                                 const Staged<R>& ev, const Staged<R>& prev,
+                                                 const Staged<R>& next, bool two_d, R& NE,
+                                                 R& NFx, R& NFy)
 {
-    __shared__ Level<R> L;
-    __shared__ Tile<R> t;
-    __shared__ double red[kThreads / 32];
+    const R c = L.c, bx = L.bx, by = L.by;
+    NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
+    NFx = c * bx * ((wv.Fx + ev.Fx) + c * (wv.Pxx - ev.Pxx));
+    NFy = c * bx * ((wv.Fy + ev.Fy) + c * (wv.Pxy - ev.Pxy));
+    if (two_d) {
+        NE += by * (c * (prev.E + next.E) + (prev.Fy - next.Fy));
+        NFx += c * by * ((prev.Fx + next.Fx) + c * (prev.Pxy - next.Pxy));
+        NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
+    }
+}
+
+// March one warp up an (instance, strip) item with the staged rows j - 1, j,
+// j + 1 in registers (loads of row j + 2 issued before row j is used) and call
+// cell(k, wv, ev, prev, next, cur) for each own cell (lanes 1..30 inside the
+// grid).  The layout is the sweep's (strip_regs).
+template <typename R, bool DELTA, typename F>
+__device__ __forceinline__ void strip_march(const Level<R>& L, int2 it, int lane,
+                                            const Cell4<R>* __restrict__ src, F&& cell)
+{
+    const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
+    const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+    const int i = min(x0 - 1 + lane, nx);
+    const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const int rows = min(L.sh, ny - y0);
+    Staged<R> prev{}, cur, next{};
+    Raw<R> rn{};
+    if (two_d) {
+        prev = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0 - 1, colfast && y0 >= 1));
+        rn = load_raw<R, DELTA>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
+    }
+    cur = stage_raw<R, DELTA>(L, load_raw<R, DELTA>(L, src, i, y0, colfast));
+    size_t k = (size_t)y0 * nx + i;
+    for (int r = 0; r < rows; ++r, k += nx) {
+        const int j = y0 + r;
+        if (two_d) {
+            next = stage_raw<R, DELTA>(L, rn);
+            if (r + 1 < rows) rn = load_raw<R, DELTA>(L, src, i, j + 2, colfast && j + 2 < ny);
+        }
+        const Staged<R> wv = shfl_staged(cur, (lane + 31) & 31);
+        const Staged<R> ev = shfl_staged(cur, (lane + 1) & 31);
+        if (own) cell(k, wv, ev, prev, next, cur);
+        prev = cur;
+        cur = next;
+    }
+}
+
+// A(u) of Eq. (12) (+ sources) at one level, per (instance, strip) item:
+//   APPLY_RESID  r = f - A(u) (Eq. (13)), written to L.r if write_r, and the
+//                weighted norm partial of the strip (partials != null)
+//   APPLY_FAS    f = A(v) + r (Eq. (24))
+//   APPLY_A      r = A(u), or aw = A(w) when state_buf = -2
+// DELTA (correction form): u is a correction e around the base w and the
+// operator is the difference A(w + e) - A(w).
+template <typename R, int MODE, bool DELTA = false>
+__global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __restrict__ lv,
+                                                            WorkList wl, Ctl* __restrict__ ctls,
+                                                            int state_buf,
+                                                            double* __restrict__ partials,
+                                                            int write_r)
+{
+    __shared__ Level<R> Ls[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<R>& L = Ls[wib];
     const int nw = *wl.count;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        load_level(L, lv + it.x);
-        __syncthreads();
-        int x0, y0;
-        tile_origin(L, it.y, x0, y0);
+        load_level_warp(L, lv + it.x, lane);
         // state_buf: 0/1 the iterate, -1 the restricted iterate v, -2 the base w
         const Cell4<R>* __restrict__ src =
             state_buf == -2 ? L.w : (state_buf < 0 ? L.v : L.u[state_buf]);
-        load_tile<R, DELTA>(L, src, x0, y0, t);
-        __syncthreads();
-        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-        const int i = x0 + lx, j = y0 + ly;
+        const bool two_d = L.dim == 2;
         double nrm = 0.0;
-        if (i < L.nx && j < L.ny) {
-            const size_t k = (size_t)j * L.nx + i;
-            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+        strip_march<R, DELTA>(L, it, lane, src, [&](size_t k, const Staged<R>& wv,
+                                                     const Staged<R>& ev, const Staged<R>& prev,
+                                                     const Staged<R>& next, const Staged<R>& cur) {
             R NE, NFx, NFy;
-            neighbour_sum(L, t, ck, NE, NFx, NFy);
+            strip_neighbours(L, wv, ev, prev, next, two_d, NE, NFx, NFy);
             const Cell4<R> u = src[k];
             const Sig2<R> sg = L.sig[k];
             const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
@@ -527,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
                 src_e = ka * (u.E - L.a_r * T2 * T2);
             } else {
                 // A(w + e) - A(w): source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
-                src_e = ka * (u.E - L.a_r * quartic_delta(L.w[k].T, u.T));
+                src_e = ka * (u.E - L.a_r * quartic_delta(cur.T, u.T));
             }
             Cell4<R> a;
             a.E = L.diag * u.E + src_e - NE;
@@ -536,56 +528,55 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Level<R>* __restrict__
             a.T = L.c_v * u.T - src_e;
             if (MODE == APPLY_RESID) {
                 const Cell4<R> f = L.f[k];
-                Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
+                const Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
                 if (write_r) L.r[k] = r;
-                const double ic2 = (double)L.ic2;
-                nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
-                      (double)r.T * r.T;
+                nrm += (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * (double)L.ic2 +
+                       (double)r.T * r.T;
             } else if (MODE == APPLY_FAS) {
                 const Cell4<R> r = L.r[k];
-                Cell4<R> o = { a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
-                L.f[k] = o;
+                L.f[k] = Cell4<R>{ a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
             } else if (state_buf == -2) {
                 L.aw[k] = a;
             } else {
                 L.r[k] = a;
             }
-        }
+        });
         if (MODE == APPLY_RESID && partials) {
-            double s = block_sum(nrm, red);
-            if (threadIdx.x == 0) partials[L.part_off + it.y] = s * L.vol;
+            const double sum = warp_sum(nrm);
+            if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
-// Norm of the right-hand side f of each instance (for ||b||): per-tile partials.
+// Norm of the right-hand side f of each instance (for ||b||): per-strip partials.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_norm_state(const Level<R>* __restrict__ lv,
-                                                         WorkList wl, const Ctl* __restrict__ ctls,
-                                                         double* __restrict__ partials)
+__global__ void __launch_bounds__(kStripWarps * 32) k_norm_state(const Level<R>* __restrict__ lv,
+                                                                 WorkList wl,
+                                                                 const Ctl* __restrict__ ctls,
+                                                                 double* __restrict__ partials)
 {
-    __shared__ Level<R> L;
-    __shared__ double red[kThreads / 32];
+    __shared__ Level<R> Ls[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<R>& L = Ls[wib];
     const int nw = *wl.count;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
         if (ctls && !ctls[it.x].active) continue;
-        load_level(L, lv + it.x);
-        __syncthreads();
-        int x0, y0;
-        tile_origin(L, it.y, x0, y0);
-        const int i = x0 + threadIdx.x % L.tx, j = y0 + threadIdx.x / L.tx;
+        load_level_warp(L, lv + it.x, lane);
+        const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+        const int i = x0 - 1 + lane;
+        const int rows = min(L.sh, L.ny - y0);
         double nrm = 0.0;
-        if (i < L.nx && j < L.ny) {
-            const Cell4<R> r = L.f[(size_t)j * L.nx + i];
-            const double ic2 = 1.0 / ((double)L.c * (double)L.c);
-            nrm = (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * ic2 +
-                  (double)r.T * r.T;
-        }
-        double sum = block_sum(nrm, red);
-        if (threadIdx.x == 0) partials[L.part_off + it.y] = sum * L.vol;
-        __syncthreads();
+        if (lane >= 1 && lane <= kStripW && i < L.nx)
+            for (int r = 0; r < rows; ++r) {
+                const Cell4<R> f = L.f[(size_t)(y0 + r) * L.nx + i];
+                nrm += (double)f.E * f.E + ((double)f.Fx * f.Fx + (double)f.Fy * f.Fy) *
+                       (double)L.ic2 + (double)f.T * f.T;
+            }
+        const double sum = warp_sum(nrm);
+        if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncwarp();
     }
 }
 
@@ -792,7 +783,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
     if (!ctl->active) return;
     if (mode == FIN_CYCLE && ctl->done) return;
     const Level<R>* L = lv0 + slot;
-    const int off = L->part_off, np = L->tiles;
+    const int off = L->part_off, np = L->strips;
     const double s = block_reduce_fixed(part + off, np, red);
     double sb = 0.0;
     if (mode == FIN_INIT) sb = block_reduce_fixed(partb + off, np, red);
@@ -886,35 +877,32 @@ __global__ void k_check_state(const Cell4<R>* __restrict__ s, const Sig2<R>* __r
 // stop test), and the FP32 fine problem of the next cycle in correction form:
 // base state w = fl32(v64), initial correction e = 0, source g = fl32(r64)
 // (the FP32 cycle solves A32(w + e) - A32(w) = r64 for e).
-__global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __restrict__ lv64,
-                                                     const Level<float>* __restrict__ lv32,
-                                                     WorkList wl, Ctl* __restrict__ ctls,
-                                                     double* __restrict__ partials)
+__global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>* __restrict__ lv64,
+                                                             const Level<float>* __restrict__ lv32,
+                                                             WorkList wl, Ctl* __restrict__ ctls,
+                                                             double* __restrict__ partials)
 {
-    __shared__ Level<double> L;
-    __shared__ Level<float> M;
-    __shared__ Tile<double> t;
-    __shared__ double red[kThreads / 32];
+    __shared__ Level<double> Ls[kStripWarps];
+    __shared__ Level<float> Ms[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<double>& L = Ls[wib];
+    Level<float>& M = Ms[wib];
     const int nw = *wl.count;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        load_level(L, lv64 + it.x);
-        load_level(M, lv32 + it.x);
-        __syncthreads();
-        int x0, y0;
-        tile_origin(L, it.y, x0, y0);
-        load_tile(L, L.u[0], x0, y0, t);
-        __syncthreads();
-        const int lx = threadIdx.x % L.tx, ly = threadIdx.x / L.tx;
-        const int i = x0 + lx, j = y0 + ly;
+        load_level_warp(L, lv64 + it.x, lane);
+        load_level_warp(M, lv32 + it.x, lane);
+        const bool two_d = L.dim == 2;
         double nrm = 0.0;
-        if (i < L.nx && j < L.ny) {
-            const size_t k = (size_t)j * L.nx + i;
-            const int ck = (ly + (L.dim == 2 ? 1 : 0)) * (L.tx + 2) + lx + 1;
+        strip_march<double, false>(L, it, lane, L.u[0], [&](size_t k, const Staged<double>& wv,
+                                                             const Staged<double>& ev,
+                                                             const Staged<double>& prev,
+                                                             const Staged<double>& next,
+                                                             const Staged<double>& cur) {
             double NE, NFx, NFy;
-            neighbour_sum(L, t, ck, NE, NFx, NFy);
-            const Cell4<double> u = L.u[0][k];
+            strip_neighbours(L, wv, ev, prev, next, two_d, NE, NFx, NFy);
+            const Cell4<double> u = { cur.E, cur.Fx, cur.Fy, cur.T };
             const Sig2<double> sg = L.sig[k];
             const double ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
             const double T2 = u.T * u.T, se = ka * (u.E - L.a_r * T2 * T2);
@@ -923,17 +911,14 @@ __global__ void __launch_bounds__(kThreads) k_defect(const Level<double>* __rest
             const double rFx = b.Fx - ((L.diag + kt) * u.Fx - NFx);
             const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
             const double rT = b.T - (L.c_v * u.T - se);
-            nrm = rE * rE + (rFx * rFx + rFy * rFy) * L.ic2 + rT * rT;
-            const Cell4<float> wb = { (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
-            const Cell4<float> g = { (float)rE, (float)rFx, (float)rFy, (float)rT };
-            const Cell4<float> z = { 0.f, 0.f, 0.f, 0.f };
-            M.w[k] = wb;
-            M.f[k] = g;
-            M.u[0][k] = z;
-        }
-        double sum = block_sum(nrm, red);
-        if (threadIdx.x == 0) partials[L.part_off + it.y] = sum * L.vol;
-        __syncthreads();
+            nrm += rE * rE + (rFx * rFx + rFy * rFy) * L.ic2 + rT * rT;
+            M.w[k] = Cell4<float>{ (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
+            M.f[k] = Cell4<float>{ (float)rE, (float)rFx, (float)rFy, (float)rT };
+            M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
+        });
+        const double sum = warp_sum(nrm);
+        if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncwarp();
     }
 }
 
@@ -1018,7 +1003,7 @@ template <typename R>
 void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int state_buf,
                   double* partials, int write_r, cudaStream_t s, bool delta)
 {
-    const int g = pgrid(wl);
+    const int g = pgrid_warps(wl), kThreads = kStripWarps * 32;
     if (delta && std::is_same<R, float>::value) {
         if (mode == APPLY_RESID)
             k_apply<R, APPLY_RESID, true><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
@@ -1040,7 +1025,7 @@ template <typename R>
 void launch_norm_state(const Level<R>* lv, WorkList wl, const Ctl* ctls, double* partials,
                        cudaStream_t s)
 {
-    k_norm_state<R><<<pgrid(wl), kThreads, 0, s>>>(lv, wl, ctls, partials);
+    k_norm_state<R><<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv, wl, ctls, partials);
 }
 
 template <typename R>
@@ -1114,7 +1099,7 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
                    double* partials, cudaStream_t s)
 {
-    k_defect<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, partials);
+    k_defect<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
 }
 
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,

@@ -12,6 +12,11 @@ CFL 100, at n x n cells):
   stepmixed one implicit step on a MIXED grid with L_max = --lmax
 The state and opacities are set once; each case runs its launches once after one
 untimed warm-up of the same launches, so `ncu -s` skips the warm-up.
+
+--tune-file PATH: the strip shapes of the sweep kernels.  If PATH exists its
+table is installed (no tuning launches, so a profiled run sees only the case's
+kernels); otherwise the autotuner runs and its table is written to PATH (run the
+command once without ncu first).
 """
 from __future__ import annotations
 
@@ -26,9 +31,19 @@ def main():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--lmax", type=int, default=6)
     ap.add_argument("--cycles", type=int, default=50, help="max_cycles of the step cases")
+    ap.add_argument("--tune-file", default=None)
     args = ap.parse_args()
 
     from paper_2208_14703_gb300 import inputs, m1
+    if args.tune_file:
+        import json
+        import os
+        if os.path.exists(args.tune_file):
+            with open(args.tune_file) as fh:
+                m1.set_tuning(json.load(fh))
+        else:
+            with open(args.tune_file, "w") as fh:
+                json.dump(m1.autotune(), fh)
     mixed = args.case in ("sweep32", "stepmixed")
     lmax = 1 if args.case.startswith("sweep") else args.lmax
     case = inputs.hot_square_2d(args.n, lmax=lmax)
