@@ -286,17 +286,22 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
     Cell4<R> o;
     R A = w0 + w1 * diag;
     R k = w1 * ka;
-    R iF = Fm<R>::rcp(w0 + w1 * (diag + kt));
-    o.Fx = bFx * iF;
-    o.Fy = bFy * iF;
     R C = w0 + w1 * c_v;
     ok = true;
     if (k == R(0)) {
+        const R iF = Fm<R>::rcp(w0 + w1 * (diag + kt));
+        o.Fx = bFx * iF;
+        o.Fy = bFy * iF;
         o.T = bT / C;
         o.E = bE / A;
         return o;
     }
-    R iAk = Fm<R>::rcp(A + k);
+    // one reciprocal serves both denominators: 1/a = b / (a b), 1/b = a / (a b)
+    const R dF = w0 + w1 * (diag + kt), dE = A + k;
+    const R ip = Fm<R>::rcp(dF * dE);
+    const R iF = dE * ip, iAk = dF * ip;
+    o.Fx = bFx * iF;
+    o.Fy = bFy * iF;
     R K = k * A * a_r * iAk;
     R Rr = bT + k * bE * iAk;
     R T = Quartic<R>::solve(C, K, Rr, ok);

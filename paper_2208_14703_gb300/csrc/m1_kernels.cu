@@ -38,12 +38,12 @@ __device__ __forceinline__ void load_level(Level<R>& dst, const Level<R>* src)
 // (tau* = the largest admissible step from u along f).  The admissible set is
 // convex, so when u + (dtau / theta) f is admissible tau* >= dtau / theta and
 // the step is dtau: the divisions and the square root of tau* are needed only
-// in cells where the bound may bind.
+// in cells where the bound may bind.  s = dtau / theta is passed in (once per
+// strip).
 template <typename R>
 __device__ __forceinline__ R limited_step(const Cell4<R>& u, const Cell4<R>& f, R dtau, R theta,
-                                          R c)
+                                          R s, R c)
 {
-    const R s = dtau / theta;
     const Cell4<R> p = { u.E + s * f.E, u.Fx + s * f.Fx, u.Fy + s * f.Fy, u.T + s * f.T };
     if (p.E > R(0) && p.T > R(0) && p.Fx * p.Fx + p.Fy * p.Fy <= c * c * p.E * p.E) return dtau;
     return fmin(dtau, theta * max_admissible_step(u, f, c));
@@ -116,6 +116,20 @@ __device__ __forceinline__ Staged<R> stage_raw(const Level<R>& L, const Raw<R>& 
     return o;
 }
 
+// The pseudo-time constants of a sweep, read once per strip: dtau_im, theta_ex
+// and dtau_im / theta_ex.
+template <typename R>
+struct Pseudo {
+    R dtau, theta, s;
+};
+
+template <typename R>
+__device__ __forceinline__ Pseudo<R> pseudo_of(const Ctl* ctl)
+{
+    const double dtau = ctl->dtau, theta = ctl->theta_ex;
+    return Pseudo<R>{ (R)dtau, (R)theta, (R)(dtau / theta) };
+}
+
 // The update of one strip cell (lanes 1..30): neighbour operators of Eq. (9)
 // from the staged west/east (shuffled) and south/north rows, then the local
 // solve of a Jacobi sweep (Algorithm 1) or of the fused pseudo-time step
@@ -127,7 +141,7 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
                                             const Staged<R>& next, const Staged<R>& cur,
                                             const Cell4<R>& b, const Sig2<R>& sg, size_t k,
                                             int out_buf, bool two_d, const Cell4<R>& u,
-                                            const Cell4<R>& wb)
+                                            const Cell4<R>& wb, const Pseudo<R>& ps)
 {
     const R c = L.c, bx = L.bx, by = L.by;
     R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
@@ -151,10 +165,9 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
     } else {
         // explicit half: u~ = u + tau f, tau = min(dtau, theta tau*); implicit half:
         // one Jacobi sweep of u + dtau A(u) = u~ from the old iterate.
-        const R dtau = (R)ctl->dtau;
-        const R theta = (R)ctl->theta_ex;
+        const R dtau = ps.dtau, theta = ps.theta, dts = ps.s;
         if (!DELTA) {
-            const R tau = limited_step(u, b, dtau, theta, c);
+            const R tau = limited_step(u, b, dtau, theta, dts, c);
             out = local_solve<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r,
                                  u.E + tau * b.E + dtau * NE, u.Fx + tau * b.Fx + dtau * NFx,
                                  u.Fy + tau * b.Fy + dtau * NFy, u.T + tau * b.T, ok);
@@ -166,7 +179,7 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
             const Cell4<R> aw = L.aw[k];
             const Cell4<R> full = { wb.E + u.E, wb.Fx + u.Fx, wb.Fy + u.Fy, wb.T + u.T };
             const Cell4<R> ff = { aw.E + b.E, aw.Fx + b.Fx, aw.Fy + b.Fy, aw.T + b.T };
-            const R tau = limited_step(full, ff, dtau, theta, c);
+            const R tau = limited_step(full, ff, dtau, theta, dts, c);
             const R lim = tau - dtau;
             out = local_solve_delta<R>(R(1), dtau, L.diag, ka, kt, L.c_v, L.a_r, wb.T,
                                        u.E + tau * b.E + lim * aw.E + dtau * NE,
@@ -200,6 +213,7 @@ __device__ __forceinline__ void strip_regs(const Level<R>& L, Ctl* ctl, int2 it,
     const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
     const bool own = lane >= 1 && lane <= kStripW && i < nx;
     const int rows = min(L.sh, ny - y0);
+    const Pseudo<R> ps = PSEUDO ? pseudo_of<R>(ctl) : Pseudo<R>{};
     Staged<R> prev{}, cur, next{};
     Raw<R> rn{};
     if (two_d) {
@@ -229,7 +243,7 @@ __device__ __forceinline__ void strip_regs(const Level<R>& L, Ctl* ctl, int2 it,
                 else { u = src[k]; wb = L.w[k]; }
             }
             update_cell<R, PSEUDO, DELTA>(L, ctl, wv, ev, prev, next, cur, b, sg, k, out_buf,
-                                          two_d, u, wb);
+                                          two_d, u, wb, ps);
         }
         prev = cur;
         cur = next;
@@ -247,8 +261,10 @@ __device__ __forceinline__ void load_level_warp(Level<R>& L, const Level<R>* src
 }
 
 // Persistent sweep over every listed (instance, strip): one warp per item.
+// FP64 instances are held to 128 registers (8 blocks per SM): one register
+// more (the pseudo-time variant) cost 4% of the FP64 step on GB300.
 template <typename R, bool PSEUDO, bool DELTA = false>
-__global__ void __launch_bounds__(kStripWarps * 32) k_sweep(const Level<R>* __restrict__ lv,
+__global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k_sweep(const Level<R>* __restrict__ lv,
                                                             WorkList wl, Ctl* __restrict__ ctls,
                                                             int in_buf, int out_buf)
 {
@@ -337,6 +353,7 @@ __device__ __forceinline__ void row_1d32(const Level<float>& L, Ctl* ctl, int2 i
     const int i = min(x0 - 1 + lane, nx);
     const bool own = lane >= 1 && lane <= kStripW && i < nx;
     const bool fast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const Pseudo<float> ps = PSEUDO ? pseudo_of<float>(ctl) : Pseudo<float>{};
     const Staged<float> cur = stage_raw<float, true>(L, load_raw<float, true>(L, src, i, 0, fast));
     const Staged<float> wv = shfl_staged(cur, (lane + 31) & 31);
     const Staged<float> ev = shfl_staged(cur, (lane + 1) & 31);
@@ -345,7 +362,7 @@ __device__ __forceinline__ void row_1d32(const Level<float>& L, Ctl* ctl, int2 i
         Cell4<float> u{}, wb{};
         if (PSEUDO) { u = src[k]; wb = L.w[k]; }
         update_cell<float, PSEUDO, true>(L, ctl, wv, ev, cur, cur, cur, L.f[k], L.sig[k], k,
-                                         out_buf, false, u, wb);
+                                         out_buf, false, u, wb, ps);
     }
 }
 
@@ -360,6 +377,7 @@ __device__ __forceinline__ void strip_ring32(const Level<float>& L, Ctl* ctl, in
     const bool own = lane >= 1 && lane <= kStripW && i < nx;
     const int rows = min(L.sh, ny - y0);
     const int last = y0 + rows;               // the last row the strip reads
+    const Pseudo<float> ps = PSEUDO ? pseudo_of<float>(ctl) : Pseudo<float>{};
     // ring slot of row q: (q - y0 + 1) mod kRing
     for (int q = y0 - 1; q <= y0 + 2; ++q) issue_row32(L, src, ring[(q - y0 + 1) & 3], i, q, last,
                                                        lane, own);
@@ -385,7 +403,7 @@ __device__ __forceinline__ void strip_ring32(const Level<float>& L, Ctl* ctl, in
             Cell4<float> u{}, wb{};
             if (PSEUDO) { u = S.e[lane]; wb = S.w[lane]; }
             update_cell<float, PSEUDO, true>(L, ctl, wv, ev, prev, next, cur, b, sg, k, out_buf,
-                                             true, u, wb);
+                                             true, u, wb, ps);
         }
         prev = cur;
         cur = next;
