@@ -65,9 +65,10 @@ SWEEP64_TRAFFIC_PER_CELL = 457.0e6 / (2048 * 2048)
 #     reciprocal of 2 + s 6, coefficients 4, P 8)
 #   neighbour operators 26 (x faces 13, y faces 13)
 #   opacity products and right-hand sides 6
-#   local solve 59 (two reciprocals 12, flux 2, quartic setup 9, two FP64
-#     Newton polish steps of 14 after the FP32 iteration, E 4 and checks)
-SWEEP_OPS = 39 + 26 + 6 + 59
+#   local solve 48 (one reciprocal for both denominators 10, flux 2, quartic
+#     setup and conversions 9, one FP64 Halley step after the FP32 Newton
+#     iteration 23, E 4)
+SWEEP_OPS = 39 + 26 + 6 + 48
 # GB300 FP64 pipe: 2 operations per clock per SM (nominal 1.25 TFLOP/s counts a
 # DFMA as 2 flops): 152 SMs x 2 x 2.07 GHz.
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
