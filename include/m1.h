@@ -194,13 +194,15 @@ m1_status m1_batch_implicit_step(m1_batch_t b, const double* dt, const m1_solve_
  * length dt.  A scheduler thread admits queued requests in arrival order into
  * free slots while their level hierarchies fit hbm_budget_bytes, copies the
  * state in on the device (it stays resident for all steps), and launches V-cycle
- * graphs over every active slot; a slot whose step converged starts its next
- * step at once, and a finished request's state is copied back into its grid
- * and its slot and budget are freed, all between V-cycles, so requests arriving
- * while others run join the running batch.  The caller must not use a
- * submitted grid until its ticket completes.  Submit, poll, wait and stats are
- * thread safe.  Step latency is the host time from the start of a step to the
- * poll (every 2 cycles) that sees it converged. */
+ * graphs over every active slot, one cycle at a time; while a cycle runs it
+ * reads the control blocks left by the previous one: a slot whose step
+ * converged starts its next step (behind the running cycle), and a finished
+ * request's state is copied back into its grid and its slot and budget are
+ * freed, all between V-cycles, so requests arriving while others run join the
+ * running batch.  The caller must not use a submitted grid until its ticket
+ * completes.  Submit, poll, wait and stats are thread safe.  Step latency is
+ * the host time from the start of a step to the reading that sees it
+ * converged. */
 typedef struct m1_server* m1_server_t;
 typedef struct {
     long long requests_done, steps_done, cycles;

@@ -553,6 +553,21 @@ void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
     }
 }
 
+// The FAS right-hand side of coarse level l (Eq. (24)); in the correction form
+// with the base operator A(w_l) in the same pass.
+template <typename R>
+void Engine<R>::fas_rhs(int l, cudaStream_t s)
+{
+    Level<R>* dl = d + (size_t)l * cap;
+    if constexpr (std::is_same<R, float>::value) {
+        if (delta) {
+            launch_fas_aw32(dl, strips[l].view(), ctl, s);
+            return;
+        }
+    }
+    launch_apply<R>(dl, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+}
+
 // One V-cycle of Algorithm 4 over every instance.  tail: end with the fine
 // residual norm and the stop test (the mixed-precision driver does its own).
 template <typename R>
@@ -566,8 +581,7 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
             sweeps_fine(cur[0], p.nu0, s);
             launch_apply<R>(dl, strips[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
         } else {
-            if (delta) launch_apply<R>(dl, strips[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
-            launch_apply<R>(dl, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+            fas_rhs(l, s);
             pseudo(l, cur[l], p.m, true, s);
             launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
         }
@@ -577,9 +591,7 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         sweeps_fine(cur[0], p.nu0, s);
     } else {
         const int l = L - 1;
-        if (delta)
-            launch_apply<R>(d + (size_t)l * cap, strips[l].view(), ctl, APPLY_A, -2, nullptr, 0, s, false);
-        launch_apply<R>(d + (size_t)l * cap, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
+        fas_rhs(l, s);
         pseudo(l, cur[l], p.mc, true, s);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -599,7 +611,8 @@ template <typename R>
 long long Engine<R>::kernels_per_cycle(const Params& p) const
 {
     if (L == 1) return p.nu0 + 2;
-    const int aw = delta ? 1 : 0;                      // A(w) of the base (correction form)
+    // the correction form computes A(w) in the FAS right-hand side kernel (FP32)
+    const int aw = (delta && !std::is_same<R, float>::value) ? 1 : 0;
     long long k = p.nu0 + 2;                           // fine pre-smooth, residual, restrict
     k += (long long)(L - 2) * (p.m + 3 + aw);          // FAS rhs, pseudo, residual, restrict
     k += 1 + p.mc + aw;                                // coarsest
@@ -953,9 +966,9 @@ m1_status Engine<R>::copy_slot_out(int slot, Engine<R>& dst)
 
 // Bring a finished slot's result into buffer 0 (where its next step starts).
 template <typename R>
-m1_status Engine<R>::settle(int slot)
+m1_status Engine<R>::settle(int slot, int result_buf)
 {
-    if (ctl_h[slot].result_buf == 1)
+    if (result_buf == 1)
         M1_CK(cudaMemcpyAsync(h[slot].u[0], h[slot].u[1], sizeof(Cell4<R>) * h[slot].n,
                               cudaMemcpyDeviceToDevice, stream));
     return M1_OK;
@@ -1006,13 +1019,6 @@ m1_status PlainModel::sv_cycles(const Params& p, int n)
     return M1_OK;
 }
 
-m1_status PlainModel::sv_read(std::vector<Ctl>& out)
-{
-    M1_CK(cudaMemcpyAsync(e.ctl_h, e.ctl, sizeof(Ctl) * e.cap, cudaMemcpyDeviceToHost, e.stream));
-    M1_CK(cudaStreamSynchronize(e.stream));
-    out.assign(e.ctl_h, e.ctl_h + e.cap);
-    return M1_OK;
-}
 
 m1_status MixedModel::sv_init(int cap, int L, cudaStream_t s)
 {
@@ -1098,13 +1104,6 @@ m1_status MixedModel::sv_cycles(const Params& p, int n)
     return M1_OK;
 }
 
-m1_status MixedModel::sv_read(std::vector<Ctl>& out)
-{
-    M1_CK(cudaMemcpyAsync(hi.ctl_h, hi.ctl, sizeof(Ctl) * hi.cap, cudaMemcpyDeviceToHost, hi.stream));
-    M1_CK(cudaStreamSynchronize(hi.stream));
-    out.assign(hi.ctl_h, hi.ctl_h + hi.cap);
-    return M1_OK;
-}
 
 // ---------------------------------------------------------------------------
 m1_status PlainModel::create(const std::vector<m1_grid_desc>& descs, cudaStream_t s)

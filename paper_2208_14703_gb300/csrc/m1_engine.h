@@ -131,6 +131,7 @@ struct Engine {
     m1_status set_inflow(int i, int side, const double* E, const double* Fx, const double* Fy);
     m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev);
     void sweeps_fine(int& cur, int count, cudaStream_t s);
+    void fas_rhs(int l, cudaStream_t s);
     void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s);
     void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true);
     long long kernels_per_cycle(const Params& p) const;
@@ -153,7 +154,7 @@ struct Engine {
     m1_status set_init_lists(const std::vector<int>& slots);
     m1_status copy_slot_in(int slot, Engine<R>& src);
     m1_status copy_slot_out(int slot, Engine<R>& dst);
-    m1_status settle(int slot);
+    m1_status settle(int slot, int result_buf);
 };
 
 // One or more instances behind the C ABI: the plain FP64 engine, or the mixed
@@ -182,8 +183,9 @@ struct Model {
     virtual m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
                                const std::vector<m1_solve_params>& ps) = 0;
     virtual m1_status sv_cycles(const Params& p, int n) = 0;
-    virtual m1_status sv_read(std::vector<Ctl>& out) = 0;
-    virtual m1_status sv_settle(int slot) = 0;
+    virtual m1_status sv_settle(int slot, int result_buf) = 0;
+    virtual Ctl* sv_ctl() = 0;                           // device control blocks [cap]
+    virtual cudaStream_t sv_stream() = 0;
     virtual int sv_graph_cycles() const { return 1; }   // V-cycles per graph launch
 };
 
@@ -229,8 +231,9 @@ struct PlainModel : Model {
     m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
                        const std::vector<m1_solve_params>& ps) override;
     m1_status sv_cycles(const Params& p, int n) override;
-    m1_status sv_read(std::vector<Ctl>& out) override;
-    m1_status sv_settle(int slot) override { return e.settle(slot); }
+    m1_status sv_settle(int slot, int rb) override { return e.settle(slot, rb); }
+    Ctl* sv_ctl() override { return e.ctl; }
+    cudaStream_t sv_stream() override { return e.stream; }
     int sv_graph_cycles() const override { return e.graph_cycles; }
 };
 
@@ -273,8 +276,9 @@ struct MixedModel : Model {
     m1_status sv_begin(const std::vector<int>& slots, const std::vector<double>& dts,
                        const std::vector<m1_solve_params>& ps) override;
     m1_status sv_cycles(const Params& p, int n) override;
-    m1_status sv_read(std::vector<Ctl>& out) override;
-    m1_status sv_settle(int) override { return M1_OK; }
+    m1_status sv_settle(int, int) override { return M1_OK; }
+    Ctl* sv_ctl() override { return hi.ctl; }
+    cudaStream_t sv_stream() override { return hi.stream; }
 };
 
 m1_status make_model(const std::vector<m1_grid_desc>& descs, cudaStream_t s,

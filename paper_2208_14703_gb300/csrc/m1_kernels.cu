@@ -567,6 +567,78 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __re
     }
 }
 
+// The coarse-level right-hand side of the correction form in one pass: the base
+// operator A(w) (kept for the pseudo-time steps of the cycle) and the FAS
+// right-hand side f = [A(w + v) - A(w)] + r of the restricted correction v
+// (Eq. (24) in correction form).  Both come from the same staged rows: one load
+// of w and v per cell feeds the closure of w and the closure difference.
+__global__ void __launch_bounds__(kStripWarps * 32) k_fas_aw32(const Level<float>* __restrict__ lv,
+                                                               WorkList wl,
+                                                               Ctl* __restrict__ ctls)
+{
+    __shared__ Level<float> Ls[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<float>& L = Ls[wib];
+    const int nw = *wl.count;
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
+        const int2 it = wl.items[w];
+        if (skip(ctls, it.x)) continue;
+        load_level_warp(L, lv + it.x, lane);
+        const int nx = L.nx, ny = L.ny;
+        const bool two_d = L.dim == 2;
+        const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+        const int i = min(x0 - 1 + lane, nx);
+        const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+        const bool own = lane >= 1 && lane <= kStripW && i < nx;
+        const int rows = min(L.sh, ny - y0);
+        auto stage2 = [&](const Raw<float>& r, Staged<float>& sw, Staged<float>& sd) {
+            Raw<float> rw;
+            rw.c = r.w;
+            sw = stage_raw<float, false>(L, rw);
+            sd = stage_raw<float, true>(L, r);
+        };
+        Staged<float> pw{}, cw, nw_{}, pd{}, cd, nd{};
+        Raw<float> rn{};
+        if (two_d) {
+            stage2(load_raw<float, true>(L, L.v, i, y0 - 1, colfast && y0 >= 1), pw, pd);
+            rn = load_raw<float, true>(L, L.v, i, y0 + 1, colfast && y0 + 1 < ny);
+        }
+        stage2(load_raw<float, true>(L, L.v, i, y0, colfast), cw, cd);
+        size_t k = (size_t)y0 * nx + i;
+        for (int r = 0; r < rows; ++r, k += nx) {
+            const int j = y0 + r;
+            if (two_d) {
+                stage2(rn, nw_, nd);
+                if (r + 1 < rows) rn = load_raw<float, true>(L, L.v, i, j + 2, colfast && j + 2 < ny);
+            }
+            const Staged<float> wvw = shfl_staged(cw, (lane + 31) & 31);
+            const Staged<float> evw = shfl_staged(cw, (lane + 1) & 31);
+            const Staged<float> wvd = shfl_staged(cd, (lane + 31) & 31);
+            const Staged<float> evd = shfl_staged(cd, (lane + 1) & 31);
+            if (own) {
+                const Sig2<float> sg = L.sig[k];
+                const float ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+                const Cell4<float> wb = L.w[k], v = L.v[k];
+                float NE, NFx, NFy;
+                strip_neighbours(L, wvw, evw, pw, nw_, two_d, NE, NFx, NFy);
+                const float T2 = wb.T * wb.T, sw = ka * (wb.E - L.a_r * T2 * T2);
+                L.aw[k] = Cell4<float>{ L.diag * wb.E + sw - NE, (L.diag + kt) * wb.Fx - NFx,
+                                        (L.diag + kt) * wb.Fy - NFy, L.c_v * wb.T - sw };
+                strip_neighbours(L, wvd, evd, pd, nd, two_d, NE, NFx, NFy);
+                const float sd = ka * (v.E - L.a_r * quartic_delta(wb.T, v.T));
+                const Cell4<float> rr = L.r[k];
+                L.f[k] = Cell4<float>{ (L.diag * v.E + sd - NE) + rr.E,
+                                       ((L.diag + kt) * v.Fx - NFx) + rr.Fx,
+                                       ((L.diag + kt) * v.Fy - NFy) + rr.Fy,
+                                       (L.c_v * v.T - sd) + rr.T };
+            }
+            pw = cw; cw = nw_;
+            pd = cd; cd = nd;
+        }
+        __syncwarp();
+    }
+}
+
 // Norm of the right-hand side f of each instance (for ||b||): per-strip partials.
 template <typename R>
 __global__ void __launch_bounds__(kStripWarps * 32) k_norm_state(const Level<R>* __restrict__ lv,
@@ -1037,6 +1109,11 @@ void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int stat
         k_apply<R, APPLY_FAS><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
     else
         k_apply<R, APPLY_A><<<g, kThreads, 0, s>>>(lv, wl, ctls, state_buf, partials, write_r);
+}
+
+void launch_fas_aw32(const Level<float>* lv, WorkList wl, Ctl* ctls, cudaStream_t s)
+{
+    k_fas_aw32<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv, wl, ctls);
 }
 
 template <typename R>

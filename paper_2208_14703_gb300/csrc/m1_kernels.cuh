@@ -44,6 +44,8 @@ template <typename R>
 void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c, unsigned int* bad,
                         cudaStream_t s);
 
+// FP32 correction form, coarse level: A(w) -> aw and f = [A(w + v) - A(w)] + r.
+void launch_fas_aw32(const Level<float>* lv, WorkList wl, Ctl* ctls, cudaStream_t s);
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
                    double* partials, cudaStream_t s);
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,

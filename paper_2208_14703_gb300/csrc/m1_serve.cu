@@ -5,13 +5,17 @@
 // The scheduler thread admits queued requests in arrival order into free slots
 // of one engine while their level hierarchies fit the HBM budget (the state is
 // copied device to device; it stays resident for all of the request's steps),
-// and launches V-cycle graphs over every active slot.  Every two cycles it reads
-// the slots' control blocks: a slot whose step converged starts its next step
-// at once (or, after its last step, copies the result back into the caller's
-// grid and frees its slot and budget), and queued requests join between cycles.
-// Instances never share arithmetic, so a request's result is the same served
-// alone or in a mix.  Step latency is the host time from the start of a step to
-// the poll that sees it converged.
+// and launches V-cycle graphs over every active slot, one cycle per batch.
+// After queueing a batch it copies the control blocks asynchronously into a
+// pinned snapshot and then handles the snapshot of the previous batch while the
+// new one runs, so the GPU does not wait for the host: a slot whose step
+// converged starts its next step (queued behind the running batch), or, after
+// its last step, its result is copied back into the caller's grid and its slot
+// and budget are freed; queued requests join between batches.  A snapshot
+// taken before a slot's step was started says nothing about that step and is
+// ignored for it.  Instances never share arithmetic, so a request's result is
+// the same served alone or in a mix.  Step latency is the host time from the
+// start of a step to the handling of the snapshot that sees it converged.
 #include <m1.h>
 
 #include <algorithm>
@@ -44,6 +48,7 @@ struct Request {
     m1_solve_params params{};
     size_t bytes = 0;
     int slot = -1;
+    long long started_at = 0;     // batches queued before the current step was started
     int steps_done = 0;
     int status = M1_PENDING;
     bool finished = false;
@@ -63,7 +68,7 @@ struct m1_server {
     m1::Params structure{};
     int precision = 0, L = 0, max_slots = 0, device = 0;
     size_t budget = 0, used = 0, peak = 0;
-    int poll_cycles = 2;
+    int poll_cycles = 1;
     bool stop = false;
     int error = M1_OK;
     unsigned long long next_ticket = 1;
@@ -72,11 +77,26 @@ struct m1_server {
     long long steps_done = 0, requests_done = 0, cycles = 0;
     double t_first = 0.0, t_last = 0.0;
     std::thread th;
+    // pipelined snapshots of the control blocks (two pinned buffers)
+    Ctl* snap[2] = { nullptr, nullptr };
+    cudaEvent_t snap_ev[2] = { nullptr, nullptr };
+    long long batches = 0;        // batches queued so far
+    long long handled = 0;        // batches whose snapshot has been handled
 
+    ~m1_server();
     void loop();
     m1_status admit_and_start(std::vector<std::shared_ptr<Request>>& admit);
     m1_status service_cycles();
+    m1_status handle_snapshot(long long b);
 };
+
+m1_server::~m1_server()
+{
+    for (int k = 0; k < 2; ++k) {
+        if (snap_ev[k]) cudaEventDestroy(snap_ev[k]);
+        if (snap[k]) cudaFreeHost(snap[k]);
+    }
+}
 
 m1_status m1_server::admit_and_start(std::vector<std::shared_ptr<Request>>& admit)
 {
@@ -98,29 +118,45 @@ m1_status m1_server::admit_and_start(std::vector<std::shared_ptr<Request>>& admi
     }
     M1_TRY(model->sv_begin(slots, dts, ps));
     const double t = now_s();
-    for (auto& r : admit) r->t_step = t;
+    for (auto& r : admit) { r->t_step = t; r->started_at = batches; }
     return M1_OK;
 }
 
-// A few V-cycles over every active slot, then the per-slot bookkeeping.
+// Queue a batch of V-cycles over every active slot and an asynchronous
+// snapshot of the control blocks, then handle the previous batch's snapshot.
 m1_status m1_server::service_cycles()
 {
     M1_TRY(model->sv_cycles(structure, poll_cycles));
-    std::vector<Ctl> ctl;
-    M1_TRY(model->sv_read(ctl));
-    const double t = now_s();
+    const long long b = ++batches;
+    const int nb = (int)(b & 1);
+    M1_CK(cudaMemcpyAsync(snap[nb], model->sv_ctl(), sizeof(Ctl) * max_slots,
+                          cudaMemcpyDeviceToHost, model->sv_stream()));
+    M1_CK(cudaEventRecord(snap_ev[nb], model->sv_stream()));
     {
         std::lock_guard<std::mutex> lk(mu);
         cycles += (long long)poll_cycles * model->sv_graph_cycles();
     }
+    if (b > 1) M1_TRY(handle_snapshot(b - 1));
+    return M1_OK;
+}
+
+// Per-slot bookkeeping from the snapshot taken after batch b.
+m1_status m1_server::handle_snapshot(long long b)
+{
+    if (b <= handled) return M1_OK;
+    handled = b;
+    const int nb = (int)(b & 1);
+    M1_CK(cudaEventSynchronize(snap_ev[nb]));
+    const Ctl* ctl = snap[nb];
+    const double t = now_s();
     std::vector<int> restart;
     std::vector<double> rdts;
     std::vector<m1_solve_params> rps;
     bool removed = false;
     for (int s = 0; s < max_slots; ++s) {
         auto r = slot_req[s];
-        if (!r || !ctl[s].active || !ctl[s].done) continue;
-        M1_TRY(model->sv_settle(s));
+        if (!r || b <= r->started_at || !ctl[s].active || !ctl[s].done) continue;
+        M1_TRY(model->sv_settle(s, ctl[s].result_buf));
         const Ctl& c = ctl[s];
         m1_step_stats st{};
         st.cycles = c.kappa;
@@ -166,7 +202,7 @@ m1_status m1_server::service_cycles()
     if (!restart.empty()) {
         M1_TRY(model->sv_begin(restart, rdts, rps));
         const double t2 = now_s();
-        for (int s : restart) slot_req[s]->t_step = t2;
+        for (int s : restart) { slot_req[s]->t_step = t2; slot_req[s]->started_at = batches; }
     }
     return M1_OK;
 }
@@ -236,6 +272,11 @@ m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int
     s->max_slots = max_slots;
     s->budget = hbm_budget_bytes;
     s->slot_req.assign(max_slots, nullptr);
+    for (int k = 0; k < 2; ++k) {
+        if (cudaMallocHost(&s->snap[k], sizeof(m1::Ctl) * max_slots) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->snap_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return M1_ERR_OOM;
+    }
     cudaGetDevice(&s->device);
     m1_server* raw = s.release();
     raw->th = std::thread([raw] { raw->loop(); });
