@@ -54,8 +54,8 @@ def peaks():
 # Bytes: read the iterate u, the right-hand side b and (sigma_a, sigma_s); write u'.
 SWEEP_BYTES = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8
 # DRAM bytes per cell of the FP64 sweep kernel measured by ncu on one 2048^2
-# launch (dram__bytes_read.sum + dram__bytes_write.sum = 457.0 MB / 4,194,304 cells)
-SWEEP64_TRAFFIC_PER_CELL = 457.0e6 / (2048 * 2048)
+# launch (dram__bytes_read.sum + dram__bytes_write.sum = 457.8 MB / 4,194,304 cells)
+SWEEP64_TRAFFIC_PER_CELL = 457.8e6 / (2048 * 2048)
 # FP64 work of one fine Jacobi update (2D), counted in FP64-pipe operations
 # (each DFMA, DMUL or DADD is one issue slot; a reciprocal = hardware estimate +
 # 4 DFMA of Newton refinement = 5; a square root = estimate + 8) on the
@@ -76,8 +76,9 @@ FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 # correction e, the base state w and the source g (3 x 16 B), (sigma_a, sigma_s)
 # (8 B); write e' (16 B).
 SWEEP32_BYTES = 3 * 16 + 8 + 16
-# DRAM bytes per cell of that kernel, ncu on one 2048^2 launch (292.2 MB)
-SWEEP32_TRAFFIC_PER_CELL = 292.2e6 / (2048 * 2048)
+# DRAM bytes per cell of that kernel (cp.async staging, the tuned choice), ncu on
+# one 2048^2 launch (306.5 MB)
+SWEEP32_TRAFFIC_PER_CELL = 306.5e6 / (2048 * 2048)
 
 
 class ClockSampler:
@@ -433,7 +434,7 @@ def main():
                            "peak in MEASURED_PEAKS.json)",
             "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL or DADD)",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                              "2048^2 launch (457.0 MB), scaled to 1024^2 by cells",
+                              "2048^2 launch (457.8 MB), scaled to 1024^2 by cells",
             "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / pk["hbm_gbs"], "bytes_per_cell": SWEEP_BYTES}}
 
