@@ -370,6 +370,14 @@ m1_status Engine<R>::rebuild()
         M1_TRY(upload_list(strips[l]));
         M1_TRY(upload_list(chunks[l]));
     }
+    // a captured cycle launches nothing for an empty list: re-capture when a
+    // list becomes empty or stops being empty
+    std::vector<char> sig;
+    for (int l = 0; l < L; ++l) {
+        sig.push_back(strips[l].n > 0);
+        sig.push_back(chunks[l].n > 0);
+    }
+    if (sig != list_sig) { list_sig = sig; graph_dirty = true; }
     // level-0 sweeps of all slots share one launch: the cp.async kernel when
     // the slots holding most level-0 cells chose it
     long long with = 0, without = 0;
@@ -542,12 +550,13 @@ template <typename R>
 void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
 {
     Level<R>* dl = d + (size_t)l * cap;
+    const bool go = strips[l].n > 0;          // an empty level only advances the buffer
     for (int k = 0; k < m; ++k) {
         if (k == 0 && from_v) {
-            launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta);
+            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta);
             cur = 0;
         } else {
-            launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta);
+            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta);
             cur = 1 - cur;
         }
     }
@@ -558,6 +567,7 @@ void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
 template <typename R>
 void Engine<R>::fas_rhs(int l, cudaStream_t s)
 {
+    if (strips[l].n == 0) return;
     Level<R>* dl = d + (size_t)l * cap;
     if constexpr (std::is_same<R, float>::value) {
         if (delta) {
@@ -583,9 +593,11 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         } else {
             fas_rhs(l, s);
             pseudo(l, cur[l], p.m, true, s);
-            launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
+            if (strips[l].n)
+                launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
         }
-        launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
+        if (chunks[l + 1].n)
+            launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
     }
     if (L == 1) {
         sweeps_fine(cur[0], p.nu0, s);
@@ -596,7 +608,8 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
     }
     for (int l = L - 2; l >= 0; --l) {
         Level<R>* dl = d + (size_t)l * cap;
-        launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
+        if (chunks[l].n)
+            launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
         if (l == 0) sweeps_fine(cur[0], p.nu0, s);
         else pseudo(l, cur[l], p.m, false, s);
     }

@@ -110,6 +110,7 @@ struct Engine {
     int graph_cycles = 1;
     bool graph_dirty = true;
     bool ring0 = false;                     // level-0 sweeps take the cp.async kernel
+    std::vector<char> list_sig;             // which work lists were non-empty at capture
 
     ~Engine();
     std::vector<DevList*> all_lists();

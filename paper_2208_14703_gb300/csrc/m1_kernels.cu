@@ -496,6 +496,54 @@ __device__ __forceinline__ void strip_march(const Level<R>& L, int2 it, int lane
     }
 }
 
+template <typename R, int MODE, bool DELTA>
+__device__ __forceinline__ double apply_item(const Level<R>& L, int2 it, int lane, int state_buf,
+                                             int write_r)
+{
+    // state_buf: 0/1 the iterate, -1 the restricted iterate v, -2 the base w
+    const Cell4<R>* __restrict__ src =
+        state_buf == -2 ? L.w : (state_buf < 0 ? L.v : L.u[state_buf]);
+    const bool two_d = L.dim == 2;
+    double nrm = 0.0;
+    strip_march<R, DELTA>(L, it, lane, src, [&](size_t k, const Staged<R>& wv,
+                                                 const Staged<R>& ev, const Staged<R>& prev,
+                                                 const Staged<R>& next, const Staged<R>& cur) {
+        R NE, NFx, NFy;
+        strip_neighbours(L, wv, ev, prev, next, two_d, NE, NFx, NFy);
+        const Cell4<R> u = src[k];
+        const Sig2<R> sg = L.sig[k];
+        const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+        R src_e;
+        if (!DELTA) {
+            const R T2 = u.T * u.T;
+            src_e = ka * (u.E - L.a_r * T2 * T2);
+        } else {
+            // A(w + e) - A(w): source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
+            src_e = ka * (u.E - L.a_r * quartic_delta(cur.T, u.T));
+        }
+        Cell4<R> a;
+        a.E = L.diag * u.E + src_e - NE;
+        a.Fx = (L.diag + kt) * u.Fx - NFx;
+        a.Fy = (L.diag + kt) * u.Fy - NFy;
+        a.T = L.c_v * u.T - src_e;
+        if (MODE == APPLY_RESID) {
+            const Cell4<R> f = L.f[k];
+            const Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
+            if (write_r) L.r[k] = r;
+            nrm += (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * (double)L.ic2 +
+                   (double)r.T * r.T;
+        } else if (MODE == APPLY_FAS) {
+            const Cell4<R> r = L.r[k];
+            L.f[k] = Cell4<R>{ a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
+        } else if (state_buf == -2) {
+            L.aw[k] = a;
+        } else {
+            L.r[k] = a;
+        }
+    });
+    return nrm;
+}
+
 // A(u) of Eq. (12) (+ sources) at one level, per (instance, strip) item:
 //   APPLY_RESID  r = f - A(u) (Eq. (13)), written to L.r if write_r, and the
 //                weighted norm partial of the strip (partials != null)
@@ -518,47 +566,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __re
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
         load_level_warp(L, lv + it.x, lane);
-        // state_buf: 0/1 the iterate, -1 the restricted iterate v, -2 the base w
-        const Cell4<R>* __restrict__ src =
-            state_buf == -2 ? L.w : (state_buf < 0 ? L.v : L.u[state_buf]);
-        const bool two_d = L.dim == 2;
-        double nrm = 0.0;
-        strip_march<R, DELTA>(L, it, lane, src, [&](size_t k, const Staged<R>& wv,
-                                                     const Staged<R>& ev, const Staged<R>& prev,
-                                                     const Staged<R>& next, const Staged<R>& cur) {
-            R NE, NFx, NFy;
-            strip_neighbours(L, wv, ev, prev, next, two_d, NE, NFx, NFy);
-            const Cell4<R> u = src[k];
-            const Sig2<R> sg = L.sig[k];
-            const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-            R src_e;
-            if (!DELTA) {
-                const R T2 = u.T * u.T;
-                src_e = ka * (u.E - L.a_r * T2 * T2);
-            } else {
-                // A(w + e) - A(w): source difference ka (e_E - a_r ((T + e_T)^4 - T^4))
-                src_e = ka * (u.E - L.a_r * quartic_delta(cur.T, u.T));
-            }
-            Cell4<R> a;
-            a.E = L.diag * u.E + src_e - NE;
-            a.Fx = (L.diag + kt) * u.Fx - NFx;
-            a.Fy = (L.diag + kt) * u.Fy - NFy;
-            a.T = L.c_v * u.T - src_e;
-            if (MODE == APPLY_RESID) {
-                const Cell4<R> f = L.f[k];
-                const Cell4<R> r = { f.E - a.E, f.Fx - a.Fx, f.Fy - a.Fy, f.T - a.T };
-                if (write_r) L.r[k] = r;
-                nrm += (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * (double)L.ic2 +
-                       (double)r.T * r.T;
-            } else if (MODE == APPLY_FAS) {
-                const Cell4<R> r = L.r[k];
-                L.f[k] = Cell4<R>{ a.E + r.E, a.Fx + r.Fx, a.Fy + r.Fy, a.T + r.T };
-            } else if (state_buf == -2) {
-                L.aw[k] = a;
-            } else {
-                L.r[k] = a;
-            }
-        });
+        const double nrm = apply_item<R, MODE, DELTA>(L, it, lane, state_buf, write_r);
         if (MODE == APPLY_RESID && partials) {
             const double sum = warp_sum(nrm);
             if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
@@ -572,6 +580,61 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __re
 // right-hand side f = [A(w + v) - A(w)] + r of the restricted correction v
 // (Eq. (24) in correction form).  Both come from the same staged rows: one load
 // of w and v per cell feeds the closure of w and the closure difference.
+__device__ __forceinline__ void fas_aw32_item(const Level<float>& L, int2 it, int lane)
+{
+    const int nx = L.nx, ny = L.ny;
+    const bool two_d = L.dim == 2;
+    const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+    const int i = min(x0 - 1 + lane, nx);
+    const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const int rows = min(L.sh, ny - y0);
+    auto stage2 = [&](const Raw<float>& r, Staged<float>& sw, Staged<float>& sd) {
+        Raw<float> rw;
+        rw.c = r.w;
+        sw = stage_raw<float, false>(L, rw);
+        sd = stage_raw<float, true>(L, r);
+    };
+    Staged<float> pw{}, cw, nw_{}, pd{}, cd, nd{};
+    Raw<float> rn{};
+    if (two_d) {
+        stage2(load_raw<float, true>(L, L.v, i, y0 - 1, colfast && y0 >= 1), pw, pd);
+        rn = load_raw<float, true>(L, L.v, i, y0 + 1, colfast && y0 + 1 < ny);
+    }
+    stage2(load_raw<float, true>(L, L.v, i, y0, colfast), cw, cd);
+    size_t k = (size_t)y0 * nx + i;
+    for (int r = 0; r < rows; ++r, k += nx) {
+        const int j = y0 + r;
+        if (two_d) {
+            stage2(rn, nw_, nd);
+            if (r + 1 < rows) rn = load_raw<float, true>(L, L.v, i, j + 2, colfast && j + 2 < ny);
+        }
+        const Staged<float> wvw = shfl_staged(cw, (lane + 31) & 31);
+        const Staged<float> evw = shfl_staged(cw, (lane + 1) & 31);
+        const Staged<float> wvd = shfl_staged(cd, (lane + 31) & 31);
+        const Staged<float> evd = shfl_staged(cd, (lane + 1) & 31);
+        if (own) {
+            const Sig2<float> sg = L.sig[k];
+            const float ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+            const Cell4<float> wb = L.w[k], v = L.v[k];
+            float NE, NFx, NFy;
+            strip_neighbours(L, wvw, evw, pw, nw_, two_d, NE, NFx, NFy);
+            const float T2 = wb.T * wb.T, sw = ka * (wb.E - L.a_r * T2 * T2);
+            L.aw[k] = Cell4<float>{ L.diag * wb.E + sw - NE, (L.diag + kt) * wb.Fx - NFx,
+                                    (L.diag + kt) * wb.Fy - NFy, L.c_v * wb.T - sw };
+            strip_neighbours(L, wvd, evd, pd, nd, two_d, NE, NFx, NFy);
+            const float sd = ka * (v.E - L.a_r * quartic_delta(wb.T, v.T));
+            const Cell4<float> rr = L.r[k];
+            L.f[k] = Cell4<float>{ (L.diag * v.E + sd - NE) + rr.E,
+                                   ((L.diag + kt) * v.Fx - NFx) + rr.Fx,
+                                   ((L.diag + kt) * v.Fy - NFy) + rr.Fy,
+                                   (L.c_v * v.T - sd) + rr.T };
+        }
+        pw = cw; cw = nw_;
+        pd = cd; cd = nd;
+    }
+}
+
 __global__ void __launch_bounds__(kStripWarps * 32) k_fas_aw32(const Level<float>* __restrict__ lv,
                                                                WorkList wl,
                                                                Ctl* __restrict__ ctls)
@@ -584,57 +647,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_fas_aw32(const Level<float
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
         load_level_warp(L, lv + it.x, lane);
-        const int nx = L.nx, ny = L.ny;
-        const bool two_d = L.dim == 2;
-        const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
-        const int i = min(x0 - 1 + lane, nx);
-        const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
-        const bool own = lane >= 1 && lane <= kStripW && i < nx;
-        const int rows = min(L.sh, ny - y0);
-        auto stage2 = [&](const Raw<float>& r, Staged<float>& sw, Staged<float>& sd) {
-            Raw<float> rw;
-            rw.c = r.w;
-            sw = stage_raw<float, false>(L, rw);
-            sd = stage_raw<float, true>(L, r);
-        };
-        Staged<float> pw{}, cw, nw_{}, pd{}, cd, nd{};
-        Raw<float> rn{};
-        if (two_d) {
-            stage2(load_raw<float, true>(L, L.v, i, y0 - 1, colfast && y0 >= 1), pw, pd);
-            rn = load_raw<float, true>(L, L.v, i, y0 + 1, colfast && y0 + 1 < ny);
-        }
-        stage2(load_raw<float, true>(L, L.v, i, y0, colfast), cw, cd);
-        size_t k = (size_t)y0 * nx + i;
-        for (int r = 0; r < rows; ++r, k += nx) {
-            const int j = y0 + r;
-            if (two_d) {
-                stage2(rn, nw_, nd);
-                if (r + 1 < rows) rn = load_raw<float, true>(L, L.v, i, j + 2, colfast && j + 2 < ny);
-            }
-            const Staged<float> wvw = shfl_staged(cw, (lane + 31) & 31);
-            const Staged<float> evw = shfl_staged(cw, (lane + 1) & 31);
-            const Staged<float> wvd = shfl_staged(cd, (lane + 31) & 31);
-            const Staged<float> evd = shfl_staged(cd, (lane + 1) & 31);
-            if (own) {
-                const Sig2<float> sg = L.sig[k];
-                const float ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
-                const Cell4<float> wb = L.w[k], v = L.v[k];
-                float NE, NFx, NFy;
-                strip_neighbours(L, wvw, evw, pw, nw_, two_d, NE, NFx, NFy);
-                const float T2 = wb.T * wb.T, sw = ka * (wb.E - L.a_r * T2 * T2);
-                L.aw[k] = Cell4<float>{ L.diag * wb.E + sw - NE, (L.diag + kt) * wb.Fx - NFx,
-                                        (L.diag + kt) * wb.Fy - NFy, L.c_v * wb.T - sw };
-                strip_neighbours(L, wvd, evd, pd, nd, two_d, NE, NFx, NFy);
-                const float sd = ka * (v.E - L.a_r * quartic_delta(wb.T, v.T));
-                const Cell4<float> rr = L.r[k];
-                L.f[k] = Cell4<float>{ (L.diag * v.E + sd - NE) + rr.E,
-                                       ((L.diag + kt) * v.Fx - NFx) + rr.Fx,
-                                       ((L.diag + kt) * v.Fy - NFy) + rr.Fy,
-                                       (L.c_v * v.T - sd) + rr.T };
-            }
-            pw = cw; cw = nw_;
-            pd = cd; cd = nd;
-        }
+        fas_aw32_item(L, it, lane);
         __syncwarp();
     }
 }
@@ -672,8 +685,40 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_norm_state(const Level<R>*
 
 // ---------------------------------------------------------------------------
 // Full weighting, coarse cell (ic, jc) <- fine cells 2ic-1..2ic+1 (x) and
-// 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis.  Items are
-// (instance, 256-cell chunk of the coarse level).
+// 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis: the iterate of
+// buffer fine_buf, the residual and, in the correction form, the base w.
+template <typename R, bool DELTA>
+__device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>& Lc, int kc,
+                                              int fine_buf)
+{
+    const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
+    const int ic = kc % Lc.nx, jc = kc / Lc.nx;
+    const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
+    Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
+    const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+    for (int b = b0; b <= b1; ++b) {
+        const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
+        const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+        for (int a = -1; a <= 1; ++a) {
+            const R wt = wy * wgt[a + 1];
+            // correction form: the correction has zero inflow ghosts, the base
+            // carries the prescribed state
+            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
+            const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
+            av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
+            ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+            if (DELTA) {
+                const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
+                aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+            }
+        }
+    }
+    Lc.v[kc] = av;
+    Lc.r[kc] = ar;
+    if (DELTA) Lc.w[kc] = aw;
+}
+
+// Items are (instance, 256-cell chunk of the coarse level).
 template <typename R, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restrict__ lvf,
                                                        const Level<R>* __restrict__ lvc,
@@ -682,7 +727,6 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
 {
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
-    const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
@@ -690,32 +734,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
         load_level(Lc, lvc + it.x);
         __syncthreads();
         const int kc = it.y * kThreads + threadIdx.x;
-        if (kc < Lc.n) {
-            const int ic = kc % Lc.nx, jc = kc / Lc.nx;
-            const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
-            Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
-            const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
-            for (int b = b0; b <= b1; ++b) {
-                const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
-                const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
-                for (int a = -1; a <= 1; ++a) {
-                    const R wt = wy * wgt[a + 1];
-                    // correction form: the correction has zero inflow ghosts, the base
-                    // carries the prescribed state
-                    const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
-                    const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
-                    av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
-                    ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
-                    if (DELTA) {
-                        const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
-                        aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
-                    }
-                }
-            }
-            Lc.v[kc] = av;
-            Lc.r[kc] = ar;
-            if (DELTA) Lc.w[kc] = aw;
-        }
+        if (kc < Lc.n) restrict_cell<R, DELTA>(Lf, Lc, kc, fine_buf);
         __syncthreads();
     }
 }
@@ -756,6 +775,39 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>*
 // u_l += P(u_{l+1} - v_{l+1}) per fine cell (fine 2i <- coarse i, fine 2i+1 <-
 // half of coarse i and i+1; tensor product in 2D); a target outside the
 // admissible set is replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).
+template <typename R, bool DELTA>
+__device__ __forceinline__ void prolong_cell(const Level<R>& Lc, const Level<R>& Lf, int k,
+                                             int coarse_buf, int fine_buf, Ctl* ctl)
+{
+    const int i = k % Lf.nx, j = k / Lf.nx;
+    const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
+    const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
+    const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
+    const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
+    Cell4<R> pe = { 0, 0, 0, 0 };
+    for (int b = 0; b <= oy; ++b)
+        for (int a = 0; a <= ox; ++a) {
+            const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
+            const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
+            pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
+            pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
+        }
+    Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
+    const Cell4<R> e = uf[k];
+    Cell4<R> u = e;
+    if (DELTA) {   // correction form: the admissible set constrains w + e
+        const Cell4<R> wb = Lf.w[k];
+        u.E += wb.E; u.Fx += wb.Fx; u.Fy += wb.Fy; u.T += wb.T;
+    }
+    const Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
+    R th = R(1);
+    if (!admissible(tg, Lf.c)) {
+        th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
+        atomicAdd(&ctl->damped, 1u);
+    }
+    uf[k] = Cell4<R>{ e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy, e.T + th * pe.T };
+}
+
 // Items are (instance, 256-cell chunk of the fine level).
 template <typename R, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ lvc,
@@ -768,42 +820,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        Ctl* ctl = ctls + it.x;
         load_level(Lf, lvf + it.x);
         load_level(Lc, lvc + it.x);
         __syncthreads();
         const int k = it.y * kThreads + threadIdx.x;
-        if (k < Lf.n) {
-            const int i = k % Lf.nx, j = k / Lf.nx;
-            const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
-            const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
-            const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
-            const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
-            Cell4<R> pe = { 0, 0, 0, 0 };
-            for (int b = 0; b <= oy; ++b)
-                for (int a = 0; a <= ox; ++a) {
-                    const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
-                    const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
-                    pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
-                    pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
-                }
-            Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
-            const Cell4<R> e = uf[k];
-            Cell4<R> u = e;
-            if (DELTA) {   // correction form: the admissible set constrains w + e
-                const Cell4<R> wb = Lf.w[k];
-                u.E += wb.E; u.Fx += wb.Fx; u.Fy += wb.Fy; u.T += wb.T;
-            }
-            const Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
-            R th = R(1);
-            if (!admissible(tg, Lf.c)) {
-                th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
-                atomicAdd(&ctl->damped, 1u);
-            }
-            const Cell4<R> out = { e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy,
-                                   e.T + th * pe.T };
-            uf[k] = out;
-        }
+        if (k < Lf.n) prolong_cell<R, DELTA>(Lc, Lf, k, coarse_buf, fine_buf, ctls + it.x);
         __syncthreads();
     }
 }
