@@ -696,6 +696,12 @@ __device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>
     const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
     Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
     const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
+    // the whole 3 x 3 (1D: 3) fine stencil inside the grid: plain loads
+    const bool inside = 2 * ic >= 1 && 2 * ic + 1 < Lf.nx &&
+                        (Lf.dim != 2 || (2 * jc >= 1 && 2 * jc + 1 < Lf.ny));
+    auto get = [&](const Cell4<R>* arr, int i, int j, int kind) {
+        return inside ? arr[(size_t)j * Lf.nx + i] : fetch(Lf, arr, i, j, kind);
+    };
     for (int b = b0; b <= b1; ++b) {
         const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
         const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
@@ -703,12 +709,12 @@ __device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>
             const R wt = wy * wgt[a + 1];
             // correction form: the correction has zero inflow ghosts, the base
             // carries the prescribed state
-            const Cell4<R> s = fetch(Lf, us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
-            const Cell4<R> r = fetch(Lf, Lf.r, 2 * ic + a, jf, KIND_DIFF);
+            const Cell4<R> s = get(us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
+            const Cell4<R> r = get(Lf.r, 2 * ic + a, jf, KIND_DIFF);
             av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
             ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
             if (DELTA) {
-                const Cell4<R> q = fetch(Lf, Lf.w, 2 * ic + a, jf, KIND_STATE);
+                const Cell4<R> q = get(Lf.w, 2 * ic + a, jf, KIND_STATE);
                 aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
             }
         }
@@ -727,15 +733,19 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
 {
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
+    int inst = -1;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        load_level(Lf, lvf + it.x);
-        load_level(Lc, lvc + it.x);
-        __syncthreads();
+        if (it.x != inst) {                   // descriptors of a new instance
+            __syncthreads();
+            load_level(Lf, lvf + it.x);
+            load_level(Lc, lvc + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
         const int kc = it.y * kThreads + threadIdx.x;
         if (kc < Lc.n) restrict_cell<R, DELTA>(Lf, Lc, kc, fine_buf);
-        __syncthreads();
     }
 }
 
@@ -745,12 +755,17 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>*
 {
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
+    int inst = -1;
     const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
-        load_level(Lf, lvf + it.x);
-        load_level(Lc, lvc + it.x);
-        __syncthreads();
+        if (it.x != inst) {                   // descriptors of a new instance
+            __syncthreads();
+            load_level(Lf, lvf + it.x);
+            load_level(Lc, lvc + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
         const int kc = it.y * kThreads + threadIdx.x;
         if (kc < Lc.n) {
             const int ic = kc % Lc.nx, jc = kc / Lc.nx;
@@ -767,7 +782,6 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>*
             }
             Lc.sig[kc] = acc;
         }
-        __syncthreads();
     }
 }
 
@@ -785,10 +799,13 @@ __device__ __forceinline__ void prolong_cell(const Level<R>& Lc, const Level<R>&
     const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
     const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
     Cell4<R> pe = { 0, 0, 0, 0 };
+    // the coarse cells read lie inside the grid: plain loads
+    const bool inside = ic + 1 < Lc.nx && (Lf.dim != 2 || jc + 1 < Lc.ny);
     for (int b = 0; b <= oy; ++b)
         for (int a = 0; a <= ox; ++a) {
-            const Cell4<R> cu = fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
-            const Cell4<R> cv = fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
+            const size_t kc = (size_t)(jc + b) * Lc.nx + ic + a;
+            const Cell4<R> cu = inside ? uc[kc] : fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
+            const Cell4<R> cv = inside ? Lc.v[kc] : fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
             pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
             pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
         }
@@ -817,15 +834,19 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
 {
     __shared__ Level<R> Lf, Lc;
     const int nw = *wl.count;
+    int inst = -1;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
-        load_level(Lf, lvf + it.x);
-        load_level(Lc, lvc + it.x);
-        __syncthreads();
+        if (it.x != inst) {                   // descriptors of a new instance
+            __syncthreads();
+            load_level(Lf, lvf + it.x);
+            load_level(Lc, lvc + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
         const int k = it.y * kThreads + threadIdx.x;
         if (k < Lf.n) prolong_cell<R, DELTA>(Lc, Lf, k, coarse_buf, fine_buf, ctls + it.x);
-        __syncthreads();
     }
 }
 
@@ -837,18 +858,22 @@ __global__ void k_make_rhs(const Level<R>* __restrict__ lv, WorkList wl,
 {
     __shared__ Level<R> L;
     const int nw = *wl.count;
+    int inst = -1;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (ctls && !ctls[it.x].active) continue;
-        load_level(L, lv + it.x);
-        __syncthreads();
+        if (it.x != inst) {                   // descriptor of a new instance
+            __syncthreads();
+            load_level(L, lv + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
         const int k = it.y * kThreads + threadIdx.x;
         if (k < L.n) {
             Cell4<R> s = L.u[buf][k];
             s.T *= L.c_v;
             L.f[k] = s;
         }
-        __syncthreads();
     }
 }
 
@@ -1044,13 +1069,18 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
     __shared__ Level<double> L;
     __shared__ Level<float> M;
     const int nw = *wl.count;
+    int inst = -1;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl.items[w];
         if (skip(ctls, it.x)) continue;
         Ctl* ctl = ctls + it.x;
-        load_level(L, lv64 + it.x);
-        load_level(M, lv32 + it.x);
-        __syncthreads();
+        if (it.x != inst) {                   // descriptors of a new instance
+            __syncthreads();
+            load_level(L, lv64 + it.x);
+            load_level(M, lv32 + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
         const int k = it.y * kThreads + threadIdx.x;
         if (k < L.n) {
             const Cell4<float> a = M.u[buf][k];
@@ -1070,7 +1100,6 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
             }
             L.u[0][k] = tg;
         }
-        __syncthreads();
     }
 }
 
