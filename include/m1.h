@@ -166,7 +166,7 @@ m1_status m1_step_history(m1_grid_t g, double* hist, double* dtau, int len);
  * A batch holds `count` instances (grids) that share lmax and precision; sizes,
  * dimension (1D and 2D may mix), walls, constants and time steps are per
  * instance.  One persistent launch per level and kernel serves all instances
- * (their tiles are items of a device work list), one CUDA graph holds the
+ * (their strips of cells are items of a device work list), one CUDA graph holds the
  * V-cycle, and each instance keeps its own dtau_im, residual norms and stop flag
  * (Algorithm 4 per instance): an instance's result is the same alone and in a
  * batch.  Index arguments are 0 .. count-1. */

@@ -227,10 +227,6 @@ m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
         std::memset(&q, 0, sizeof(q));
         q.dim = g.dim; q.nx = nx; q.ny = ny; q.n = nx * ny;
         for (int w = 0; w < 4; ++w) q.bc[w] = g.bc[w];
-        q.tx = g.dim == 2 ? kTx2 : kTx1;
-        q.ty = g.dim == 2 ? kTy2 : 1;
-        q.tiles_x = (nx + q.tx - 1) / q.tx;
-        q.tiles = q.tiles_x * ((ny + q.ty - 1) / q.ty);
         q.chunks = (q.n + kThreads - 1) / kThreads;
         q.prof_len = std::max(nx, ny);
         // strip height: the autotuned value for this level size and precision

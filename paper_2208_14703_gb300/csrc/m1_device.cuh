@@ -26,16 +26,16 @@ template <> struct Slack<float> { static constexpr float v = 1e-6f; };
 template <typename R> struct alignas(4 * sizeof(R)) Cell4 { R E, Fx, Fy, T; };
 template <typename R> struct alignas(2 * sizeof(R)) Sig2 { R sa, ss; };
 
-// Tile shape of the stencil kernels: 256 threads, 32 x 8 cells in 2D, 256 x 1 in 1D.
+// Block size of the cell-parallel kernels (256 threads) and the tile shape of the
+// no-allocation residual: 32 x 8 cells in 2D, 256 x 1 in 1D.
 constexpr int kThreads = 256;
 constexpr int kTx2 = 32, kTy2 = 8, kTx1 = 256;
-// Warp strips of the Jacobi sweep: a warp's 32 lanes own 32 consecutive columns
+// Warp strips of the stencil kernels: a warp's 32 lanes own 32 consecutive columns
 // (kStripW = 30 output columns and one halo column on each side) and march up
 // to kStripH rows (2D; one row in 1D).
 constexpr int kStripW = 30, kStripH = 16, kStripWarps = 2;
 // Blocks of a persistent strip launch: up to 16 resident 2-warp blocks per SM.
 constexpr int kStripBlocks = 152 * 16;
-constexpr int kHalo = (kTx2 + 2) * (kTy2 + 2) > (kTx1 + 2) ? (kTx2 + 2) * (kTy2 + 2) : (kTx1 + 2);
 
 // One grid level as the kernels see it.  Constants that depend on the time
 // step (ax, bx, diag, cdt) are rewritten before every implicit step.
@@ -43,7 +43,7 @@ template <typename R>
 struct Level {
     int dim, nx, ny, n;
     int bc[4];
-    int tx, ty, tiles_x, tiles;   // tile shape and count
+    int tx, ty, tiles_x, tiles;   // 32 x 8 tiles of the no-allocation residual (else 0)
     int chunks;                   // 256-cell chunks (cell-parallel kernels)
     int part_off;                 // first norm partial of this instance (level 0)
     int prof_len;                 // stride of the inflow profile table
@@ -92,7 +92,7 @@ struct BatchCtl {
     int n_done, n_active, all_done, pad;
 };
 
-// A work list: items[0 .. *count) of (instance, tile or 256-cell chunk), read by
+// A work list: items[0 .. *count) of (instance, strip or 256-cell chunk), read by
 // persistent kernels (a fixed grid striding over the items), so the list can
 // change between V-cycles without changing a captured graph.
 struct WorkList {

@@ -3,7 +3,7 @@
 // Engine<R>: a fixed number of slots, each holding one instance's level
 // hierarchy (all instances share the level count L and the precision R; sizes,
 // dimension, walls and time steps are per instance).  Device descriptors are
-// laid out [level][slot]; work lists per level enumerate (slot, tile) and
+// laid out [level][slot]; work lists per level enumerate (slot, warp strip) and
 // (slot, 256-cell chunk) items of the used slots.  A single grid is an engine
 // with one slot, a batch an engine with one slot per instance; the server adds
 // and removes slots between V-cycles.

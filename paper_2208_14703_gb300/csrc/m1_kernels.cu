@@ -877,7 +877,7 @@ __global__ void k_make_rhs(const Level<R>* __restrict__ lv, WorkList wl,
     }
 }
 
-// Deterministic reduction of one instance's per-tile partials (fixed order:
+// Deterministic reduction of one instance's per-strip partials (fixed order:
 // thread t sums entries t, t+256, ... then a fixed tree), then the control
 // logic of Algorithm 4 for that instance.  One block per instance slot.
 __device__ double block_reduce_fixed(const double* __restrict__ p, int n, double* red)
