@@ -92,6 +92,7 @@ struct m1_server {
 
 m1_server::~m1_server()
 {
+    if (model) cudaStreamSynchronize(model->sv_stream());   // no snapshot copy in flight
     for (int k = 0; k < 2; ++k) {
         if (snap_ev[k]) cudaEventDestroy(snap_ev[k]);
         if (snap[k]) cudaFreeHost(snap[k]);
