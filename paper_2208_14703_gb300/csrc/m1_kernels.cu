@@ -260,6 +260,24 @@ __device__ __forceinline__ void load_level_warp(Level<R>& L, const Level<R>* src
     __syncwarp();
 }
 
+// Begin a warp's item of instance `inst`: the level descriptor is read (one
+// word per lane) together with the instance's control flags, in one round trip,
+// then stored to the warp's shared copy.  False (for the whole warp) when the
+// instance is done or inactive.
+template <typename R>
+__device__ __forceinline__ bool enter_item(Level<R>& L, const Level<R>* src, const Ctl* ctls,
+                                           int inst, int lane)
+{
+    static_assert(sizeof(Level<R>) % 8 == 0 && sizeof(Level<R>) <= 32 * 8, "one word per lane");
+    constexpr int nwords = (int)(sizeof(Level<R>) / 8);
+    const unsigned long long word =
+        lane < nwords ? reinterpret_cast<const unsigned long long*>(src)[lane] : 0ull;
+    if (skip(ctls, inst)) return false;
+    if (lane < nwords) reinterpret_cast<unsigned long long*>(&L)[lane] = word;
+    __syncwarp();
+    return true;
+}
+
 // Persistent sweep over every listed (instance, strip): one warp per item.
 // FP64 instances are held to 128 registers (8 blocks per SM): one register
 // more (the pseudo-time variant) cost 4% of the FP64 step on GB300.
@@ -274,8 +292,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k
     const int nw = *wl.count;
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
-        if (skip(ctls, it.x)) continue;
-        load_level_warp(L, lv + it.x, lane);
+        if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
         strip_regs<R, PSEUDO, DELTA>(L, ctls + it.x, it, lane, src, out_buf);
         __syncwarp();
@@ -424,8 +441,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep_ring32(const Level<f
     const int nw = *wl.count;
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
-        if (skip(ctls, it.x)) continue;
-        load_level_warp(L, lv + it.x, lane);
+        if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<float>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
         if (L.dim == 2) strip_ring32<PSEUDO>(L, ctls + it.x, it, lane, src, out_buf, ring[wib]);
         else row_1d32<PSEUDO>(L, ctls + it.x, it, lane, src, out_buf);
@@ -564,8 +580,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __re
     const int nw = *wl.count;
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
-        if (skip(ctls, it.x)) continue;
-        load_level_warp(L, lv + it.x, lane);
+        if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const double nrm = apply_item<R, MODE, DELTA>(L, it, lane, state_buf, write_r);
         if (MODE == APPLY_RESID && partials) {
             const double sum = warp_sum(nrm);
@@ -645,8 +660,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_fas_aw32(const Level<float
     const int nw = *wl.count;
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
-        if (skip(ctls, it.x)) continue;
-        load_level_warp(L, lv + it.x, lane);
+        if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         fas_aw32_item(L, it, lane);
         __syncwarp();
     }
@@ -1026,9 +1040,14 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
     const int nw = *wl.count;
     for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
         const int2 it = wl.items[w];
-        if (skip(ctls, it.x)) continue;
-        load_level_warp(L, lv64 + it.x, lane);
-        load_level_warp(M, lv32 + it.x, lane);
+        {
+            constexpr int nm = (int)(sizeof(Level<float>) / 8);
+            const unsigned long long wm =
+                lane < nm ? reinterpret_cast<const unsigned long long*>(lv32 + it.x)[lane] : 0ull;
+            if (!enter_item(L, lv64 + it.x, ctls, it.x, lane)) continue;
+            if (lane < nm) reinterpret_cast<unsigned long long*>(&M)[lane] = wm;
+            __syncwarp();
+        }
         const bool two_d = L.dim == 2;
         double nrm = 0.0;
         strip_march<double, false>(L, it, lane, L.u[0], [&](size_t k, const Staged<double>& wv,
