@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from tests.conftest import ROOT
@@ -54,3 +55,71 @@ def test_host_side_validation_without_gpu(lib):
     assert m1._lib.m1_create_grid(ctypes.byref(bad), None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_create_grid(None, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_destroy_grid(None) == m1.ERR_INVALID_ARG
+
+
+# (name, descriptor fields, also invalid for the single-level op entry points,
+# which ignore lmax)
+BAD_DESCS = [
+    ("dim 3", dict(dim=3, nx=64, ny=64), True),
+    ("1D with ny > 1", dict(dim=1, nx=64, ny=2), True),
+    ("empty grid", dict(dim=2, nx=0, ny=64), True),
+    ("negative size", dict(dim=2, nx=64, ny=-8), True),
+    ("lmax 0", dict(dim=2, nx=64, ny=64, lmax=0), False),
+    ("lmax 21", dict(dim=1, nx=1 << 20, ny=1, lmax=21), False),
+    ("ny not divisible by 2^(lmax-1)", dict(dim=2, nx=64, ny=60, lmax=4), False),
+    ("nx not divisible by 2^(lmax-1)", dict(dim=1, nx=100, ny=1, lmax=4), False),
+    ("c = 0", dict(dim=2, nx=64, ny=64, c=0.0), True),
+    ("a_r < 0", dict(dim=2, nx=64, ny=64, a_r=-1.0), True),
+    ("C_v nan", dict(dim=2, nx=64, ny=64, c_v=float("nan")), True),
+    ("zero length", dict(dim=2, nx=64, ny=64, lx=0.0), True),
+    ("precision 2", dict(dim=2, nx=64, ny=64, precision=2), True),
+    ("unpaired periodic y wall", dict(dim=2, nx=64, ny=64, bc=["reflect", "reflect", "periodic",
+                                                                "inflow"]), True),
+    ("more than 2^30 cells", dict(dim=2, nx=1 << 16, ny=1 << 15, lmax=1), False),
+]
+
+
+@pytest.mark.parametrize("name,kw,op", BAD_DESCS, ids=[n for n, _, _ in BAD_DESCS])
+def test_invalid_descriptors_rejected_before_any_cuda_call(lib, name, kw, op):
+    from paper_2208_14703_gb300 import m1
+    args = dict(dim=2, nx=64, ny=64, lx=1.0, ly=1.0, bc=["reflect"] * 4, lmax=3)
+    args.update(kw)
+    d = m1.make_desc(args["dim"], args["nx"], args["ny"], args["lx"], args["ly"], args["bc"],
+                     args["lmax"], c=args.get("c", 1.0), a_r=args.get("a_r", 1.0),
+                     c_v=args.get("c_v", 1.0), precision=args.get("precision", m1.FP64))
+    d.ny = args["ny"]
+    h = ctypes.c_void_p()
+    assert m1._lib.m1_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    arr = (m1.GridDesc * 1)(d)
+    assert m1._lib.m1_create_batch(arr, 1, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    if op:
+        buf = np.zeros(4 * 64 * 64)
+        assert m1._lib.m1_op_level(ctypes.byref(d), None, 0.1, m1._ptr(buf), m1._ptr(buf), None,
+                                   m1.OP_APPLY, 0.0, 0.5, m1._ptr(buf),
+                                   None) == m1.ERR_INVALID_ARG
+
+
+def test_invalid_batches_servers_and_parameters_rejected(lib):
+    from paper_2208_14703_gb300 import m1
+    h = ctypes.c_void_p()
+    a = m1.make_desc(1, 64, 1, 1.0, 1.0, ["periodic"] * 4, 2)
+    b = m1.make_desc(1, 64, 1, 1.0, 1.0, ["periodic"] * 4, 3)
+    arr = (m1.GridDesc * 2)(a, b)                 # level counts differ
+    assert m1._lib.m1_create_batch(arr, 2, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_create_batch(arr, 0, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    for budget, slots, lmax, prec in ((0, 4, 3, 0), (1 << 20, 0, 3, 0), (1 << 20, 4, 0, 0),
+                                      (1 << 20, 4, 3, 2)):
+        assert m1._lib.m1_server_create(budget, slots, lmax, prec, None, None,
+                                        ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    p = m1.m1_default_params(nu_l=2)              # the paper fixes one sweep per pseudo step
+    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), None,
+                                    ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    p = m1.m1_default_params(dtau_rule=2)
+    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), None,
+                                    ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    t = ctypes.c_ulonglong()
+    assert m1._lib.m1_serve_submit(None, None, 1, 0.1, None, ctypes.byref(t)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_serve_poll(None, 1, None, None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_serve_wait(None, 1, 1.0) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_server_destroy(None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_implicit_step(None, 0.1, None, None) == m1.ERR_INVALID_ARG
