@@ -96,3 +96,31 @@ def test_mixed_not_converged_and_admissible():
     g.close()
     assert st.status == m1.ERR_NOT_CONVERGED and st.cycles == 3
     assert np.all(out[0] > 0) and np.all(np.hypot(out[1], out[2]) <= out[0] * (1 + 1e-12))
+
+
+def test_mixed_beam_4096_configuration():
+    """The mixed-precision configuration at full size: a 4096^2 beam in a
+    channel (L_max = 10), one step to 1e-8 in mixed precision and in FP64.  The
+    oracle evaluates the residual of the mixed result over the whole grid; the
+    per-field difference to the FP64 GPU path (itself parity-checked against
+    the oracle at smaller sizes) is reported and bounded."""
+    case = inputs.beam_channel_2d(4096)
+    out, st = mixed_step(case, 1e-8)
+    assert st.status == 0
+    g = m1.grid_from_case(case)
+    st64 = g.implicit_step(case["dt"], m1.m1_default_params(tol=1e-8))
+    ref = np.stack(g.get_state())
+    g.close()
+    assert st64.status == 0
+    og = O.Grid.from_case(case)
+    b = O.rhs_of(og, case["state"])
+    res = O.norm(og, O.residual(og, case["dt"], case["sa"], case["ss"], b, out))
+    assert res <= 1e-8 * st64.res0 * 1.001
+    err = field_errors(out, ref)
+    print("4096^2 beam mixed cycles", st.cycles, "fp64 cycles", st64.cycles, "ms", st.ms,
+          st64.ms, "errors", err)
+    # the two paths take the same cycles (same residual history up to FP32
+    # rounding of the corrections), so their results agree far below tol
+    assert st.cycles == st64.cycles
+    assert max(err.values()) <= BOUND, err
+    assert np.all(out[0] > 0) and np.all(np.hypot(out[1], out[2]) <= out[0] * (1 + 1e-12))
