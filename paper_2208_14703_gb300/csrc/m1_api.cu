@@ -374,13 +374,19 @@ m1_status Engine<R>::rebuild()
         sig.push_back(chunks[l].n > 0);
     }
     if (sig != list_sig) { list_sig = sig; graph_dirty = true; }
-    // level-0 sweeps of all slots share one launch: the cp.async kernel when
-    // the slots holding most level-0 cells chose it
-    long long with = 0, without = 0;
-    for (int i = 0; i < cap; ++i)
-        if (used[i]) (h[i].ring ? with : without) += h[i].n;
-    const bool r0 = with > without;
-    if (r0 != ring0) { ring0 = r0; graph_dirty = true; }
+    // the sweeps of a level share one launch for all slots: the cp.async kernel
+    // when the slots holding most of the level's cells chose it
+    std::vector<char> rl(L, 0);
+    for (int l = 0; l < L; ++l) {
+        long long with = 0, without = 0;
+        for (int i = 0; i < cap; ++i)
+            if (used[i]) {
+                const Level<R>& q = h[(size_t)l * cap + i];
+                (q.ring ? with : without) += q.n;
+            }
+        rl[l] = with > without;
+    }
+    if (rl != ring) { ring = rl; graph_dirty = true; }
     M1_CK(cudaMemcpyAsync(d, h.data(), sizeof(Level<R>) * h.size(), cudaMemcpyHostToDevice, stream));
     M1_CK(cudaStreamSynchronize(stream));
     return M1_OK;
@@ -535,7 +541,7 @@ template <typename R>
 void Engine<R>::sweeps_fine(int& cur, int count, cudaStream_t s)
 {
     for (int k = 0; k < count; ++k) {
-        launch_sweep<R>(d, strips[0].view(), ctl, false, cur, 1 - cur, s, delta, ring0);
+        launch_sweep<R>(d, strips[0].view(), ctl, false, cur, 1 - cur, s, delta, ring[0] != 0);
         cur = 1 - cur;
     }
 }
@@ -547,12 +553,13 @@ void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
 {
     Level<R>* dl = d + (size_t)l * cap;
     const bool go = strips[l].n > 0;          // an empty level only advances the buffer
+    const bool rg = ring[l] != 0;
     for (int k = 0; k < m; ++k) {
         if (k == 0 && from_v) {
-            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta);
+            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta, rg);
             cur = 0;
         } else {
-            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta);
+            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta, rg);
             cur = 1 - cur;
         }
     }

@@ -109,7 +109,7 @@ struct Engine {
     Params gparams{};
     int graph_cycles = 1;
     bool graph_dirty = true;
-    bool ring0 = false;                     // level-0 sweeps take the cp.async kernel
+    std::vector<char> ring;                 // per level: the sweeps take the cp.async kernel
     std::vector<char> list_sig;             // which work lists were non-empty at capture
 
     ~Engine();
