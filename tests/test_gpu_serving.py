@@ -154,3 +154,18 @@ def test_poll_reports_progress_and_queue():
     srv.close()
     for g in grids:
         g.close()
+
+
+def test_destroy_finishes_submitted_requests():
+    """Destroying a server right after submitting finishes every request first:
+    each grid then holds the result of its steps, the same as run alone."""
+    reqs = requests()[:3]
+    srv = m1.Server(1 << 34, 2, 4)                # two slots: the third request queues
+    grids = [m1.grid_from_case(c) for c, _, _ in reqs]
+    for g, (c, n, tol) in zip(grids, reqs):
+        srv.submit(g, n, c["dt"], m1.m1_default_params(tol=tol))
+    srv.close()
+    for g, (c, n, tol) in zip(grids, reqs):
+        alone, _ = run_alone(c, n, tol, 0)
+        np.testing.assert_array_equal(alone, np.stack(g.get_state()))
+        g.close()
