@@ -84,3 +84,28 @@ def test_strip_shape_changes_no_arithmetic(precision, restore_tuning):
             assert a[0] == b[0]
             for f in range(4):
                 assert np.linalg.norm(a[1][f] - b[1][f]) <= 1e-10 * np.linalg.norm(a[1][0])
+
+
+@pytest.mark.gpu
+def test_ring_staging_serves_1d_instances_of_a_batch(restore_tuning):
+    """A batch mixing 2D and 1D instances, with every size class tuned to the
+    cp.async staging: the 2D instances choose it for every level, so the 1D
+    instances' strips run through that kernel's one-row path.  Their steps agree
+    with the register staging to rounding."""
+    cases = [inputs.hot_square_2d(64, lmax=4), inputs.random_admissible_2d(
+        48, 32, seed=5, fmax=0.9, cfl=20, bc=("periodic",) * 4, lmax=4),
+        inputs.gaussian_1d(64, lmax=4), inputs.gaussian_1d(128, lmax=4)]
+    cases[1]["tol"] = 1e-8
+    outs = {}
+    for staging in (0, 1):
+        m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": 0,
+                        "staging": staging if k == 1 else 0} for k in (0, 1) for c in range(16)])
+        b = m1.batch_from_cases(cases, precision=m1.MIXED)
+        st = b.implicit_step([c["dt"] for c in cases], m1.m1_default_params(tol=1e-10))
+        outs[staging] = ([s.cycles for s in st],
+                         [np.stack(b.get_state(k)) for k in range(len(cases))])
+        b.close()
+    assert outs[0][0] == outs[1][0]
+    for a, b in zip(outs[0][1], outs[1][1]):
+        for f in range(4):
+            assert np.linalg.norm(a[f] - b[f]) <= 1e-10 * np.linalg.norm(a[0])
