@@ -243,15 +243,17 @@ def bench_batched(m1, count, stream):
     return out
 
 
-def bench_serving(m1, reqs, stream, budget):
+def bench_serving(m1, reqs, stream, budget, paths=("mixed", "fp64")):
     """A Poisson arrival stream of simulations served with continuous batching,
     mixed precision against the plain FP64 path (the same stream through an FP64
-    server)."""
+    server); `paths` selects which of the two run."""
     out = {"requests": len(reqs), "steps": sum(r["nsteps"] for r in reqs),
            "sizes": sorted({(r["case"]["desc"]["dim"], r["case"]["desc"]["nx"]) for r in reqs}),
            "arrival_span_s": reqs[-1]["arrival_s"], "budget_bytes": budget,
            "dtau_rule": "signed (decrease of the residual norm)"}
     for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
+        if name not in paths:
+            continue
         grids = [m1.grid_from_case(r["case"], precision=prec) for r in reqs]
         srv = m1.Server(budget, 64, reqs[0]["case"]["lmax"], prec, stream=stream.cuda_stream)
         t0 = time.perf_counter()
@@ -273,7 +275,8 @@ def bench_serving(m1, reqs, stream, budget):
                      "p50_ms": s.p50_ms, "p99_ms": s.p99_ms, "mean_ms": s.mean_ms,
                      "wall_s": wall, "cycles": s.cycles, "bytes_peak": s.bytes_peak,
                      "failed": sum(1 for x in status if x != m1.OK)}
-    out["mixed_over_fp64_solves"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    if "mixed" in out and "fp64" in out:
+        out["mixed_over_fp64_solves"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     return out
 
 
