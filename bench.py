@@ -243,19 +243,23 @@ def bench_batched(m1, count, stream):
     return out
 
 
-def bench_serving(m1, reqs, stream, budget, paths=("mixed", "fp64")):
+def bench_serving(m1, reqs, stream, budget, paths=("mixed", "fp64"), small_cells=None):
     """A Poisson arrival stream of simulations served with continuous batching,
     mixed precision against the plain FP64 path (the same stream through an FP64
-    server); `paths` selects which of the two run."""
+    server); `paths` selects which of the two run, `small_cells` the size up to
+    which requests take the server's small lane (0: one lane)."""
+    if small_cells is None:
+        small_cells = m1.SMALL_CELLS
     out = {"requests": len(reqs), "steps": sum(r["nsteps"] for r in reqs),
            "sizes": sorted({(r["case"]["desc"]["dim"], r["case"]["desc"]["nx"]) for r in reqs}),
            "arrival_span_s": reqs[-1]["arrival_s"], "budget_bytes": budget,
-           "dtau_rule": "signed (decrease of the residual norm)"}
+           "dtau_rule": "signed (decrease of the residual norm)", "small_lane_cells": small_cells}
     for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
         if name not in paths:
             continue
         grids = [m1.grid_from_case(r["case"], precision=prec) for r in reqs]
-        srv = m1.Server(budget, 64, reqs[0]["case"]["lmax"], prec, stream=stream.cuda_stream)
+        srv = m1.Server(budget, 64, reqs[0]["case"]["lmax"], prec, stream=stream.cuda_stream,
+                        small_cells=small_cells)
         t0 = time.perf_counter()
         tickets = []
         for r, g in zip(reqs, grids):

@@ -187,22 +187,27 @@ m1_status m1_batch_implicit_step(m1_batch_t b, const double* dt, const m1_solve_
                                  m1_step_stats* stats);
 
 /* ---- serving: many simulations stepping on one GPU with continuous batching ----
- * A server owns one engine of max_slots slots (level count lmax, precision FP64
- * or MIXED; the structural solver parameters nu0, m_pseudo, m_coarse are fixed
- * at creation, the others are per request).  m1_serve_submit queues a caller's
- * grid (its state set, same lmax and precision) for nsteps implicit steps of
- * length dt.  A scheduler thread admits queued requests in arrival order into
- * free slots while their level hierarchies fit hbm_budget_bytes, copies the
- * state in on the device (it stays resident for all steps), and launches V-cycle
- * graphs over every active slot, one cycle at a time; while a cycle runs it
- * reads the control blocks left by the previous one: a slot whose step
- * converged starts its next step (behind the running cycle), and a finished
- * request's state is copied back into its grid and its slot and budget are
- * freed, all between V-cycles, so requests arriving while others run join the
- * running batch.  The caller must not use a submitted grid until its ticket
- * completes.  Submit, poll, wait and stats are thread safe.  Step latency is
- * the host time from the start of a step to the reading that sees it
- * converged. */
+ * A server holds two lanes, each an engine of max_slots slots (level count
+ * lmax, precision FP64 or MIXED; the structural solver parameters nu0,
+ * m_pseudo, m_coarse are fixed at creation, the others are per request) with a
+ * scheduler thread and a CUDA stream of its own: requests of at most
+ * small_cells fine cells go to the small lane (a stream the server creates at
+ * the highest priority), the others to the large lane (cuda_stream, or a
+ * stream of the server's when NULL); small_cells = 0 puts every request in the
+ * large lane.  A small request's V-cycles thus never wait for the levels of
+ * the largest instances.  m1_serve_submit queues a caller's grid (its state
+ * set, same lmax and precision) for nsteps implicit steps of length dt.  Each
+ * lane admits its queued requests in arrival order into free slots while the
+ * level hierarchies of both lanes fit hbm_budget_bytes, copies the state in on
+ * the device (it stays resident for all steps), and launches V-cycle graphs
+ * over every active slot, one cycle at a time; while a cycle runs it reads the
+ * control blocks left by the previous one: a slot whose step converged starts
+ * its next step (behind the running cycle), and a finished request's state is
+ * copied back into its grid and its slot and budget are freed, all between
+ * V-cycles, so requests arriving while others run join the running batch.
+ * The caller must not use a submitted grid until its ticket completes.
+ * Submit, poll, wait and stats are thread safe.  Step latency is the host time
+ * from the start of a step to the reading that sees it converged. */
 typedef struct m1_server* m1_server_t;
 typedef struct {
     long long requests_done, steps_done, cycles;
@@ -212,8 +217,11 @@ typedef struct {
     int active, queued;
     long long bytes_in_use, bytes_peak;   /* budgeted device bytes of admitted requests */
 } m1_server_stats;
+/* INVALID_ARG: max_slots < 1, lmax outside 1..20, a zero budget, small_cells < 0,
+ * an unknown precision or invalid structural parameters. */
 m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int precision,
-                           const m1_solve_params* structure, void* cuda_stream, m1_server_t* out);
+                           const m1_solve_params* structure, long long small_cells,
+                           void* cuda_stream, m1_server_t* out);
 /* REJECTED: the grid alone exceeds the budget; INVALID_ARG: precision, lmax or
  * structural parameters differ from the server's. */
 m1_status m1_serve_submit(m1_server_t s, m1_grid_t g, int nsteps, double dt,

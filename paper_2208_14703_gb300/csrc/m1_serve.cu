@@ -2,14 +2,20 @@
 // GPU with continuous batching.
 //
 // A request is a caller's grid (its state already set) and a number of steps.
-// The scheduler thread admits queued requests in arrival order into free slots
-// of one engine while their level hierarchies fit the HBM budget (the state is
-// copied device to device; it stays resident for all of the request's steps),
-// and launches V-cycle graphs over every active slot, one cycle per batch.
-// After queueing a batch it copies the control blocks asynchronously into a
-// pinned snapshot and then handles the snapshot of the previous batch while the
-// new one runs, so the GPU does not wait for the host: a slot whose step
-// converged starts its next step (queued behind the running batch), or, after
+// Requests go to one of two lanes by size: small ones (at most `small_cells`
+// fine cells) and large ones.  Each lane is an engine of its own, driven by a
+// scheduler thread of its own on a stream of its own (the small lane's at the
+// highest stream priority), so a small request's V-cycle never waits for the
+// levels of the largest instances, and the host work of one lane (admission
+// copies that wait for its stream) never holds up the other: the two lanes'
+// kernels interleave on the GPU.  Within a lane the scheduler admits queued
+// requests in arrival order into free slots while all admitted level
+// hierarchies of both lanes fit the HBM budget (the state is copied device to
+// device; it stays resident for all of the request's steps) and launches
+// V-cycle graphs over every active slot, one cycle per batch.  After queueing
+// batch b it copies the control blocks asynchronously into a pinned snapshot,
+// then waits for the snapshot of batch b - 1 and handles it while b runs: a
+// slot whose step converged starts its next step (queued behind b), or, after
 // its last step, its result is copied back into the caller's grid and its slot
 // and budget are freed; queued requests join between batches.  A snapshot
 // taken before a slot's step was started says nothing about that step and is
@@ -47,8 +53,9 @@ struct Request {
     double dt = 0.0;
     m1_solve_params params{};
     size_t bytes = 0;
+    int lane = 0;
     int slot = -1;
-    long long started_at = 0;     // batches queued before the current step was started
+    long long started_at = 0;     // batches of its lane queued before the current step started
     int steps_done = 0;
     int status = M1_PENDING;
     bool finished = false;
@@ -56,18 +63,43 @@ struct Request {
     m1_step_stats last{};
 };
 
+// One engine with its slots, queue, stream and snapshot pipeline.
+struct Lane {
+    std::unique_ptr<Model> model;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> slot_req;
+    Ctl* snap[2] = { nullptr, nullptr };
+    cudaEvent_t snap_ev[2] = { nullptr, nullptr };
+    long long batches = 0;        // batches queued so far
+    long long handled = 0;        // batches whose snapshot has been handled
+
+    bool active() const
+    {
+        for (auto& r : slot_req)
+            if (r) return true;
+        return false;
+    }
+    int free_slots() const
+    {
+        int n = 0;
+        for (auto& r : slot_req) n += r ? 0 : 1;
+        return n;
+    }
+};
+
 }  // namespace
 
 struct m1_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<Request>> queue;
     std::map<unsigned long long, std::shared_ptr<Request>> reqs;
-    std::vector<std::shared_ptr<Request>> slot_req;
-    std::unique_ptr<Model> model;
+    Lane lanes[2];
     m1::Params structure{};
     int precision = 0, L = 0, max_slots = 0, device = 0;
     size_t budget = 0, used = 0, peak = 0;
+    long long small_cells = 0;
     int poll_cycles = 1;
     bool stop = false;
     int error = M1_OK;
@@ -76,88 +108,83 @@ struct m1_server {
     std::vector<double> latencies_ms;
     long long steps_done = 0, requests_done = 0, cycles = 0;
     double t_first = 0.0, t_last = 0.0;
-    std::thread th;
-    // pipelined snapshots of the control blocks (two pinned buffers)
-    Ctl* snap[2] = { nullptr, nullptr };
-    cudaEvent_t snap_ev[2] = { nullptr, nullptr };
-    long long batches = 0;        // batches queued so far
-    long long handled = 0;        // batches whose snapshot has been handled
+    std::thread th[2];
 
     ~m1_server();
-    void loop();
-    m1_status admit_and_start(std::vector<std::shared_ptr<Request>>& admit);
-    m1_status service_cycles();
-    m1_status handle_snapshot(long long b);
+    void loop(int k);
+    m1_status admit_and_start(Lane& ln, std::vector<std::shared_ptr<Request>>& admit);
+    m1_status launch_batch(Lane& ln);
+    m1_status handle_snapshot(Lane& ln, long long b);
 };
 
 m1_server::~m1_server()
 {
-    if (model) cudaStreamSynchronize(model->sv_stream());   // no snapshot copy in flight
-    for (int k = 0; k < 2; ++k) {
-        if (snap_ev[k]) cudaEventDestroy(snap_ev[k]);
-        if (snap[k]) cudaFreeHost(snap[k]);
+    for (Lane& ln : lanes) {
+        if (ln.stream) cudaStreamSynchronize(ln.stream);   // no snapshot copy in flight
+        ln.model.reset();
+        for (int k = 0; k < 2; ++k) {
+            if (ln.snap_ev[k]) cudaEventDestroy(ln.snap_ev[k]);
+            if (ln.snap[k]) cudaFreeHost(ln.snap[k]);
+        }
+        if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
     }
 }
 
-m1_status m1_server::admit_and_start(std::vector<std::shared_ptr<Request>>& admit)
+m1_status m1_server::admit_and_start(Lane& ln, std::vector<std::shared_ptr<Request>>& admit)
 {
     std::vector<int> slots;
     std::vector<double> dts;
     std::vector<m1_solve_params> ps;
     for (auto& r : admit) {
         int slot = -1;
-        M1_TRY(model->sv_add(r->grid->model->desc0(), &slot));
+        M1_TRY(ln.model->sv_add(r->grid->model->desc0(), &slot));
         r->slot = slot;
-        slot_req[slot] = r;
+        std::lock_guard<std::mutex> lk(mu);
+        ln.slot_req[slot] = r;
     }
-    M1_TRY(model->sv_rebuild());
+    M1_TRY(ln.model->sv_rebuild());
     for (auto& r : admit) {
-        M1_TRY(model->sv_copy_in(r->slot, *r->grid->model));
+        M1_TRY(ln.model->sv_copy_in(r->slot, *r->grid->model));
         slots.push_back(r->slot);
         dts.push_back(r->dt);
         ps.push_back(r->params);
     }
-    M1_TRY(model->sv_begin(slots, dts, ps));
+    M1_TRY(ln.model->sv_begin(slots, dts, ps));
     const double t = now_s();
-    for (auto& r : admit) { r->t_step = t; r->started_at = batches; }
+    for (auto& r : admit) { r->t_step = t; r->started_at = ln.batches; }
     return M1_OK;
 }
 
-// Queue a batch of V-cycles over every active slot and an asynchronous
-// snapshot of the control blocks, then handle the previous batch's snapshot.
-m1_status m1_server::service_cycles()
+// Queue a batch of V-cycles over every active slot of the lane and an
+// asynchronous snapshot of its control blocks.
+m1_status m1_server::launch_batch(Lane& ln)
 {
-    M1_TRY(model->sv_cycles(structure, poll_cycles));
-    const long long b = ++batches;
+    M1_TRY(ln.model->sv_cycles(structure, poll_cycles));
+    const long long b = ++ln.batches;
     const int nb = (int)(b & 1);
-    M1_CK(cudaMemcpyAsync(snap[nb], model->sv_ctl(), sizeof(Ctl) * max_slots,
-                          cudaMemcpyDeviceToHost, model->sv_stream()));
-    M1_CK(cudaEventRecord(snap_ev[nb], model->sv_stream()));
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        cycles += (long long)poll_cycles * model->sv_graph_cycles();
-    }
-    if (b > 1) M1_TRY(handle_snapshot(b - 1));
+    M1_CK(cudaMemcpyAsync(ln.snap[nb], ln.model->sv_ctl(), sizeof(Ctl) * max_slots,
+                          cudaMemcpyDeviceToHost, ln.model->sv_stream()));
+    M1_CK(cudaEventRecord(ln.snap_ev[nb], ln.model->sv_stream()));
+    std::lock_guard<std::mutex> lk(mu);
+    cycles += (long long)poll_cycles * ln.model->sv_graph_cycles();
     return M1_OK;
 }
 
-// Per-slot bookkeeping from the snapshot taken after batch b.
-m1_status m1_server::handle_snapshot(long long b)
+// Per-slot bookkeeping from the snapshot taken after batch b of a lane (its
+// copy has completed).
+m1_status m1_server::handle_snapshot(Lane& ln, long long b)
 {
-    if (b <= handled) return M1_OK;
-    handled = b;
-    const int nb = (int)(b & 1);
-    M1_CK(cudaEventSynchronize(snap_ev[nb]));
-    const Ctl* ctl = snap[nb];
+    ln.handled = b;
+    const Ctl* ctl = ln.snap[(int)(b & 1)];
     const double t = now_s();
     std::vector<int> restart;
     std::vector<double> rdts;
     std::vector<m1_solve_params> rps;
     bool removed = false;
     for (int s = 0; s < max_slots; ++s) {
-        auto r = slot_req[s];
+        auto r = ln.slot_req[s];
         if (!r || b <= r->started_at || !ctl[s].active || !ctl[s].done) continue;
-        M1_TRY(model->sv_settle(s, ctl[s].result_buf));
+        M1_TRY(ln.model->sv_settle(s, ctl[s].result_buf));
         const Ctl& c = ctl[s];
         m1_step_stats st{};
         st.cycles = c.kappa;
@@ -186,12 +213,12 @@ m1_status m1_server::handle_snapshot(long long b)
             rps.push_back(r->params);
             continue;
         }
-        M1_TRY(model->sv_copy_out(s, *r->grid->model));
-        M1_TRY(model->sv_remove(s));
+        M1_TRY(ln.model->sv_copy_out(s, *r->grid->model));
+        M1_TRY(ln.model->sv_remove(s));
         removed = true;
-        slot_req[s].reset();
         {
             std::lock_guard<std::mutex> lk(mu);
+            ln.slot_req[s].reset();
             used -= r->bytes;
             r->status = ok ? M1_OK : M1_ERR_NOT_CONVERGED;
             r->finished = true;
@@ -199,31 +226,31 @@ m1_status m1_server::handle_snapshot(long long b)
         }
         cv_done.notify_all();
     }
-    if (removed) M1_TRY(model->sv_rebuild());
+    if (removed) M1_TRY(ln.model->sv_rebuild());
     if (!restart.empty()) {
-        M1_TRY(model->sv_begin(restart, rdts, rps));
+        M1_TRY(ln.model->sv_begin(restart, rdts, rps));
         const double t2 = now_s();
-        for (int s : restart) { slot_req[s]->t_step = t2; slot_req[s]->started_at = batches; }
+        for (int s : restart) { ln.slot_req[s]->t_step = t2; ln.slot_req[s]->started_at = ln.batches; }
     }
     return M1_OK;
 }
 
-void m1_server::loop()
+void m1_server::loop(int k)
 {
     cudaSetDevice(device);
+    Lane& ln = lanes[k];
     for (;;) {
         std::vector<std::shared_ptr<Request>> admit;
-        bool active = false;
+        const bool active = ln.active();
         {
             std::unique_lock<std::mutex> lk(mu);
-            for (auto& r : slot_req) active = active || (bool)r;
-            if (stop && queue.empty() && !active) break;
+            if (error != M1_OK) break;
+            if (stop && ln.queue.empty() && !active) break;
             // admission in arrival order while a slot is free and the budget allows
-            int free_slots = 0;
-            for (auto& r : slot_req) free_slots += r ? 0 : 1;
-            while (!queue.empty() && free_slots > 0 && used + queue.front()->bytes <= budget) {
-                auto r = queue.front();
-                queue.pop_front();
+            int free_slots = ln.free_slots();
+            while (!ln.queue.empty() && free_slots > 0 && used + ln.queue.front()->bytes <= budget) {
+                auto r = ln.queue.front();
+                ln.queue.pop_front();
                 used += r->bytes;
                 peak = std::max(peak, used);
                 admit.push_back(r);
@@ -236,27 +263,36 @@ void m1_server::loop()
             if (t_first == 0.0) t_first = now_s();
         }
         m1_status st = M1_OK;
-        if (!admit.empty()) st = admit_and_start(admit);
-        if (st == M1_OK) st = service_cycles();
+        if (!admit.empty()) st = admit_and_start(ln, admit);
+        // queue batch b, then handle the snapshot of batch b - 1 while b runs
+        if (st == M1_OK && ln.active()) st = launch_batch(ln);
+        const long long prev = ln.batches - 1;
+        if (st == M1_OK && prev > ln.handled) {
+            const cudaError_t e = cudaEventSynchronize(ln.snap_ev[(int)(prev & 1)]);
+            if (e != cudaSuccess) { m1::set_err(e, "cudaEventSynchronize"); st = M1_ERR_CUDA; }
+            else st = handle_snapshot(ln, prev);
+        }
         if (st != M1_OK) {
             std::lock_guard<std::mutex> lk(mu);
-            error = st;
+            if (error == M1_OK) error = st;
             for (auto& kv : reqs)
                 if (!kv.second->finished) { kv.second->status = st; kv.second->finished = true; }
-            queue.clear();
+            for (Lane& other : lanes) other.queue.clear();
             stop = true;
             cv_done.notify_all();
             break;
         }
     }
+    cv_work.notify_all();
 }
 
 extern "C" {
 
 m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int precision,
-                           const m1_solve_params* structure, void* cuda_stream, m1_server_t* out)
+                           const m1_solve_params* structure, long long small_cells,
+                           void* cuda_stream, m1_server_t* out)
 {
-    if (!out || max_slots < 1 || lmax < 1 || lmax > 20 || hbm_budget_bytes == 0 ||
+    if (!out || max_slots < 1 || lmax < 1 || lmax > 20 || hbm_budget_bytes == 0 || small_cells < 0 ||
         (precision != M1_FP64 && precision != M1_MIXED))
         return M1_ERR_INVALID_ARG;
     *out = nullptr;
@@ -264,23 +300,38 @@ m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int
     if (structure) p = *structure; else m1_default_params(&p);
     M1_TRY(m1::validate_params(p));
     std::unique_ptr<m1_server> s(new m1_server());
-    if (precision == M1_MIXED) s->model.reset(new m1::MixedModel());
-    else s->model.reset(new m1::PlainModel());
-    M1_TRY(s->model->sv_init(max_slots, lmax, static_cast<cudaStream_t>(cuda_stream)));
+    int lo_prio = 0, hi_prio = 0;
+    M1_CK(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    for (int k = 0; k < 2; ++k) {
+        Lane& ln = s->lanes[k];
+        if (k == 1 && cuda_stream) {
+            ln.stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            // the small lane at the highest priority: its short cycles take SMs
+            // as soon as the large lane's blocks free them
+            M1_CK(cudaStreamCreateWithPriority(&ln.stream, cudaStreamNonBlocking,
+                                               k == 0 ? hi_prio : lo_prio));
+            ln.own_stream = true;
+        }
+        if (precision == M1_MIXED) ln.model.reset(new m1::MixedModel());
+        else ln.model.reset(new m1::PlainModel());
+        M1_TRY(ln.model->sv_init(max_slots, lmax, ln.stream));
+        ln.slot_req.assign(max_slots, nullptr);
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMallocHost(&ln.snap[b], sizeof(m1::Ctl) * max_slots) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ln.snap_ev[b], cudaEventDisableTiming) != cudaSuccess)
+                return M1_ERR_OOM;
+        }
+    }
     s->structure = m1::Params{ p.nu0, p.nu_l, p.m_pseudo, p.m_coarse };
     s->precision = precision;
     s->L = lmax;
     s->max_slots = max_slots;
     s->budget = hbm_budget_bytes;
-    s->slot_req.assign(max_slots, nullptr);
-    for (int k = 0; k < 2; ++k) {
-        if (cudaMallocHost(&s->snap[k], sizeof(m1::Ctl) * max_slots) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->snap_ev[k], cudaEventDisableTiming) != cudaSuccess)
-            return M1_ERR_OOM;
-    }
+    s->small_cells = small_cells;
     cudaGetDevice(&s->device);
     m1_server* raw = s.release();
-    raw->th = std::thread([raw] { raw->loop(); });
+    for (int k = 0; k < 2; ++k) raw->th[k] = std::thread([raw, k] { raw->loop(k); });
     *out = raw;
     return M1_OK;
 }
@@ -300,14 +351,15 @@ m1_status m1_serve_submit(m1_server_t s, m1_grid_t g, int nsteps, double dt,
     if (r->params.nu0 != s->structure.nu0 || r->params.m_pseudo != s->structure.m ||
         r->params.m_coarse != s->structure.mc)
         return M1_ERR_INVALID_ARG;
-    r->bytes = s->model->sv_bytes(d);
+    r->lane = (long long)d.nx * (d.dim == 2 ? d.ny : 1) <= s->small_cells ? 0 : 1;
+    r->bytes = s->lanes[r->lane].model->sv_bytes(d);
     if (r->bytes > s->budget) return M1_ERR_REJECTED;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return s->error != M1_OK ? (m1_status)s->error : M1_ERR_REJECTED;
         r->ticket = s->next_ticket++;
         s->reqs[r->ticket] = r;
-        s->queue.push_back(r);
+        s->lanes[r->lane].queue.push_back(r);
         *ticket = r->ticket;
     }
     s->cv_work.notify_all();
@@ -352,10 +404,13 @@ m1_status m1_server_get_stats(m1_server_t s, m1_server_stats* out)
     st.solves_per_s = st.wall_s > 0 ? s->steps_done / st.wall_s : 0.0;
     st.bytes_in_use = (long long)s->used;
     st.bytes_peak = (long long)s->peak;
-    int active = 0;
-    for (auto& r : s->slot_req) active += r ? 1 : 0;
+    int active = 0, queued = 0;
+    for (const Lane& ln : s->lanes) {
+        for (auto& r : ln.slot_req) active += r ? 1 : 0;
+        queued += (int)ln.queue.size();
+    }
     st.active = active;
-    st.queued = (int)s->queue.size();
+    st.queued = queued;
     if (!s->latencies_ms.empty()) {
         std::vector<double> v = s->latencies_ms;
         std::sort(v.begin(), v.end());
@@ -383,7 +438,8 @@ m1_status m1_server_destroy(m1_server_t s)
         s->stop = true;
     }
     s->cv_work.notify_all();
-    if (s->th.joinable()) s->th.join();
+    for (auto& t : s->th)
+        if (t.joinable()) t.join();
     const m1_status err = (m1_status)s->error;
     delete s;
     return err;

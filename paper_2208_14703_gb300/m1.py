@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "NONADMISSIBLE_INP
 BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
 FP64, MIXED = 0, 1
 DTAU_ABS, DTAU_SIGNED = 0, 1
+SMALL_CELLS = 65536          # servers: requests of at most this many cells take the small lane
 OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 
 EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
@@ -127,7 +128,8 @@ _lib.m1_batch_get_state.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctype
 _lib.m1_batch_implicit_step.argtypes = [_vp, _dp, ctypes.POINTER(SolveParams),
                                         ctypes.POINTER(StepStats)]
 _lib.m1_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                  ctypes.POINTER(SolveParams), _vp, ctypes.POINTER(_vp)]
+                                  ctypes.POINTER(SolveParams), ctypes.c_longlong, _vp,
+                                  ctypes.POINTER(_vp)]
 _lib.m1_serve_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_double,
                                  ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_ulonglong)]
 _lib.m1_serve_poll.argtypes = [_vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_int),
@@ -311,11 +313,11 @@ class Server:
     """Owner of one m1_server_t (continuous-batching request loop)."""
 
     def __init__(self, budget_bytes, max_slots, lmax, precision=FP64, structure=None,
-                 stream=None):
+                 stream=None, small_cells=SMALL_CELLS):
         h = _vp()
         st = _lib.m1_server_create(int(budget_bytes), max_slots, lmax, precision,
-                                   ctypes.byref(structure) if structure else None, stream,
-                                   ctypes.byref(h))
+                                   ctypes.byref(structure) if structure else None,
+                                   int(small_cells), stream, ctypes.byref(h))
         _check(st, "m1_server_create")
         self.h = h
         self._held = {}   # grids in flight, kept alive until their tickets complete

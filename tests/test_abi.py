@@ -107,15 +107,16 @@ def test_invalid_batches_servers_and_parameters_rejected(lib):
     arr = (m1.GridDesc * 2)(a, b)                 # level counts differ
     assert m1._lib.m1_create_batch(arr, 2, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_create_batch(arr, 0, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
-    for budget, slots, lmax, prec in ((0, 4, 3, 0), (1 << 20, 0, 3, 0), (1 << 20, 4, 0, 0),
-                                      (1 << 20, 4, 3, 2)):
-        assert m1._lib.m1_server_create(budget, slots, lmax, prec, None, None,
+    for budget, slots, lmax, prec, small in ((0, 4, 3, 0, 0), (1 << 20, 0, 3, 0, 0),
+                                             (1 << 20, 4, 0, 0, 0), (1 << 20, 4, 3, 2, 0),
+                                             (1 << 20, 4, 3, 0, -1)):
+        assert m1._lib.m1_server_create(budget, slots, lmax, prec, None, small, None,
                                         ctypes.byref(h)) == m1.ERR_INVALID_ARG
     p = m1.m1_default_params(nu_l=2)              # the paper fixes one sweep per pseudo step
-    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), None,
+    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), 0, None,
                                     ctypes.byref(h)) == m1.ERR_INVALID_ARG
     p = m1.m1_default_params(dtau_rule=2)
-    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), None,
+    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), 0, None,
                                     ctypes.byref(h)) == m1.ERR_INVALID_ARG
     t = ctypes.c_ulonglong()
     assert m1._lib.m1_serve_submit(None, None, 1, 0.1, None, ctypes.byref(t)) == m1.ERR_INVALID_ARG

@@ -38,8 +38,8 @@ def run_alone(case, nsteps, tol, precision):
     return out, cycles
 
 
-def serve(reqs, precision, budget, max_slots, stagger=False):
-    srv = m1.Server(budget, max_slots, reqs[0][0]["lmax"], precision)
+def serve(reqs, precision, budget, max_slots, stagger=False, small_cells=m1.SMALL_CELLS):
+    srv = m1.Server(budget, max_slots, reqs[0][0]["lmax"], precision, small_cells=small_cells)
     grids, tickets = [], []
     for k, (c, nsteps, tol) in enumerate(reqs):
         g = m1.grid_from_case(c, precision=precision)
@@ -72,6 +72,25 @@ def test_served_equals_alone(precision):
     assert stats.steps_done == sum(n for _, n, _ in reqs)
     assert 0 < stats.p50_ms <= stats.p99_ms
     assert stats.active == 0 and stats.queued == 0 and stats.bytes_in_use == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_and_large_lanes_equal_alone(precision):
+    """A 384^2 request (147456 cells) runs in the large lane, beside small
+    requests in the small lane (their own engine, stream and scheduler thread):
+    every result equals the same steps run alone, and so does a one-lane server
+    (small_cells 0) on the same mix."""
+    big = inputs.hot_square_2d(384, lmax=4, tol=1e-7)
+    reqs = [(big, 2, 1e-7)] + requests()[:3] + requests()[4:5]
+    alone = [run_alone(c, n, tol, precision) for c, n, tol in reqs]
+    for small in (m1.SMALL_CELLS, 0):
+        outs, lasts, stats = serve(reqs, precision, budget=1 << 34, max_slots=4, small_cells=small)
+        for k, (c, nsteps, tol) in enumerate(reqs):
+            st, done, last = lasts[k]
+            assert st == m1.OK and done == nsteps
+            assert last.cycles == alone[k][1][-1], (small, k)
+            np.testing.assert_array_equal(alone[k][0], outs[k])
+        assert stats.requests_done == len(reqs) and stats.bytes_in_use == 0
 
 
 def test_budget_bounds_resident_bytes():
