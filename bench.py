@@ -57,18 +57,18 @@ SWEEP_BYTES = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8
 # launch (dram__bytes_read.sum + dram__bytes_write.sum = 457.8 MB / 4,194,304 cells)
 SWEEP64_TRAFFIC_PER_CELL = 457.8e6 / (2048 * 2048)
 # FP64 work of one fine Jacobi update (2D), counted in FP64-pipe operations
-# (each DFMA, DMUL or DADD is one issue slot; a reciprocal = hardware estimate +
-# 4 DFMA of Newton refinement = 5; a square root = estimate + 8) on the
-# arithmetic as written, with one closure per cell (halo re-evaluations are
-# not algorithmic work):
-#   closure 39 (reciprocal of E 5, f^2 and its clamp 7, square root 9,
-#     reciprocal of 2 + s 6, coefficients 4, P 8)
+# (each DFMA, DMUL, DADD, FP64 compare or FP32<->FP64 conversion is one issue
+# slot; a reciprocal = hardware estimate + 3 DFMA of third-order refinement = 4;
+# a square root = estimate + 5) on the arithmetic as written, with one closure
+# per cell (halo re-evaluations are not algorithmic work):
+#   closure 29 (reciprocal of E 4, F/E 2, 4 - 3 f^2 3 and its clamp 1, square
+#     root 6, E (s - 1)/3 2, 3/(c^2 (2 + s)) 6, q F/E 2, P 3)
 #   neighbour operators 26 (x faces 13, y faces 13)
 #   opacity products and right-hand sides 6
-#   local solve 48 (one reciprocal for both denominators 10, flux 2, quartic
-#     setup and conversions 9, one FP64 Halley step after the FP32 Newton
-#     iteration 23, E 4)
-SWEEP_OPS = 39 + 26 + 6 + 48
+#   local solve 42 (one reciprocal for both denominators 9, flux 2, quartic
+#     setup and conversions 8, one FP64 Halley step after the FP32 Newton
+#     iteration 18, E 5)
+SWEEP_OPS = 29 + 26 + 6 + 42
 # GB300 FP64 pipe: 2 operations per clock per SM (nominal 1.25 TFLOP/s counts a
 # DFMA as 2 flops): 152 SMs x 2 x 2.07 GHz.
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
@@ -439,7 +439,7 @@ def main():
             "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep64_ms,
             "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (no measured FP64 "
                            "peak in MEASURED_PEAKS.json)",
-            "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL or DADD)",
+            "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL, DADD, FP64 compare or conversion)",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                               "2048^2 launch (457.8 MB), scaled to 1024^2 by cells",
             "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",

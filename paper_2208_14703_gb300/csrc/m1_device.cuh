@@ -118,23 +118,27 @@ constexpr int kPersistentBlocks = 152 * 4;
 // relative to the correction.
 template <typename R> struct Fm;
 template <> struct Fm<double> {
+    // 1/a from the hardware estimate r0 with relative error e = 1 - a r0:
+    // 1/a = r0 / (1 - e) = r0 (1 + e + e^2 + ...); keeping e^2 makes the error
+    // third order in e, so one step reaches FP64 rounding.
     __device__ static __forceinline__ double rcp(double a)
     {
         double r;
         asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
-        double e = fma(-a, r, 1.0);
-        r = fma(r, e, r);
-        e = fma(-a, r, 1.0);
-        return fma(r, e, r);
+        const double e = fma(-a, r, 1.0);
+        return fma(r, fma(e, e, e), r);
     }
+    // sqrt(a) from the hardware estimate y of 1/sqrt(a): with s0 = a y and
+    // t = 1 - s0 y (= 1 - a y^2), sqrt(a) = s0 (1 - t)^(-1/2)
+    // = s0 (1 + t/2 + 3 t^2/8 + ...) (binomial series); the t^2 term makes the
+    // error third order in t.
     __device__ static __forceinline__ double sqrt(double a)
     {
         double y;
         asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-        const double h = 0.5 * y;
-        y = fma(h, fma(-a * y, y, 1.0), y);
-        const double s = a * y;
-        return fma(0.5 * y, fma(-s, s, a), s);
+        const double s0 = a * y;
+        const double t = fma(-s0, y, 1.0);
+        return fma(s0 * t, fma(0.375, t, 0.5), s0);
     }
 };
 template <> struct Fm<float> {
@@ -162,16 +166,19 @@ template <> struct Fm<float> {
 template <typename R>
 __device__ __forceinline__ void closure(R E, R Fx, R Fy, R inv_c2, R& Pxx, R& Pxy, R& Pyy)
 {
-    R iE = Fm<R>::rcp(E);
-    R fx = Fx * iE, fy = Fy * iE;
-    R f2 = (fx * fx + fy * fy) * inv_c2;
-    f2 = f2 < R(1) ? f2 : R(1);
-    R s = Fm<R>::sqrt(R(4) - R(3) * f2);
-    R iso = (s - R(1)) * (R(1) / R(3));
-    R q = R(3) * Fm<R>::rcp(R(2) + s) * inv_c2;
-    Pxx = E * (iso + q * fx * fx);
-    Pxy = E * (q * fx * fy);
-    Pyy = E * (iso + q * fy * fy);
+    const R iE = Fm<R>::rcp(E);
+    const R fx = Fx * iE, fy = Fy * iE;
+    // 4 - 3 f^2 with f^2 = |F/E|^2 / c^2 clamped to 1
+    R a = fma(fma(fy, fy, fx * fx), R(-3) * inv_c2, R(4));
+    a = a > R(1) ? a : R(1);
+    const R s = Fm<R>::sqrt(a);
+    const R Eiso = E * fma(s, R(1) / R(3), R(-1) / R(3));
+    const R q = Fm<R>::rcp(R(2) + s) * (R(3) * inv_c2);
+    // E q (F/E)(F/E)^T = q (F/E) F^T
+    const R qx = q * fx, qy = q * fy;
+    Pxx = fma(qx, Fx, Eiso);
+    Pxy = qx * Fy;
+    Pyy = fma(qy, Fy, Eiso);
 }
 
 // Largest tau >= 0 with u + tau d admissible (E > 0, T > 0, |F| <= c E): the
@@ -241,18 +248,19 @@ template <> struct Quartic<double> {
         bool ok32;
         double T = (double)newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
         // One step of Halley's method (cubically convergent):
-        // T <- T - 2 g g' / (2 g'^2 - g g''), g' = C + 4 K T^3, g'' = 12 K T^2.
-        // From the FP32 root (relative error near 1e-7) it lands at FP64
-        // rounding.  The quotient needs only ~1e-14 relative accuracy (it
-        // multiplies a correction of ~1e-7 T): FP32 reciprocal estimate of the
-        // denominator plus one FP64 Newton step.
+        // T <- T - 2 g g' / (2 g'^2 - g g'') = T - g g' / (g'^2 - 6 K T^2 g),
+        // g' = C + 4 K T^3, g'' = 12 K T^2.  From the FP32 root (relative
+        // error near 1e-7) it lands at FP64 rounding.  The quotient needs only
+        // ~1e-14 relative accuracy (it multiplies a correction of ~1e-7 T):
+        // FP32 reciprocal estimate of the denominator plus one FP64 Newton step.
         const double T2 = T * T;
-        const double g = fma(K, T2 * T2, C * T) - Rr;
-        const double d1 = fma(4.0 * K, T2 * T, C);
-        const double den = fma(2.0 * d1, d1, -g * (12.0 * K * T2));
+        const double KT2 = K * T2;
+        const double g = fma(KT2, T2, fma(C, T, -Rr));
+        const double d1 = fma(4.0 * KT2, T, C);
+        const double den = fma(d1, d1, -(6.0 * KT2) * g);
         double r = (double)Fm<float>::rcp((float)den);
         r = fma(r, fma(-den, r, 1.0), r);
-        double dT = 2.0 * g * d1 * r;
+        double dT = g * d1 * r;
         T -= dT;
         if (fabs(dT) > 1e-6 * T) {
             // the FP32 start was not close enough for one cubic step: Newton
@@ -302,12 +310,15 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
     const R iF = dE * ip, iAk = dF * ip;
     o.Fx = bFx * iF;
     o.Fy = bFy * iF;
-    R K = k * A * a_r * iAk;
-    R Rr = bT + k * bE * iAk;
-    R T = Quartic<R>::solve(C, K, Rr, ok);
-    R T2 = T * T;
+    // with kk = k / (A + k): K = kk A a_r, R = bT + kk bE,
+    // E = (bE + k a_r T^4) / (A + k) = bE / (A + k) + kk a_r T^4
+    const R kk = k * iAk;
+    const R K = (A * a_r) * kk;
+    const R Rr = fma(kk, bE, bT);
+    const R T = Quartic<R>::solve(C, K, Rr, ok);
+    const R T2 = T * T;
     o.T = T;
-    o.E = (bE + k * a_r * T2 * T2) * iAk;
+    o.E = fma(a_r * kk, T2 * T2, bE * iAk);
     return o;
 }
 
