@@ -28,7 +28,7 @@ namespace m1 {
 namespace {
 
 constexpr int kClasses = 16;                 // size classes 2^0 .. 2^15 (sqrt of the cell count)
-constexpr int kCandidates[] = { 1, 2, 4, 8, 16, 32 };
+constexpr int kCandidates[] = { 1, 2, 4, 8, 12, 16, 24, 32 };
 
 std::mutex g_tune_mu;
 int g_rows[2][kClasses] = {};                // [kind][class], 0 = untuned

@@ -45,7 +45,7 @@ def test_autotune_entries(restore_tuning):
     ent = m1.autotune()
     assert {(e["kind"], e["n"]) for e in ent} == {(k, 1 << c) for k in (0, 1) for c in range(4, 12)}
     for e in ent:
-        assert e["strip_rows"] in (1, 2, 4, 8, 16, 32) and e["strip_rows"] <= e["n"]
+        assert e["strip_rows"] in (1, 2, 4, 8, 12, 16, 24, 32) and e["strip_rows"] <= e["n"]
         assert e["staging"] in ((0,) if e["kind"] == 0 else (0, 1))
         assert e["ms"] > 0 and (np.isnan(e["ms_default"]) or e["ms"] <= e["ms_default"])
         assert m1.strip_rows(e["kind"], e["n"], e["n"]) == e["strip_rows"]
@@ -54,8 +54,9 @@ def test_autotune_entries(restore_tuning):
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [0, 1])
 def test_strip_shape_changes_no_arithmetic(precision, restore_tuning):
-    """Strip heights 1 and 32 give bitwise equal steps (the same kernel, every
-    cell's update the same whatever strip it falls in).  The two row stagings of
+    """Strip heights 1, 24 and 32 give bitwise equal steps (the same kernel,
+    every cell's update the same whatever strip it falls in; 24 rows leave a
+    partial strip at the top of every level).  The two row stagings of
     the FP32 correction form are two kernels whose FP32 contractions may round
     differently, so their steps agree to rounding: same cycle count, results
     within 1e-10 relative.  Checked on a square hot-square grid and on a ragged
@@ -66,7 +67,7 @@ def test_strip_shape_changes_no_arithmetic(precision, restore_tuning):
     cases[1]["tol"] = 1e-8
     for case in cases:
         outs = {}
-        for rows, staging in ((1, 0), (32, 0), (1, 1), (32, 1)):
+        for rows, staging in ((1, 0), (24, 0), (32, 0), (1, 1), (24, 1), (32, 1)):
             if staging and precision == 0:
                 continue
             m1.set_tuning([{"kind": k, "n": 1 << c, "strip_rows": rows,
@@ -77,8 +78,9 @@ def test_strip_shape_changes_no_arithmetic(precision, restore_tuning):
             outs[rows, staging] = (st.cycles, np.stack(g.get_state()))
             g.close()
         for staging in (0, 1) if precision else (0,):
-            assert outs[32, staging][0] == outs[1, staging][0]
-            np.testing.assert_array_equal(outs[32, staging][1], outs[1, staging][1])
+            for rows in (24, 32):
+                assert outs[rows, staging][0] == outs[1, staging][0]
+                np.testing.assert_array_equal(outs[rows, staging][1], outs[1, staging][1])
         if precision:
             a, b = outs[1, 0], outs[1, 1]
             assert a[0] == b[0]
