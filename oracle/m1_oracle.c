@@ -693,11 +693,76 @@ static int fine_jacobi(level_t* q, double dt, const double* b, double* u, int nu
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cycle shapes.  Section 4.2 builds the V-cycle by applying the two-grid FAS
+ * correction recursively down to the coarsest grid; Section 6.3 names the W-
+ * and F-cycles as the unexplored alternatives.  A visit of coarse level l takes
+ * its FAS problem A_l(u_l) = f_l from the restriction made by level l - 1 when
+ * it is fresh (f_l = A_l(v_l) + r_l, u_l = v_l, Eq. (24)), or keeps f_l and the
+ * current u_l when it is a repeated visit; it pre-smooths, restricts to level
+ * l + 1, applies the coarse-grid corrections of level l + 1, prolongates the
+ * correction (Eq. (34)) and post-smooths.  The coarse-grid corrections of
+ * level l are [READING]: V, one visit of level l + 1; W, two visits (the second
+ * repeated: the standard gamma = 2 recursion); F, a fresh F-visit followed by a
+ * repeated V-visit; the coarsest level, solved by pseudo-time stepping, is
+ * visited once per correction whatever the shape.  With L_max <= 2 the three
+ * shapes are the same cycle. */
+enum { CYCLE_V = 0, CYCLE_W = 1, CYCLE_F = 2 };
+
+typedef struct {
+    double dt, dtau, th_ex, th_c;
+    int m, mc, nul, literal, L;
+    int newton_fail, damped;
+    double* visits;               /* visits of each level, summed over the step */
+} cycle_ctx_t;
+
+static void coarse_visit(level_t* lv, int l, int fresh, int shape, cycle_ctx_t* c);
+
+static void coarse_corrections(level_t* lv, int l, int shape, cycle_ctx_t* c)
+{
+    if (l + 1 == c->L - 1 || shape == CYCLE_V) {
+        coarse_visit(lv, l + 1, 1, shape, c);
+    } else if (shape == CYCLE_W) {
+        coarse_visit(lv, l + 1, 1, CYCLE_W, c);
+        coarse_visit(lv, l + 1, 0, CYCLE_W, c);
+    } else {
+        coarse_visit(lv, l + 1, 1, CYCLE_F, c);
+        coarse_visit(lv, l + 1, 0, CYCLE_V, c);
+    }
+}
+
+static void coarse_visit(level_t* lv, int l, int fresh, int shape, cycle_ctx_t* c)
+{
+    level_t* q = &lv[l];
+    size_t n = (size_t)q->g.nx * q->g.ny;
+    c->visits[l] += 1.0;
+    if (fresh) {
+        fas_rhs(q, c->dt);
+        memcpy(q->u, q->v, 4 * n * sizeof(double));
+    }
+    if (l == c->L - 1) {
+        if (pseudo_time_smooth(&q->g, c->dt, q->sa, q->ss, q->f, q->u, c->dtau, c->mc, c->nul, c->th_ex) < 0)
+            ++c->newton_fail;
+        return;
+    }
+    level_t* p = &lv[l + 1];
+    if (pseudo_time_smooth(&q->g, c->dt, q->sa, q->ss, q->f, q->u, c->dtau, c->m, c->nul, c->th_ex) < 0)
+        ++c->newton_fail;
+    level_residual(q, c->dt, q->f, q->u, q->r);                /* r_bar = f - A(u) */
+    restrict_state(&q->g, &p->g, c->literal ? q->v : q->u, p->v, KIND_STATE);
+    restrict_state(&q->g, &p->g, q->r, p->r, KIND_DIFF);
+    coarse_corrections(lv, l, shape, c);
+    if (c->literal) memcpy(q->u, q->v, 4 * n * sizeof(double));
+    c->damped += prolong_correct(&p->g, &q->g, p->u, p->v, q->u, c->th_c);
+    if (pseudo_time_smooth(&q->g, c->dt, q->sa, q->ss, q->f, q->u, c->dtau, c->m, c->nul, c->th_ex) < 0)
+        ++c->newton_fail;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Appendix A, Algorithm 4: one implicit time step, v^n -> v^{n+1}.
  *
  * Parameters (ip / dp arrays, Section 5 defaults in parentheses):
  *   ip = { L_max, nu0 (3), nu_l (1), m (3), m_coarse (3), max_cycles, literal_fas,
- *          dtau_rule }
+ *          dtau_rule, cycle shape (0 V, 1 W, 2 F; see coarse_corrections) }
  *   dp = { dtau0 (1e-3), grow (1.1), shrink (0.5), eps_i, eps_d, tol,
  *          dtau_min, dtau_max, theta_ex (1/2), theta_c (1/2) }
  * The state v (4 planes) holds v^n on entry, v^{n+1} on return; b = (E^n, F^n,
@@ -717,20 +782,24 @@ static int fine_jacobi(level_t* q, double dt, const double* b, double* u, int nu
  *    residual decreases fast enough, decrease when it decreases slowly), so that
  *    a growing residual shrinks dtau; Algorithm 4 prints the absolute change.
  *  - literal_fas = 1 restricts and corrects the unsmoothed v_l instead (the
- *    letter of Algorithm 4), kept only for comparison.
+ *    letter of Algorithm 4), kept only for comparison (V-cycles only).
  * Outputs: stats = { cycles, res0, res, dtau, fine_sweeps, status, newton_fail,
- *   damped_cells }, res_hist[kappa] = ||r_kappa|| (kappa = 0..cycles, length
+ *   damped_cells, visits of level 0 .. L_max - 1 summed over the step }, res_hist[kappa] = ||r_kappa|| (kappa = 0..cycles, length
  *   max_cycles+1), dtau_hist[kappa-1] = dtau used in cycle kappa.
- * status: 0 converged, -4 not converged after max_cycles, -2 inadmissible input. */
+ * status: 0 converged, -4 not converged after max_cycles, -2 inadmissible input,
+ * -1 invalid parameters (an unknown cycle shape, or literal_fas with W or F). */
 int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflow, double dt,
                       const double* sa, const double* ss, const int* ip, const double* dp,
                       double* v, double* stats, double* res_hist, double* dtau_hist)
 {
     grid_t g0; grid_from_desc(&g0, idesc, ddesc, inflow);
     int L = ip[0], nu0 = ip[1], nul = ip[2], m = ip[3], mc = ip[4], maxc = ip[5], literal = ip[6];
-    int signed_rule = ip[7];
+    int signed_rule = ip[7], shape = ip[8];
     double dtau = dp[0], grow = dp[1], shrink = dp[2], eps_i = dp[3], eps_d = dp[4], tol = dp[5];
     double dtau_min = dp[6], dtau_max = dp[7], th_ex = dp[8], th_c = dp[9];
+    if (shape < CYCLE_V || shape > CYCLE_F || (literal && shape != CYCLE_V)) {
+        stats[5] = -1; return -1;
+    }
     size_t n0 = (size_t)g0.nx * g0.ny;
     for (size_t k = 0; k < n0; ++k) {
         cell_t s = load(&g0, v, (int)(k % g0.nx), (int)(k / g0.nx));
@@ -741,6 +810,8 @@ int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflo
     level_t* lv = calloc((size_t)L, sizeof(level_t));
     build_levels(lv, L, &g0, sa, ss);
     level_t* q0 = &lv[0];
+    double* visits = stats + 8;
+    for (int l = 0; l < L; ++l) visits[l] = 0.0;
     /* Algorithm 4: b^h = v^n (E, F; [EXT] C_v T^n for the gas row), v_(0) = v^n. */
     double* b = malloc(4 * n0 * sizeof(double));
     memcpy(b, v, 4 * n0 * sizeof(double));
@@ -759,50 +830,25 @@ int ora_implicit_step(const int* idesc, const double* ddesc, const double* inflo
     if (res0 > 1e-14 * transport_diag(&g0, dt) * bnorm) {
         status = -4;
         while (kappa < maxc) {
-            /* ---- down leg ---- */
+            /* ---- fine level (Algorithm 1 sweeps), then the coarse-grid
+             * corrections of the cycle's shape ---- */
             memcpy(q0->u, q0->v, 4 * n0 * sizeof(double));
-            for (int l = 0; l < L - 1; ++l) {
-                level_t* q = &lv[l];
-                level_t* p = &lv[l + 1];
-                size_t n = (size_t)q->g.nx * q->g.ny;
-                if (l == 0) {
-                    if (fine_jacobi(q, dt, b, q->u, nu0) < 0) ++newton_fail;
-                    fine_sweeps += nu0;
-                    level_residual(q, dt, b, q->u, q->r);
-                } else {
-                    fas_rhs(q, dt);
-                    memcpy(q->u, q->v, 4 * n * sizeof(double));
-                    if (pseudo_time_smooth(&q->g, dt, q->sa, q->ss, q->f, q->u, dtau, m, nul, th_ex) < 0) ++newton_fail;
-                    level_residual(q, dt, q->f, q->u, q->r);       /* r_bar = f - A(u) */
-                }
-                restrict_state(&q->g, &p->g, literal ? q->v : q->u, p->v, KIND_STATE);
-                restrict_state(&q->g, &p->g, q->r, p->r, KIND_DIFF);
-            }
-            /* ---- coarsest level ---- */
-            {
-                level_t* q = &lv[L - 1];
-                size_t n = (size_t)q->g.nx * q->g.ny;
-                if (L == 1) {
-                    if (fine_jacobi(q, dt, b, q->u, nu0) < 0) ++newton_fail;
-                    fine_sweeps += nu0;
-                } else {
-                    fas_rhs(q, dt);
-                    memcpy(q->u, q->v, 4 * n * sizeof(double));
-                    if (pseudo_time_smooth(&q->g, dt, q->sa, q->ss, q->f, q->u, dtau, mc, nul, th_ex) < 0) ++newton_fail;
-                }
-            }
-            /* ---- up leg ---- */
-            for (int l = L - 2; l >= 0; --l) {
-                level_t* q = &lv[l];
-                level_t* p = &lv[l + 1];
-                if (literal) memcpy(q->u, q->v, 4 * (size_t)q->g.nx * q->g.ny * sizeof(double));
-                damped += prolong_correct(&p->g, &q->g, p->u, p->v, q->u, th_c);
-                if (l == 0) {
-                    if (fine_jacobi(q, dt, b, q->u, nu0) < 0) ++newton_fail;
-                    fine_sweeps += nu0;
-                } else {
-                    if (pseudo_time_smooth(&q->g, dt, q->sa, q->ss, q->f, q->u, dtau, m, nul, th_ex) < 0) ++newton_fail;
-                }
+            visits[0] += 1.0;
+            if (fine_jacobi(q0, dt, b, q0->u, nu0) < 0) ++newton_fail;
+            fine_sweeps += nu0;
+            if (L > 1) {
+                level_t* p = &lv[1];
+                cycle_ctx_t c = { dt, dtau, th_ex, th_c, m, mc, nul, literal, L, 0, 0, visits };
+                level_residual(q0, dt, b, q0->u, q0->r);
+                restrict_state(&q0->g, &p->g, literal ? q0->v : q0->u, p->v, KIND_STATE);
+                restrict_state(&q0->g, &p->g, q0->r, p->r, KIND_DIFF);
+                coarse_corrections(lv, 0, shape, &c);
+                if (literal) memcpy(q0->u, q0->v, 4 * n0 * sizeof(double));
+                c.damped += prolong_correct(&p->g, &q0->g, p->u, p->v, q0->u, th_c);
+                if (fine_jacobi(q0, dt, b, q0->u, nu0) < 0) ++c.newton_fail;
+                fine_sweeps += nu0;
+                newton_fail += c.newton_fail;
+                damped += c.damped;
             }
             /* ---- end of cycle: v <- u, residual, pseudo-time step control ---- */
             memcpy(q0->v, q0->u, 4 * n0 * sizeof(double));

@@ -234,6 +234,7 @@ class SolveParams:
     max_cycles: int = 20000
     literal_fas: int = 0
     dtau_rule: int = 0
+    cycle: int = 0              # 0 V, 1 W, 2 F (Section 6.3; shapes in m1_oracle.c)
     dtau0: float = 1e-3
     grow: float = 1.1
     shrink: float = 0.5
@@ -247,13 +248,13 @@ class SolveParams:
 
     def arrays(self):
         ip = np.array([self.lmax, self.nu0, self.nu_l, self.m, self.m_coarse, self.max_cycles,
-                       self.literal_fas, self.dtau_rule], dtype=np.int32)
+                       self.literal_fas, self.dtau_rule, self.cycle], dtype=np.int32)
         dp = np.array([self.dtau0, self.grow, self.shrink, self.eps_i, self.eps_d, self.tol,
                        self.dtau_min, self.dtau_max, self.theta_ex, self.theta_c])
         return ip, dp
 
 
-STATUS = {0: "ok", -2: "nonadmissible_input", -4: "not_converged"}
+STATUS = {0: "ok", -1: "invalid_parameters", -2: "nonadmissible_input", -4: "not_converged"}
 
 
 def implicit_step(g: Grid, dt, sa, ss, v, params: SolveParams):
@@ -261,7 +262,7 @@ def implicit_step(g: Grid, dt, sa, ss, v, params: SolveParams):
     v = _f64(v).copy()
     sa, ss = _f64(sa), _f64(ss)
     ip, dp = params.arrays()
-    stats = np.zeros(8)
+    stats = np.zeros(8 + params.lmax)
     res_hist = np.zeros(params.max_cycles + 1)
     dtau_hist = np.zeros(max(params.max_cycles, 1))
     lib().ora_implicit_step(g.ip(), g.dp(), _d(g.inflow), dt, _d(sa), _d(ss),
@@ -269,7 +270,8 @@ def implicit_step(g: Grid, dt, sa, ss, v, params: SolveParams):
                             _d(dtau_hist))
     cyc = int(stats[0])
     st = dict(cycles=cyc, res0=stats[1], res=stats[2], dtau=stats[3], fine_sweeps=int(stats[4]),
-              status=int(stats[5]), newton_fail=int(stats[6]), damped=int(stats[7]))
+              status=int(stats[5]), newton_fail=int(stats[6]), damped=int(stats[7]),
+              visits=[int(x) for x in stats[8:]])
     return v, st, res_hist[:cyc + 1].copy(), dtau_hist[:cyc].copy()
 
 

@@ -279,3 +279,82 @@ def test_dtau_rules_follow_their_wording():
             grew += 1
     assert grew >= 1
     assert st1[0]["cycles"] == st0[0]["cycles"]   # the rules agree while the residual falls
+
+
+# ---- cycle shapes (Section 4.2 builds the V-cycle by recursion; Section 6.3
+# names W- and F-cycles as the alternatives) ----
+
+def _shape_case():
+    return inputs.random_admissible_2d(32, 32, seed=21, fmax=0.8, cfl=20, bc=("reflect",) * 4,
+                                       lmax=5)
+
+
+@pytest.mark.parametrize("lmax", [1, 2])
+def test_cycle_shapes_coincide_with_two_levels(lmax):
+    """With at most two grids every shape is the same cycle: the coarsest grid is
+    visited once per coarse-grid correction, so W and F equal V bit for bit."""
+    case = _shape_case()
+    g = O.Grid.from_case(case)
+    outs = []
+    for shape in (0, 1, 2):
+        v, st, hist, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"],
+                                         O.SolveParams(lmax=lmax, tol=0.0, max_cycles=5,
+                                                       cycle=shape))
+        outs.append((v, hist))
+    for v, hist in outs[1:]:
+        np.testing.assert_array_equal(v, outs[0][0])
+        np.testing.assert_array_equal(hist, outs[0][1])
+
+
+@pytest.mark.parametrize("shape,per_cycle", [(0, [1, 1, 1, 1, 1]), (1, [1, 2, 4, 8, 8]),
+                                             (2, [1, 2, 3, 4, 4])])
+def test_cycle_shape_visits_each_level_as_its_recursion_says(shape, per_cycle):
+    """Visits per cycle with five grids.  V: every level once.  W (two coarse-grid
+    corrections per level): level l visited 2^l times, the coarsest as often as
+    the level above it.  F (an F- then a V-correction): level l visited l + 1
+    times, the coarsest as often as the level above it."""
+    case = _shape_case()
+    g = O.Grid.from_case(case)
+    _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"],
+                                  O.SolveParams(lmax=5, tol=0.0, max_cycles=3, cycle=shape))
+    assert st["cycles"] == 3 and st["fine_sweeps"] == 3 * 2 * 3
+    assert st["visits"] == [3 * k for k in per_cycle]
+
+
+def test_w_cycle_repeats_the_coarse_correction_from_the_improved_iterate():
+    """With three grids one W-cycle differs from one V-cycle: the second visit of
+    level 1 smooths on from the corrected iterate.  (Restarting it from the
+    restricted v_1 would repeat the first visit exactly and give the V-cycle.)"""
+    case = _shape_case()
+    g = O.Grid.from_case(case)
+    out = [O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"],
+                           O.SolveParams(lmax=3, tol=0.0, max_cycles=1, cycle=shape))
+           for shape in (0, 1)]
+    assert not np.array_equal(out[0][0], out[1][0])
+    assert out[1][1]["visits"] == [1, 2, 2]
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("dim,n,bc,lmax", [(1, 32, "reflect", 4), (2, 8, "periodic", 3)])
+def test_w_and_f_cycles_reach_the_brute_force_fixed_point(shape, dim, n, bc, lmax):
+    case = inputs.random_admissible_2d(n, n, seed=n + dim, fmax=0.7, cfl=4, bc=(bc,) * 4,
+                                       dim=dim)
+    g = O.Grid.from_case(case)
+    dt, sa, ss, v0 = case["dt"], case["sa"], case["ss"], case["state"]
+    b = O.rhs_of(g, v0)
+    mg, st, hist, _ = O.implicit_step(g, dt, sa, ss, v0,
+                                      O.SolveParams(lmax=lmax, tol=0.0, max_cycles=1500,
+                                                    cycle=shape))
+    assert hist[-1] <= 1e-15 * hist[0]
+    rng = np.random.default_rng(2)
+    nw = _newton_solve(g, dt, sa, ss, b, mg * (1 + 1e-3 * rng.standard_normal(mg.shape)))
+    np.testing.assert_allclose(mg, nw, rtol=0, atol=1e-11 * np.abs(nw[0]).max())
+
+
+def test_invalid_cycle_parameters_are_refused():
+    case = _shape_case()
+    g = O.Grid.from_case(case)
+    for kw in ({"cycle": 3}, {"cycle": 1, "literal_fas": 1}):
+        _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"],
+                                      O.SolveParams(lmax=3, max_cycles=2, **kw))
+        assert st["status"] == -1
