@@ -214,6 +214,33 @@ def bench_mixed(m1, case, stream, s0, flush, ref64, steps, hbm_peak):
                                     "kernel": "k_sweep<float, correction form>"}}
 
 
+def bench_cycle_shapes(m1, case, stream, s0, flush):
+    """Cycles to tolerance and step time of the same workload with V-, W- and
+    F-cycles (Section 6.3 names W and F as the alternatives), FP64 and mixed:
+    one untimed step, then one timed step per shape and precision."""
+    import torch
+    out = {}
+    for pname, prec in (("fp64", m1.FP64), ("mixed", m1.MIXED)):
+        grid = m1.grid_from_case(case, precision=prec, stream=stream.cuda_stream)
+        for sname, shape in (("V", m1.CYCLE_V), ("W", m1.CYCLE_W), ("F", m1.CYCLE_F)):
+            params = m1.m1_default_params(tol=case["tol"], cycle=shape)
+            grid.set_state(*s0, on_device=True)
+            grid.implicit_step(case["dt"], params)
+            grid.set_state(*s0, on_device=True)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = grid.implicit_step(case["dt"], params)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            out[f"{pname}_{sname}"] = {"cycles": st.cycles, "ms_per_step": ms,
+                                       "ms_per_cycle": ms / max(st.cycles, 1),
+                                       "launches_per_cycle": (st.launches - 4) / max(st.cycles, 1)}
+        grid.close()
+    return out
+
+
 def bench_batched(m1, count, stream):
     """Independent 2D instances of uneven sizes stepped together, mixed and FP64."""
     import torch
@@ -458,6 +485,7 @@ def main():
         from paper_2208_14703_gb300 import inputs
         extras["mixed"] = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps,
                                       pk["hbm_gbs"])
+        extras["cycle_shapes"] = bench_cycle_shapes(m1, case, stream, s0, flush)
         extras["batched"] = bench_batched(m1, args.batch_count, stream)
         if args.serve_full:
             reqs = inputs.serving_stream(64)

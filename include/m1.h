@@ -77,7 +77,8 @@ typedef struct {
  * shrink 0.5 (Algorithm 4), eps_i = 1e-2, eps_d = 1e-4, tol = 1e-8 (relative to
  * the initial residual), dtau clamped to [1e-12, 1e6], theta_ex = 0.5 (fraction
  * of the admissible explicit pseudo-time step), theta_c = 0.5 (damping of an
- * inadmissible prolongated cell), max_cycles = 20000, dtau_rule = M1_DTAU_ABS.
+ * inadmissible prolongated cell), max_cycles = 20000, dtau_rule = M1_DTAU_ABS,
+ * cycle = M1_CYCLE_V.
  * dtau_rule selects the residual change that drives dtau after each cycle:
  *   M1_DTAU_ABS     delta = | ||r_k|| - ||r_{k-1}|| | / ||r_0|| (as Algorithm 4
  *                   prints it): a fast-growing residual also grows dtau;
@@ -85,17 +86,28 @@ typedef struct {
  *                   Section 4 words the rule: increase dtau when the residual
  *                   decreases fast enough, decrease it when it decreases slowly),
  *                   so a growing residual halves dtau.
- * Then dtau *= grow if delta > eps_i, dtau *= shrink if delta < eps_d. */
+ * Then dtau *= grow if delta > eps_i, dtau *= shrink if delta < eps_d.
+ * cycle selects the cycle shape (default M1_CYCLE_V, the paper's; Section 6.3
+ * names W- and F-cycles as alternatives).  The coarse-grid corrections of level
+ * l are one visit of level l + 1 (V), two visits, the second continuing from
+ * the corrected iterate with the same FAS right-hand side (W), or an F-visit
+ * followed by such a repeated V-visit (F); the coarsest level is visited once
+ * per correction, so with lmax <= 2 the shapes coincide.  Each visit of a
+ * coarse level smooths m_pseudo pseudo-time steps before and after its
+ * corrections (the coarsest: m_coarse); the fine level is visited once per
+ * cycle whatever the shape. */
 enum { M1_DTAU_ABS = 0, M1_DTAU_SIGNED = 1 };
+enum { M1_CYCLE_V = 0, M1_CYCLE_W = 1, M1_CYCLE_F = 2 };
 typedef struct {
     int nu0, nu_l, m_pseudo, m_coarse;
     double dtau0, grow, shrink, eps_i, eps_d, tol, dtau_min, dtau_max, theta_ex, theta_c;
     int max_cycles;
     int dtau_rule;
+    int cycle;
 } m1_solve_params;
 
 /* Statistics of one implicit step.  res0/res: ||r|| before the first and after
- * the last V-cycle, ||r||^2 = sum over cells h^d (rE^2 + |rF|^2/c^2 + rT^2);
+ * the last cycle, ||r||^2 = sum over cells h^d (rE^2 + |rF|^2/c^2 + rT^2);
  * sweeps: fine-level Jacobi sweeps; ms: device time of the step. */
 typedef struct {
     int cycles;
@@ -133,7 +145,7 @@ m1_status m1_set_inflow(m1_grid_t g, int side, const double* E, const double* Fx
 m1_status m1_get_state(m1_grid_t g, double* E, double* Fx, double* Fy, double* T, int on_device);
 
 /* One implicit time step of length dt (Algorithm 4): b = (E^n, F^n, C_v T^n),
- * V-cycles until ||r|| <= tol ||r_0||, the state becomes v^{n+1}; no cycle at all
+ * cycles (of the shape params->cycle) until ||r|| <= tol ||r_0||, the state becomes v^{n+1}; no cycle at all
  * when ||r_0|| <= 1e-14 (1 + c dt/hx + c dt/hy) ||b|| (already solved to the
  * rounding of A, e.g. an equilibrium state E = a_r T^4, F = 0), the state
  * becomes v^{n+1}.  params may be NULL for the defaults; stats may be NULL.

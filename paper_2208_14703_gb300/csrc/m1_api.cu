@@ -94,7 +94,8 @@ m1_status validate_params(const m1_solve_params& sp)
 {
     if (sp.nu0 < 1 || sp.nu_l != 1 || sp.m_pseudo < 1 || sp.m_coarse < 1 || sp.max_cycles < 1 ||
         !(sp.tol >= 0) || !(sp.dtau0 > 0) || !(sp.theta_ex > 0) || !(sp.theta_c > 0) ||
-        (sp.dtau_rule != M1_DTAU_ABS && sp.dtau_rule != M1_DTAU_SIGNED))
+        (sp.dtau_rule != M1_DTAU_ABS && sp.dtau_rule != M1_DTAU_SIGNED) ||
+        sp.cycle < M1_CYCLE_V || sp.cycle > M1_CYCLE_F)
         return M1_ERR_INVALID_ARG;
     return M1_OK;
 }
@@ -581,40 +582,68 @@ void Engine<R>::fas_rhs(int l, cudaStream_t s)
     launch_apply<R>(dl, strips[l].view(), ctl, APPLY_FAS, -1, nullptr, 0, s, delta);
 }
 
-// One V-cycle of Algorithm 4 over every instance.  tail: end with the fine
-// residual norm and the stop test (the mixed-precision driver does its own).
+// Cycle shapes (Section 4.2 builds the V-cycle by recursion; Section 6.3 names
+// W- and F-cycles): the coarse-grid corrections of level l are one visit of
+// level l + 1 (V), two visits, the second continuing from the corrected
+// iterate (W), or an F-visit then a repeated V-visit (F); the coarsest level is
+// visited once per correction.  A fresh visit builds its FAS problem from the
+// restriction of level l; a repeated one keeps its right-hand side and iterate.
+template <typename R>
+void Engine<R>::corrections(const Params& p, int l, int shape, std::vector<int>& cur, cudaStream_t s)
+{
+    if (l + 1 == L - 1 || shape == M1_CYCLE_V) {
+        visit(p, l + 1, true, shape, cur, s);
+    } else if (shape == M1_CYCLE_W) {
+        visit(p, l + 1, true, M1_CYCLE_W, cur, s);
+        visit(p, l + 1, false, M1_CYCLE_W, cur, s);
+    } else {
+        visit(p, l + 1, true, M1_CYCLE_F, cur, s);
+        visit(p, l + 1, false, M1_CYCLE_V, cur, s);
+    }
+}
+
+// One visit of coarse level l >= 1: FAS right-hand side (Eq. (24)) when fresh,
+// m pseudo-time steps (Algorithm 3; the coarsest level: m_coarse and nothing
+// else), residual, restriction, the coarse-grid corrections, prolongation with
+// damping (Eq. (34)), m pseudo-time steps.
+template <typename R>
+void Engine<R>::visit(const Params& p, int l, bool fresh, int shape, std::vector<int>& cur,
+                      cudaStream_t s)
+{
+    Level<R>* dl = d + (size_t)l * cap;
+    if (fresh) fas_rhs(l, s);
+    if (l == L - 1) {
+        pseudo(l, cur[l], p.mc, fresh, s);
+        return;
+    }
+    pseudo(l, cur[l], p.m, fresh, s);
+    if (strips[l].n)
+        launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
+    if (chunks[l + 1].n)
+        launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
+    corrections(p, l, shape, cur, s);
+    if (chunks[l].n)
+        launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
+    pseudo(l, cur[l], p.m, false, s);
+}
+
+// One cycle of Algorithm 4 (of the shape p.cycle) over every instance.  tail:
+// end with the fine residual norm and the stop test (the mixed-precision
+// driver does its own).
 template <typename R>
 void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail)
 {
     std::vector<int> cur(L, 0);
     cur[0] = cur0;
-    for (int l = 0; l < L - 1; ++l) {
-        Level<R>* dl = d + (size_t)l * cap;
-        if (l == 0) {
-            sweeps_fine(cur[0], p.nu0, s);
-            launch_apply<R>(dl, strips[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
-        } else {
-            fas_rhs(l, s);
-            pseudo(l, cur[l], p.m, true, s);
-            if (strips[l].n)
-                launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
-        }
-        if (chunks[l + 1].n)
-            launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
-    }
-    if (L == 1) {
+    sweeps_fine(cur[0], p.nu0, s);
+    if (L > 1) {
+        launch_apply<R>(d, strips[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
+        if (chunks[1].n)
+            launch_restrict<R>(d, d + cap, chunks[1].view(), ctl, cur[0], s, delta);
+        corrections(p, 0, p.cycle, cur, s);
+        if (chunks[0].n)
+            launch_prolong<R>(d + cap, d, chunks[0].view(), ctl, cur[1], cur[0], s, delta);
         sweeps_fine(cur[0], p.nu0, s);
-    } else {
-        const int l = L - 1;
-        fas_rhs(l, s);
-        pseudo(l, cur[l], p.mc, true, s);
-    }
-    for (int l = L - 2; l >= 0; --l) {
-        Level<R>* dl = d + (size_t)l * cap;
-        if (chunks[l].n)
-            launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
-        if (l == 0) sweeps_fine(cur[0], p.nu0, s);
-        else pseudo(l, cur[l], p.m, false, s);
     }
     if (tail) {
         launch_apply<R>(d, strips[0].view(), ctl, APPLY_RESID, cur[0], part, 0, s, delta);
@@ -623,16 +652,39 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
     cur0 = cur[0];
 }
 
+namespace {
+
+// Fresh and repeated visits of each level in one cycle of the given shape.
+void count_visits(int L, int l, bool fresh, int shape, std::vector<long long>& fr,
+                  std::vector<long long>& rep)
+{
+    (fresh ? fr : rep)[l] += 1;
+    if (l == L - 1) return;
+    if (l + 1 == L - 1 || shape == M1_CYCLE_V) {
+        count_visits(L, l + 1, true, shape, fr, rep);
+    } else if (shape == M1_CYCLE_W) {
+        count_visits(L, l + 1, true, M1_CYCLE_W, fr, rep);
+        count_visits(L, l + 1, false, M1_CYCLE_W, fr, rep);
+    } else {
+        count_visits(L, l + 1, true, M1_CYCLE_F, fr, rep);
+        count_visits(L, l + 1, false, M1_CYCLE_V, fr, rep);
+    }
+}
+
+}  // namespace
+
 template <typename R>
 long long Engine<R>::kernels_per_cycle(const Params& p) const
 {
     if (L == 1) return p.nu0 + 2;
     // the correction form computes A(w) in the FAS right-hand side kernel (FP32)
     const int aw = (delta && !std::is_same<R, float>::value) ? 1 : 0;
-    long long k = p.nu0 + 2;                           // fine pre-smooth, residual, restrict
-    k += (long long)(L - 2) * (p.m + 3 + aw);          // FAS rhs, pseudo, residual, restrict
-    k += 1 + p.mc + aw;                                // coarsest
-    k += (long long)(L - 2) * (1 + p.m) + 1 + p.nu0;   // prolong + post-smooth
+    std::vector<long long> fr(L, 0), rep(L, 0);
+    count_visits(L, 0, true, p.cycle, fr, rep);
+    long long k = 2 * p.nu0 + 3;                       // fine smoothing, residual, restrict, prolong
+    for (int l = 1; l < L - 1; ++l)                    // pseudo x 2, residual, restrict, prolong
+        k += fr[l] * (1 + aw + 2 * p.m + 3) + rep[l] * (2 * p.m + 3);
+    k += fr[L - 1] * (1 + aw + p.mc);                  // coarsest
     return k + 2;                                      // final residual, finalize
 }
 
@@ -688,7 +740,7 @@ m1_status Engine<R>::step(const double* dts, const m1_solve_params& sp, m1_step_
     M1_TRY(validate_params(sp));
     for (int i = 0; i < cap; ++i)
         if (used[i] && !(dts[i] > 0)) return M1_ERR_INVALID_ARG;
-    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
+    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse, sp.cycle };
     M1_TRY(build_graph(p));
     M1_TRY(begin_step(dts, sp));
     M1_CK(cudaEventRecord(ev0, stream));
@@ -1202,7 +1254,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
         if (hi.used[i] && !(dts[i] > 0)) return M1_ERR_INVALID_ARG;
     for (int i = 0; i < lo.cap; ++i)
         if (lo.used[i]) M1_TRY(lo.set_dt(i, dts[i]));
-    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse };
+    Params p{ sp.nu0, sp.nu_l, sp.m_pseudo, sp.m_coarse, sp.cycle };
     M1_TRY(build_graph(p));
     M1_TRY(hi.begin_step(dts, sp));
     cudaStream_t s = hi.stream;
@@ -1332,6 +1384,7 @@ m1_status m1_default_params(m1_solve_params* p)
     p->tol = 1e-8; p->dtau_min = 1e-12; p->dtau_max = 1e6; p->theta_ex = 0.5; p->theta_c = 0.5;
     p->max_cycles = 20000;
     p->dtau_rule = M1_DTAU_ABS;
+    p->cycle = M1_CYCLE_V;
     return M1_OK;
 }
 

@@ -36,10 +36,10 @@ void set_error_text(const char* msg);
     } while (0)
 
 struct Params {
-    int nu0, nu_l, m, mc;
+    int nu0, nu_l, m, mc, cycle;
     bool operator==(const Params& o) const
     {
-        return nu0 == o.nu0 && nu_l == o.nu_l && m == o.m && mc == o.mc;
+        return nu0 == o.nu0 && nu_l == o.nu_l && m == o.m && mc == o.mc && cycle == o.cycle;
     }
 };
 
@@ -135,6 +135,8 @@ struct Engine {
     void fas_rhs(int l, cudaStream_t s);
     void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s);
     void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true);
+    void visit(const Params& p, int l, bool fresh, int shape, std::vector<int>& cur, cudaStream_t s);
+    void corrections(const Params& p, int l, int shape, std::vector<int>& cur, cudaStream_t s);
     long long kernels_per_cycle(const Params& p) const;
     m1_status build_graph(const Params& p);
     m1_status begin_step(const double* dts, const m1_solve_params& sp);

@@ -323,7 +323,7 @@ m1_status m1_server_create(size_t hbm_budget_bytes, int max_slots, int lmax, int
                 return M1_ERR_OOM;
         }
     }
-    s->structure = m1::Params{ p.nu0, p.nu_l, p.m_pseudo, p.m_coarse };
+    s->structure = m1::Params{ p.nu0, p.nu_l, p.m_pseudo, p.m_coarse, p.cycle };
     s->precision = precision;
     s->L = lmax;
     s->max_slots = max_slots;
@@ -349,7 +349,7 @@ m1_status m1_serve_submit(m1_server_t s, m1_grid_t g, int nsteps, double dt,
     if (params) r->params = *params; else m1_default_params(&r->params);
     M1_TRY(m1::validate_params(r->params));
     if (r->params.nu0 != s->structure.nu0 || r->params.m_pseudo != s->structure.m ||
-        r->params.m_coarse != s->structure.mc)
+        r->params.m_coarse != s->structure.mc || r->params.cycle != s->structure.cycle)
         return M1_ERR_INVALID_ARG;
     r->lane = (long long)d.nx * (d.dim == 2 ? d.ny : 1) <= s->small_cells ? 0 : 1;
     r->bytes = s->lanes[r->lane].model->sv_bytes(d);

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "NONADMISSIBLE_INP
 BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
 FP64, MIXED = 0, 1
 DTAU_ABS, DTAU_SIGNED = 0, 1
+CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
 SMALL_CELLS = 65536          # servers: requests of at most this many cells take the small lane
 OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 
@@ -67,7 +68,7 @@ class SolveParams(ctypes.Structure):
                 ("tol", ctypes.c_double), ("dtau_min", ctypes.c_double),
                 ("dtau_max", ctypes.c_double), ("theta_ex", ctypes.c_double),
                 ("theta_c", ctypes.c_double), ("max_cycles", ctypes.c_int),
-                ("dtau_rule", ctypes.c_int)]
+                ("dtau_rule", ctypes.c_int), ("cycle", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
