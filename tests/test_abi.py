@@ -118,6 +118,10 @@ def test_invalid_batches_servers_and_parameters_rejected(lib):
     p = m1.m1_default_params(dtau_rule=2)
     assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), 0, None,
                                     ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    p = m1.m1_default_params(cycle=3)                # V, W and F only
+    assert m1._lib.m1_server_create(1 << 20, 4, 3, 0, ctypes.byref(p), 0, None,
+                                    ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    assert m1.m1_default_params().cycle == m1.CYCLE_V
     t = ctypes.c_ulonglong()
     assert m1._lib.m1_serve_submit(None, None, 1, 0.1, None, ctypes.byref(t)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_serve_poll(None, 1, None, None) == m1.ERR_INVALID_ARG
