@@ -241,6 +241,75 @@ def bench_cycle_shapes(m1, case, stream, s0, flush):
     return out
 
 
+def bench_paper_beam(m1, stream, sizes=(256, 512), levels=(1, 2, 3, 4)):
+    """The paper's beam (Section 4.1, run in Section 5.1) in nondimensional form
+    at 2^k stand-ins for its 257^2 and 513^2 grids, CFL 2000, tolerance 1e-2:
+    V-cycles to tolerance, step time and time per cycle (normalised to L_max = 1,
+    as the paper's per-cycle cost table) for L_max = 1..4, and the largest E on
+    the horizontal cut at mid height against the beam's inflow E (the paper
+    compares that cut's maximum across solvers).  FP64, one untimed step then
+    one timed step per configuration."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    out = {}
+    for n in sizes:
+        rows = {}
+        for lmax in levels:
+            case = inputs.paper_beam_2d(n, lmax=lmax)
+            grid = m1.grid_from_case(case, stream=stream.cuda_stream)
+            params = m1.m1_default_params(tol=case["tol"])
+            state = [np.ascontiguousarray(case["state"][k]) for k in range(4)]
+            grid.implicit_step(case["dt"], params)
+            grid.set_state(*state)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = grid.implicit_step(case["dt"], params)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            E = grid.get_state()[0]
+            grid.close()
+            e_beam = case["inflow"][0, 0].max()
+            rows[f"L{lmax}"] = {"cycles": st.cycles, "ms_per_step": ms,
+                                "ms_per_cycle": ms / max(st.cycles, 1),
+                                "cut_max_over_beam_E": float(E[n // 2].max() / e_beam)}
+        base = rows[f"L{levels[0]}"]["ms_per_cycle"]
+        for r in rows.values():
+            r["cost_per_cycle_normalised"] = r["ms_per_cycle"] / base
+        out[f"{n}x{n}"] = rows
+    return out
+
+
+def bench_paper_riemann(m1, stream, n=256, steps=10, cfl=150.0, levels=(1, 2, 4)):
+    """The periodic 2D Riemann problem of Section 5.2 in nondimensional form: no
+    energy enters or leaves the box, so the relative change of the total
+    radiative energy after each step measures the solver's conservation at the
+    paper's residual 5e-3 (the paper: below 1e-12 with Jacobi, about 1e-8 with
+    the multigrid).  FP64; the largest relative error over the steps, the mean
+    cycles per step and the time per step for each L_max."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    out = {}
+    for lmax in levels:
+        case = inputs.riemann_2d(n, cfl=cfl, lmax=lmax, tol=5e-3)
+        grid = m1.grid_from_case(case, stream=stream.cuda_stream)
+        params = m1.m1_default_params(tol=case["tol"])
+        e0 = float(case["state"][0].sum())
+        worst, cycles = 0.0, []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            st = grid.implicit_step(case["dt"], params)
+            cycles.append(st.cycles)
+            worst = max(worst, abs(float(grid.get_state()[0].sum()) - e0) / e0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        grid.close()
+        out[f"L{lmax}"] = {"max_rel_energy_error": worst, "mean_cycles": float(np.mean(cycles)),
+                           "ms_per_step": a.elapsed_time(b) / steps}
+    return {"workload": f"riemann-2d-periodic-{n}x{n}-cfl{cfl:g}-tol5e-3-{steps}-steps", **out}
+
+
 def bench_batched(m1, count, stream):
     """Independent 2D instances of uneven sizes stepped together, mixed and FP64."""
     import torch
@@ -486,6 +555,8 @@ def main():
         extras["mixed"] = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps,
                                       pk["hbm_gbs"])
         extras["cycle_shapes"] = bench_cycle_shapes(m1, case, stream, s0, flush)
+        extras["paper_beam"] = bench_paper_beam(m1, stream)
+        extras["paper_riemann"] = bench_paper_riemann(m1, stream)
         extras["batched"] = bench_batched(m1, args.batch_count, stream)
         if args.serve_full:
             reqs = inputs.serving_stream(64)

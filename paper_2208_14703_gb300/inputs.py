@@ -132,6 +132,31 @@ def beam_channel_2d(n: int = 4096, cfl: float = 100.0, lmax: int = 10, tol: floa
                 lmax=lmax, tol=tol)
 
 
+def paper_beam_2d(n: int = 256, cfl: float = 2000.0, lmax: int = 4, tol: float = 1e-2) -> dict:
+    """The beam of Section 4.1 (run in Section 5.1) in nondimensional form.  The
+    domain is [-1, 1]^2 with n x n cells; there is no matter (sigma_a = sigma_s
+    = 0, the paper's setting); the background is at the radiative temperature
+    T_r = 300 K with F = 0, scaled to E = a_r T^4 = 1 (T = 1).  A beam at
+    T_r = 1000 K, E = (1000/300)^4, with reduced flux f = 1 at 45 degrees,
+    F = c E (1, 1)/sqrt(2), enters through the west wall at y in [-0.875, -0.75].
+    The rest of the west wall holds the background state; the other walls
+    copy their neighbour (zero-gradient outflow: the paper does not say).
+    dt = cfl * h / c with the paper's CFL 2000, so one implicit step reaches the
+    steady state; tol = 1e-2 relative residual (Section 5.1)."""
+    h = 2.0 / n
+    y = -1.0 + (np.arange(n) + 0.5) * h
+    beam = (y >= -0.875) & (y <= -0.75)
+    e_beam = (1000.0 / 300.0) ** 4
+    inflow = np.zeros((4, 3, n))
+    inflow[0, 0, :] = np.where(beam, e_beam, 1.0)
+    inflow[0, 1, :] = np.where(beam, e_beam / np.sqrt(2.0), 0.0)
+    inflow[0, 2, :] = np.where(beam, e_beam / np.sqrt(2.0), 0.0)
+    z = np.zeros((n, n))
+    return dict(desc=_desc(2, n, n, 2.0, 2.0, ["inflow", "neumann", "neumann", "neumann"]),
+                dt=cfl * h, state=_state(n, n, np.ones((n, n))), sa=z, ss=z.copy(),
+                inflow=inflow, lmax=lmax, tol=tol)
+
+
 def riemann_2d(n: int = 64, cfl: float = 2.0, lmax: int = 3, tol: float = 1e-10,
                sigma: float = 0.0) -> dict:
     """Section 5.2 Riemann problem in nondimensional form: [0,1]^2, four quadrants

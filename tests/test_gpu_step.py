@@ -189,3 +189,17 @@ def test_not_converged_keeps_last_admissible_iterate():
     out, st, _, _ = gpu_step(case, m1.m1_default_params(max_cycles=3), allow_nc=True)
     assert st.status == m1.ERR_NOT_CONVERGED and st.cycles == 3
     assert np.all(out[0] > 0) and np.all(np.hypot(out[1], out[2]) <= out[0] * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("lmax", [1, 2, 3, 4])
+def test_paper_beam_matches_oracle(lmax):
+    """The beam of Section 4.1 in nondimensional form (no matter, an f = 1 beam
+    at 45 degrees through the west wall, CFL 2000, tolerance 1e-2) at 64^2: the
+    same cycle count, residual history and damped cells as the oracle."""
+    case = inputs.paper_beam_2d(64, lmax=lmax)
+    ref, ost, ohist, _ = oracle_step(case, lmax, case["tol"])
+    assert ost["status"] == 0
+    out, st, hist, _ = gpu_step(case, m1.m1_default_params(tol=case["tol"]), lmax=lmax)
+    assert st.status == 0 and st.cycles == ost["cycles"] and st.damped == ost["damped"]
+    np.testing.assert_allclose(hist, ohist, rtol=1e-9, atol=1e-13 * ohist[0])
+    assert max(rel_l2(out, ref).values()) <= PARITY
