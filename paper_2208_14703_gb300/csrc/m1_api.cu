@@ -628,14 +628,29 @@ void Engine<R>::visit(const Params& p, int l, bool fresh, int shape, std::vector
 }
 
 // One cycle of Algorithm 4 (of the shape p.cycle) over every instance.  tail:
-// end with the fine residual norm and the stop test (the mixed-precision
-// driver does its own).
+// the stop test of the previous cycle at the start (the mixed-precision driver
+// does its own after the cycle).  The residual norm of the state a cycle
+// leaves is a by-product of the next cycle's first fine sweep, so the test of
+// cycle k runs in the graph launch of cycle k + 1: the step takes one launch
+// more than it has cycles, and no separate residual pass.
 template <typename R>
 void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail)
 {
     std::vector<int> cur(L, 0);
     cur[0] = cur0;
-    sweeps_fine(cur[0], p.nu0, s);
+    if (tail) {
+        // the first fine sweep also gives ||b - A(v)|| of the state the previous
+        // cycle left (its stop test and dtau update, taken here: if that cycle
+        // converged, the state stays in buffer `in` and the rest of this launch
+        // returns at once)
+        const int in = cur[0];
+        launch_sweep<R>(d, strips[0].view(), ctl, false, in, 1 - in, s, delta, ring[0] != 0, part);
+        cur[0] = 1 - in;
+        launch_finalize<R>(ctl, d, cap, part, nullptr, FIN_DEFER, in, bctl, s);
+        sweeps_fine(cur[0], p.nu0 - 1, s);
+    } else {
+        sweeps_fine(cur[0], p.nu0, s);
+    }
     if (L > 1) {
         launch_apply<R>(d, strips[0].view(), ctl, APPLY_RESID, cur[0], nullptr, 1, s, delta);
         if (chunks[1].n)
@@ -644,10 +659,6 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         if (chunks[0].n)
             launch_prolong<R>(d + cap, d, chunks[0].view(), ctl, cur[1], cur[0], s, delta);
         sweeps_fine(cur[0], p.nu0, s);
-    }
-    if (tail) {
-        launch_apply<R>(d, strips[0].view(), ctl, APPLY_RESID, cur[0], part, 0, s, delta);
-        launch_finalize<R>(ctl, d, cap, part, nullptr, FIN_CYCLE, cur[0], bctl, s);
     }
     cur0 = cur[0];
 }
@@ -676,7 +687,7 @@ void count_visits(int L, int l, bool fresh, int shape, std::vector<long long>& f
 template <typename R>
 long long Engine<R>::kernels_per_cycle(const Params& p) const
 {
-    if (L == 1) return p.nu0 + 2;
+    if (L == 1) return p.nu0;
     // the correction form computes A(w) in the FAS right-hand side kernel (FP32)
     const int aw = (delta && !std::is_same<R, float>::value) ? 1 : 0;
     std::vector<long long> fr(L, 0), rep(L, 0);
@@ -685,7 +696,7 @@ long long Engine<R>::kernels_per_cycle(const Params& p) const
     for (int l = 1; l < L - 1; ++l)                    // pseudo x 2, residual, restrict, prolong
         k += fr[l] * (1 + aw + 2 * p.m + 3) + rep[l] * (2 * p.m + 3);
     k += fr[L - 1] * (1 + aw + p.mc);                  // coarsest
-    return k + 2;                                      // final residual, finalize
+    return k;
 }
 
 template <typename R>
@@ -782,7 +793,7 @@ m1_status Engine<R>::step(const double* dts, const m1_solve_params& sp, m1_step_
             s.status = c.status;
             s.newton_fail = c.newton_fail;
             s.damped = c.damped;
-            s.launches = 4 + launched * kernels_per_cycle(p);
+            s.launches = 4 + launched * (kernels_per_cycle(p) + 1);   // + deferred finalize
         }
         ++k;
     }
@@ -1292,7 +1303,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
             o.status = c.status;
             o.newton_fail = c.newton_fail;
             o.damped = c.damped;
-            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 1);
+            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 3);   // accumulate, defect, finalize
         }
         ++k;
     }

@@ -79,6 +79,7 @@ struct Ctl {
     // state
     double res0, res, res_prev, bnorm, dtau;
     int kappa, done, status, result_buf;
+    int pending_r0;               // the next deferred norm is r_0 again (set by FIN_INIT)
     unsigned int newton_fail, damped;
     double* hist;                 // res_hist[kappa], length hist_len (device)
     double* dtau_hist;            // dtau used in cycle kappa, length hist_len

@@ -49,6 +49,13 @@ __device__ __forceinline__ R limited_step(const Cell4<R>& u, const Cell4<R>& f, 
     return fmin(dtau, theta * max_admissible_step(u, f, c));
 }
 
+// Sum of one double over the lanes of a warp in a fixed order (lane 0 holds it).
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
 {
     return ctls && (ctls[inst].done || !ctls[inst].active);
@@ -135,13 +142,19 @@ __device__ __forceinline__ Pseudo<R> pseudo_of(const Ctl* ctl)
 // solve of a Jacobi sweep (Algorithm 1) or of the fused pseudo-time step
 // (Eq. (30), Algorithm 3).  `u` is the cell's own iterate (the correction e in
 // the correction form) and `wb` its base state (correction form only).
-template <typename R, bool PSEUDO, bool DELTA>
+//
+// NORM (fine Jacobi sweep only): also add the cell's weighted squared residual
+// of the input state, r = b - A(u) = (b + N(u)) - D(u) (Eq. (13)), to *nrm: the
+// neighbour terms N are the sweep's own, D(u) the local part, written as the
+// residual kernel writes it.
+template <typename R, bool PSEUDO, bool DELTA, bool NORM = false>
 __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const Staged<R>& wv,
                                             const Staged<R>& ev, const Staged<R>& prev,
                                             const Staged<R>& next, const Staged<R>& cur,
                                             const Cell4<R>& b, const Sig2<R>& sg, size_t k,
                                             int out_buf, bool two_d, const Cell4<R>& u,
-                                            const Cell4<R>& wb, const Pseudo<R>& ps)
+                                            const Cell4<R>& wb, const Pseudo<R>& ps,
+                                            double* nrm = nullptr)
 {
     const R c = L.c, bx = L.bx, by = L.by;
     R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
@@ -153,6 +166,15 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
         NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
     }
     const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+    if constexpr (NORM && !PSEUDO && !DELTA) {
+        const R T2 = cur.T * cur.T;
+        const R src_e = ka * (cur.E - L.a_r * T2 * T2);
+        const Cell4<R> a = { L.diag * cur.E + src_e - NE, (L.diag + kt) * cur.Fx - NFx,
+                             (L.diag + kt) * cur.Fy - NFy, L.c_v * cur.T - src_e };
+        const Cell4<R> r = { b.E - a.E, b.Fx - a.Fx, b.Fy - a.Fy, b.T - a.T };
+        *nrm += (double)r.E * r.E + ((double)r.Fx * r.Fx + (double)r.Fy * r.Fy) * (double)L.ic2 +
+                (double)r.T * r.T;
+    }
     bool ok;
     Cell4<R> out;
     if (!PSEUDO) {
@@ -203,10 +225,11 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
 // is evaluated once per strip (32/30 x (sh + 2)/sh evaluations per updated
 // cell) with no shared-memory tile and no block barrier.  Lanes 1..30 update
 // their cell.  Ghost rows and columns follow the rules of `fetch`.
-template <typename R, bool PSEUDO, bool DELTA>
-__device__ __forceinline__ void strip_regs(const Level<R>& L, Ctl* ctl, int2 it, int lane,
-                                           const Cell4<R>* __restrict__ src, int out_buf)
+template <typename R, bool PSEUDO, bool DELTA, bool NORM = false>
+__device__ __forceinline__ double strip_regs(const Level<R>& L, Ctl* ctl, int2 it, int lane,
+                                             const Cell4<R>* __restrict__ src, int out_buf)
 {
+    double nrm = 0.0;
     const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
     const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
     const int i = min(x0 - 1 + lane, nx);       // lanes past the east ghost repeat it
@@ -242,12 +265,13 @@ __device__ __forceinline__ void strip_regs(const Level<R>& L, Ctl* ctl, int2 it,
                 if (!DELTA) { u = Cell4<R>{ cur.E, cur.Fx, cur.Fy, cur.T }; }
                 else { u = src[k]; wb = L.w[k]; }
             }
-            update_cell<R, PSEUDO, DELTA>(L, ctl, wv, ev, prev, next, cur, b, sg, k, out_buf,
-                                          two_d, u, wb, ps);
+            update_cell<R, PSEUDO, DELTA, NORM>(L, ctl, wv, ev, prev, next, cur, b, sg, k,
+                                                out_buf, two_d, u, wb, ps, &nrm);
         }
         prev = cur;
         cur = next;
     }
+    return nrm;
 }
 
 // Copy the per-warp Level descriptor of item `inst` into shared memory.
@@ -281,10 +305,13 @@ __device__ __forceinline__ bool enter_item(Level<R>& L, const Level<R>* src, con
 // Persistent sweep over every listed (instance, strip): one warp per item.
 // FP64 instances are held to 128 registers (8 blocks per SM): one register
 // more (the pseudo-time variant) cost 4% of the FP64 step on GB300.
-template <typename R, bool PSEUDO, bool DELTA = false>
+// NORM: the fine Jacobi sweep that also writes each strip's weighted residual
+// norm partial of its input state (the stop test of the cycle that left it).
+template <typename R, bool PSEUDO, bool DELTA = false, bool NORM = false>
 __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k_sweep(const Level<R>* __restrict__ lv,
                                                             WorkList wl, Ctl* __restrict__ ctls,
-                                                            int in_buf, int out_buf)
+                                                            int in_buf, int out_buf,
+                                                            double* __restrict__ partials)
 {
     __shared__ Level<R> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -294,7 +321,11 @@ __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k
         const int2 it = wl.items[w];
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-        strip_regs<R, PSEUDO, DELTA>(L, ctls + it.x, it, lane, src, out_buf);
+        const double nrm = strip_regs<R, PSEUDO, DELTA, NORM>(L, ctls + it.x, it, lane, src, out_buf);
+        if (NORM) {
+            const double sum = warp_sum(nrm);
+            if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
+        }
         __syncwarp();
     }
 }
@@ -449,13 +480,6 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep_ring32(const Level<f
     }
 }
 
-
-// Sum of one double over the lanes of a warp in a fixed order (lane 0 holds it).
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Neighbour operators L and R of Eq. (9) of a strip cell from its staged west /
 // east (shuffled) and south / north rows.
@@ -931,7 +955,15 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
     const int slot = slot_ids ? slot_ids[blockIdx.x] : (int)blockIdx.x;
     Ctl* ctl = ctls + slot;
     if (!ctl->active) return;
-    if (mode == FIN_CYCLE && ctl->done) return;
+    if (mode != FIN_INIT && ctl->done) return;
+    if (mode == FIN_DEFER) {
+        const int first = ctl->pending_r0;
+        __syncthreads();
+        if (first) {
+            if (threadIdx.x == 0) ctl->pending_r0 = 0;
+            return;
+        }
+    }
     const Level<R>* L = lv0 + slot;
     const int off = L->part_off, np = L->strips;
     const double s = block_reduce_fixed(part + off, np, red);
@@ -947,6 +979,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
         if (ctl->hist_len > 0) ctl->hist[0] = res;
         ctl->result_buf = cur;
         ctl->status = CTL_NOT_CONVERGED;
+        ctl->pending_r0 = 1;
         if (res <= ctl->res0_floor * ctl->bnorm) mark_done(ctl, bctl, CTL_OK);
         return;
     }
@@ -1139,9 +1172,13 @@ static inline int pgrid_warps(const WorkList& wl)
 
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
-                  int out_buf, cudaStream_t s, bool delta, bool ring)
+                  int out_buf, cudaStream_t s, bool delta, bool ring, double* partials)
 {
     const int g = pgrid_warps(wl), t = kStripWarps * 32;
+    if (partials && !pseudo && !delta) {
+        k_sweep<R, false, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, partials);
+        return;
+    }
     if constexpr (std::is_same<R, float>::value) {
         if (delta && ring) {
             if (pseudo) k_sweep_ring32<true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
@@ -1150,12 +1187,12 @@ void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int i
         }
     }
     if (delta) {
-        if (pseudo) k_sweep<R, true, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
-        else k_sweep<R, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+        if (pseudo) k_sweep<R, true, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, nullptr);
+        else k_sweep<R, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, nullptr);
         return;
     }
-    if (pseudo) k_sweep<R, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
-    else k_sweep<R, false><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf);
+    if (pseudo) k_sweep<R, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, nullptr);
+    else k_sweep<R, false><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, nullptr);
 }
 
 template <typename R>
@@ -1274,7 +1311,7 @@ void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, Work
 
 #define M1_INSTANTIATE(R)                                                                          \
     template void launch_sweep<R>(const Level<R>*, WorkList, Ctl*, bool, int, int, cudaStream_t,  \
-                                  bool, bool);                                                     \
+                                  bool, bool, double*);                                            \
     template void launch_apply<R>(const Level<R>*, WorkList, Ctl*, int, int, double*, int,        \
                                   cudaStream_t, bool);                                             \
     template void launch_norm_state<R>(const Level<R>*, WorkList, const Ctl*, double*,            \

@@ -7,11 +7,16 @@
 namespace m1 {
 
 enum ApplyMode { APPLY_RESID = 0, APPLY_FAS = 1, APPLY_A = 2 };
-enum FinMode { FIN_INIT = 0, FIN_CYCLE = 1 };
+// FIN_INIT: r_0 and ||b|| of a new step.  FIN_CYCLE: the residual after a
+// cycle, stop test and dtau.  FIN_DEFER: the same for the residual of the state
+// a cycle left, computed by the next cycle's first fine sweep (the first such
+// norm of a step is r_0 again and only clears the pending flag).
+enum FinMode { FIN_INIT = 0, FIN_CYCLE = 1, FIN_DEFER = 2 };
 
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
-                  int out_buf, cudaStream_t s, bool delta = false, bool ring = false);
+                  int out_buf, cudaStream_t s, bool delta = false, bool ring = false,
+                  double* partials = nullptr);
 template <typename R>
 void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int state_buf,
                   double* partials, int write_r, cudaStream_t s, bool delta = false);
