@@ -214,6 +214,30 @@ def bench_mixed(m1, case, stream, s0, flush, ref64, steps, hbm_peak):
                                     "kernel": "k_sweep<float, correction form>"}}
 
 
+def bench_fp32_sweep_large(m1, stream, flush, hbm_peak, n=4096):
+    """The FP32 correction-form sweep at the mixed-precision configuration's size
+    (the 4096^2 beam-in-a-channel grid): one fine sweep timed as in `sweep_ms`
+    (state reset on the device before each call), 72 algorithmic bytes per
+    cell against the measured HBM peak."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    case = inputs.beam_channel_2d(n)
+    grid = m1.grid_from_case(case, precision=m1.MIXED, stream=stream.cuda_stream)
+    s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).to("cuda") for k in range(4)]
+    torch.cuda.synchronize()
+    ms = sweep_ms(grid, case["dt"], stream, flush, lambda: grid.set_state(*s0, on_device=True))
+    grid.close()
+    cells = n * n
+    gbs = SWEEP32_BYTES * cells / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": gbs / hbm_peak, "kernel_ms": ms, "cells": cells, "bytes_per_cell": SWEEP32_BYTES,
+            "traffic": SWEEP32_TRAFFIC_PER_CELL * cells,
+            "traffic_source": "ncu DRAM bytes of the 2048^2 cp.async launch (307.1 MB), scaled "
+                              "by cells (both working sets exceed L2)",
+            "strip_rows": m1.strip_rows(1, n, n),
+            "kernel": "k_sweep FP32 correction form at the 4096^2 mixed configuration"}
+
+
 def bench_cycle_shapes(m1, case, stream, s0, flush):
     """Cycles to tolerance and step time of the same workload with V-, W- and
     F-cycles (Section 6.3 names W and F as the alternatives), FP64 and mixed:
@@ -554,6 +578,8 @@ def main():
         from paper_2208_14703_gb300 import inputs
         extras["mixed"] = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps,
                                       pk["hbm_gbs"])
+        extras["mixed"]["roofline_fp32_sweep_4096"] = bench_fp32_sweep_large(m1, stream, flush,
+                                                                             pk["hbm_gbs"])
         extras["cycle_shapes"] = bench_cycle_shapes(m1, case, stream, s0, flush)
         extras["paper_beam"] = bench_paper_beam(m1, stream)
         extras["paper_riemann"] = bench_paper_riemann(m1, stream)
@@ -581,7 +607,9 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "reset": "v^n restored on the device before every step (timed)",
                        "strip_rows": {f"{'fp64' if t['kind'] == 0 else 'fp32'}-{t['n']}": t["strip_rows"]
-                                      for t in tuning}},
+                                      for t in tuning},
+                       "fp32_cp_async_staging": sorted(t["n"] for t in tuning
+                                                       if t["kind"] == 1 and t["staging"] == 1)},
             "cycles_per_step": cycles, "fine_sweeps_per_step": sweeps,
             "steps_cells_per_s": cells * args.steps / (ms_max * 1e-3) * world,
             "wall_s": wall,

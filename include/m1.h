@@ -251,7 +251,8 @@ m1_status m1_server_destroy(m1_server_t s);
 /* ---- autotuning of the sweep kernels' strip shape ----
  * The Jacobi and pseudo-time sweeps (Algorithm 1, Algorithm 3) of a 2D level
  * give each warp a strip of 30 columns and `strip_rows` rows.  m1_autotune
- * times one sweep of a synthetic admissible n x n level (n = 16 .. 2048) for
+ * times one sweep of a synthetic admissible n x n level (n = 16 .. 2048; the
+ * FP32 correction form also 4096) for
  * strip heights 1, 2, 4, 8, 12, 16, 24, 32, for FP64 (kind 0) and for the FP32
  * correction form of the mixed path (kind 1, also both row stagings), and keeps
  * the fastest shape per size class (grids of about the same cell count) in a

@@ -5,7 +5,8 @@
 // ((sh + 2) / sh) but leave fewer strips, hence fewer warps, per level; the
 // best height depends on the level size, the precision and the GPU.  The tuner
 // times one sweep of a synthetic admissible 2D level for every candidate height
-// and size class and keeps the fastest; for the FP32 correction form it also
+// and size class (n = 16 .. 2048; the FP32 form up to 4096) and keeps the
+// fastest; for the FP32 correction form it also
 // chooses how strip rows are staged (loads into registers one row ahead, or
 // asynchronous copies into a shared-memory ring three rows ahead).  Levels
 // created afterwards take both from the table (before any tuning: ny / 64
@@ -149,8 +150,10 @@ m1_status m1_autotune(void* cuda_stream, m1_tune_entry* out, int max_entries, in
     if (max_entries < 0 || (max_entries > 0 && !out)) return M1_ERR_INVALID_ARG;
     const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     std::vector<m1_tune_entry> found;
+    // FP64 up to 2048^2 (the FP64 workloads); the FP32 correction form also at
+    // 4096^2, the mixed-precision configuration
     for (int kind = 0; kind < 2; ++kind)
-        for (int lg = 4; lg <= 11; ++lg) {
+        for (int lg = 4; lg <= (kind == 0 ? 11 : 12); ++lg) {
             const int n = 1 << lg;
             std::vector<double> ms;
             m1_status st = kind == 0 ? m1::time_level<double>(n, false, s, ms)
