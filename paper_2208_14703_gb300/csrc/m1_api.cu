@@ -549,15 +549,19 @@ void Engine<R>::sweeps_fine(int& cur, int count, cudaStream_t s)
 
 // m pseudo-time steps (nu_l = 1 Jacobi sweep each) at level l; from_v: the
 // first step starts from v_l (initial guess u_l = v_l, Algorithm 4).
+// fas: the first step also forms the FAS right-hand side (plain form; the
+// caller then launches no separate FAS kernel).
 template <typename R>
-void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s)
+void Engine<R>::pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s, bool fas)
 {
     Level<R>* dl = d + (size_t)l * cap;
     const bool go = strips[l].n > 0;          // an empty level only advances the buffer
     const bool rg = ring[l] != 0;
     for (int k = 0; k < m; ++k) {
         if (k == 0 && from_v) {
-            if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta, rg);
+            if (go)
+                launch_sweep<R>(dl, strips[l].view(), ctl, true, -1, 0, s, delta, rg, nullptr,
+                                fas && !delta);
             cur = 0;
         } else {
             if (go) launch_sweep<R>(dl, strips[l].view(), ctl, true, cur, 1 - cur, s, delta, rg);
@@ -611,12 +615,15 @@ void Engine<R>::visit(const Params& p, int l, bool fresh, int shape, std::vector
                       cudaStream_t s)
 {
     Level<R>* dl = d + (size_t)l * cap;
-    if (fresh) fas_rhs(l, s);
+    // a fresh visit needs the FAS right-hand side first: the plain form forms
+    // it inside the first pseudo-time step, the correction form in its own pass
+    // (with A(w))
+    if (fresh && delta) fas_rhs(l, s);
     if (l == L - 1) {
-        pseudo(l, cur[l], p.mc, fresh, s);
+        pseudo(l, cur[l], p.mc, fresh, s, fresh);
         return;
     }
-    pseudo(l, cur[l], p.m, fresh, s);
+    pseudo(l, cur[l], p.m, fresh, s, fresh);
     if (strips[l].n)
         launch_apply<R>(dl, strips[l].view(), ctl, APPLY_RESID, cur[l], nullptr, 1, s, delta);
     if (chunks[l + 1].n)
@@ -688,14 +695,15 @@ template <typename R>
 long long Engine<R>::kernels_per_cycle(const Params& p) const
 {
     if (L == 1) return p.nu0;
-    // the correction form computes A(w) in the FAS right-hand side kernel (FP32)
-    const int aw = (delta && !std::is_same<R, float>::value) ? 1 : 0;
+    // a fresh visit's FAS right-hand side: fused into the first pseudo-time step
+    // in the plain form, its own kernel in the correction form
+    const int aw = delta ? 1 : 0;
     std::vector<long long> fr(L, 0), rep(L, 0);
     count_visits(L, 0, true, p.cycle, fr, rep);
     long long k = 2 * p.nu0 + 3;                       // fine smoothing, residual, restrict, prolong
     for (int l = 1; l < L - 1; ++l)                    // pseudo x 2, residual, restrict, prolong
-        k += fr[l] * (1 + aw + 2 * p.m + 3) + rep[l] * (2 * p.m + 3);
-    k += fr[L - 1] * (1 + aw + p.mc);                  // coarsest
+        k += fr[l] * (aw + 2 * p.m + 3) + rep[l] * (2 * p.m + 3);
+    k += fr[L - 1] * (aw + p.mc);                      // coarsest
     return k;
 }
 

@@ -133,7 +133,7 @@ struct Engine {
     m1_status get_state(int i, double* E, double* Fx, double* Fy, double* T, int dev);
     void sweeps_fine(int& cur, int count, cudaStream_t s);
     void fas_rhs(int l, cudaStream_t s);
-    void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s);
+    void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s, bool fas = false);
     void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true);
     void visit(const Params& p, int l, bool fresh, int shape, std::vector<int>& cur, cudaStream_t s);
     void corrections(const Params& p, int l, int shape, std::vector<int>& cur, cudaStream_t s);

@@ -147,15 +147,22 @@ __device__ __forceinline__ Pseudo<R> pseudo_of(const Ctl* ctl)
 // of the input state, r = b - A(u) = (b + N(u)) - D(u) (Eq. (13)), to *nrm: the
 // neighbour terms N are the sweep's own, D(u) the local part, written as the
 // residual kernel writes it.
-template <typename R, bool PSEUDO, bool DELTA, bool NORM = false>
+//
+// FAS (first pseudo-time step of a fresh coarse visit, plain form): the input is
+// the restricted iterate v and `b_in` holds the restricted residual r; the
+// step first forms the FAS right-hand side f = A(v) + r (Eq. (24)) from its own
+// neighbour terms, as the FAS kernel writes it, stores it for the later steps
+// and uses it.
+template <typename R, bool PSEUDO, bool DELTA, bool NORM = false, bool FAS = false>
 __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const Staged<R>& wv,
                                             const Staged<R>& ev, const Staged<R>& prev,
                                             const Staged<R>& next, const Staged<R>& cur,
-                                            const Cell4<R>& b, const Sig2<R>& sg, size_t k,
+                                            const Cell4<R>& b_in, const Sig2<R>& sg, size_t k,
                                             int out_buf, bool two_d, const Cell4<R>& u,
                                             const Cell4<R>& wb, const Pseudo<R>& ps,
                                             double* nrm = nullptr)
 {
+    Cell4<R> b = b_in;
     const R c = L.c, bx = L.bx, by = L.by;
     R NE = bx * (c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
     R NFx = c * bx * ((wv.Fx + ev.Fx) + c * (wv.Pxx - ev.Pxx));
@@ -166,6 +173,14 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
         NFy += c * by * ((prev.Fy + next.Fy) + c * (prev.Pyy - next.Pyy));
     }
     const R ka = L.cdt * sg.sa, kt = L.cdt * (sg.sa + sg.ss);
+    if constexpr (FAS && PSEUDO && !DELTA) {
+        const R T2 = cur.T * cur.T;
+        const R src_e = ka * (cur.E - L.a_r * T2 * T2);
+        const Cell4<R> a = { L.diag * cur.E + src_e - NE, (L.diag + kt) * cur.Fx - NFx,
+                             (L.diag + kt) * cur.Fy - NFy, L.c_v * cur.T - src_e };
+        b = Cell4<R>{ a.E + b_in.E, a.Fx + b_in.Fx, a.Fy + b_in.Fy, a.T + b_in.T };
+        L.f[k] = b;
+    }
     if constexpr (NORM && !PSEUDO && !DELTA) {
         const R T2 = cur.T * cur.T;
         const R src_e = ka * (cur.E - L.a_r * T2 * T2);
@@ -225,10 +240,12 @@ __device__ __forceinline__ void update_cell(const Level<R>& L, Ctl* ctl, const S
 // is evaluated once per strip (32/30 x (sh + 2)/sh evaluations per updated
 // cell) with no shared-memory tile and no block barrier.  Lanes 1..30 update
 // their cell.  Ghost rows and columns follow the rules of `fetch`.
-template <typename R, bool PSEUDO, bool DELTA, bool NORM = false>
+template <typename R, bool PSEUDO, bool DELTA, bool NORM = false, bool FAS = false>
 __device__ __forceinline__ double strip_regs(const Level<R>& L, Ctl* ctl, int2 it, int lane,
                                              const Cell4<R>* __restrict__ src, int out_buf)
 {
+    // the cell's right-hand side (FAS: the restricted residual)
+    auto rhs = [&](size_t q) { return FAS ? L.r[q] : L.f[q]; };
     double nrm = 0.0;
     const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
     const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
@@ -247,7 +264,7 @@ __device__ __forceinline__ double strip_regs(const Level<R>& L, Ctl* ctl, int2 i
     size_t k = (size_t)y0 * nx + i;
     Cell4<R> bn{};
     Sig2<R> sn{};
-    if (own) { bn = L.f[k]; sn = L.sig[k]; }
+    if (own) { bn = rhs(k); sn = L.sig[k]; }
     for (int r = 0; r < rows; ++r, k += nx) {
         const int j = y0 + r;
         if (two_d) {
@@ -256,7 +273,7 @@ __device__ __forceinline__ double strip_regs(const Level<R>& L, Ctl* ctl, int2 i
         }
         const Cell4<R> b = bn;
         const Sig2<R> sg = sn;
-        if (own && r + 1 < rows) { bn = L.f[k + nx]; sn = L.sig[k + nx]; }
+        if (own && r + 1 < rows) { bn = rhs(k + nx); sn = L.sig[k + nx]; }
         const Staged<R> wv = shfl_staged(cur, (lane + 31) & 31);
         const Staged<R> ev = shfl_staged(cur, (lane + 1) & 31);
         if (own) {
@@ -265,8 +282,8 @@ __device__ __forceinline__ double strip_regs(const Level<R>& L, Ctl* ctl, int2 i
                 if (!DELTA) { u = Cell4<R>{ cur.E, cur.Fx, cur.Fy, cur.T }; }
                 else { u = src[k]; wb = L.w[k]; }
             }
-            update_cell<R, PSEUDO, DELTA, NORM>(L, ctl, wv, ev, prev, next, cur, b, sg, k,
-                                                out_buf, two_d, u, wb, ps, &nrm);
+            update_cell<R, PSEUDO, DELTA, NORM, FAS>(L, ctl, wv, ev, prev, next, cur, b, sg, k,
+                                                     out_buf, two_d, u, wb, ps, &nrm);
         }
         prev = cur;
         cur = next;
@@ -307,7 +324,9 @@ __device__ __forceinline__ bool enter_item(Level<R>& L, const Level<R>* src, con
 // more (the pseudo-time variant) cost 4% of the FP64 step on GB300.
 // NORM: the fine Jacobi sweep that also writes each strip's weighted residual
 // norm partial of its input state (the stop test of the cycle that left it).
-template <typename R, bool PSEUDO, bool DELTA = false, bool NORM = false>
+// FAS: the first pseudo-time step of a fresh coarse visit, which also forms the
+// FAS right-hand side.
+template <typename R, bool PSEUDO, bool DELTA = false, bool NORM = false, bool FAS = false>
 __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k_sweep(const Level<R>* __restrict__ lv,
                                                             WorkList wl, Ctl* __restrict__ ctls,
                                                             int in_buf, int out_buf,
@@ -321,7 +340,8 @@ __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k
         const int2 it = wl.items[w];
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
-        const double nrm = strip_regs<R, PSEUDO, DELTA, NORM>(L, ctls + it.x, it, lane, src, out_buf);
+        const double nrm =
+            strip_regs<R, PSEUDO, DELTA, NORM, FAS>(L, ctls + it.x, it, lane, src, out_buf);
         if (NORM) {
             const double sum = warp_sum(nrm);
             if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
@@ -1172,9 +1192,13 @@ static inline int pgrid_warps(const WorkList& wl)
 
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
-                  int out_buf, cudaStream_t s, bool delta, bool ring, double* partials)
+                  int out_buf, cudaStream_t s, bool delta, bool ring, double* partials, bool fas)
 {
     const int g = pgrid_warps(wl), t = kStripWarps * 32;
+    if (fas && pseudo && !delta) {
+        k_sweep<R, true, false, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, nullptr);
+        return;
+    }
     if (partials && !pseudo && !delta) {
         k_sweep<R, false, false, true><<<g, t, 0, s>>>(lv, wl, ctls, in_buf, out_buf, partials);
         return;
@@ -1311,7 +1335,7 @@ void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, Work
 
 #define M1_INSTANTIATE(R)                                                                          \
     template void launch_sweep<R>(const Level<R>*, WorkList, Ctl*, bool, int, int, cudaStream_t,  \
-                                  bool, bool, double*);                                            \
+                                  bool, bool, double*, bool);                                      \
     template void launch_apply<R>(const Level<R>*, WorkList, Ctl*, int, int, double*, int,        \
                                   cudaStream_t, bool);                                             \
     template void launch_norm_state<R>(const Level<R>*, WorkList, const Ctl*, double*,            \

@@ -16,7 +16,7 @@ enum FinMode { FIN_INIT = 0, FIN_CYCLE = 1, FIN_DEFER = 2 };
 template <typename R>
 void launch_sweep(const Level<R>* lv, WorkList wl, Ctl* ctls, bool pseudo, int in_buf,
                   int out_buf, cudaStream_t s, bool delta = false, bool ring = false,
-                  double* partials = nullptr);
+                  double* partials = nullptr, bool fas = false);
 template <typename R>
 void launch_apply(const Level<R>* lv, WorkList wl, Ctl* ctls, int mode, int state_buf,
                   double* partials, int write_r, cudaStream_t s, bool delta = false);
