@@ -271,8 +271,9 @@ def bench_paper_beam(m1, stream, sizes=(256, 512), levels=(1, 2, 3, 4)):
     V-cycles to tolerance, step time and time per cycle (normalised to L_max = 1,
     as the paper's per-cycle cost table) for L_max = 1..4, and the largest E on
     the horizontal cut at mid height against the beam's inflow E (the paper
-    compares that cut's maximum across solvers).  FP64, one untimed step then
-    one timed step per configuration."""
+    compares that cut's maximum across solvers), and the W- and F-cycles at the
+    deepest hierarchy.  FP64, one untimed step then one timed step per
+    configuration."""
     import torch
     from paper_2208_14703_gb300 import inputs
     out = {}
@@ -300,6 +301,23 @@ def bench_paper_beam(m1, stream, sizes=(256, 512), levels=(1, 2, 3, 4)):
         base = rows[f"L{levels[0]}"]["ms_per_cycle"]
         for r in rows.values():
             r["cost_per_cycle_normalised"] = r["ms_per_cycle"] / base
+        # the W- and F-cycle at the deepest hierarchy (the coarse correction is
+        # the bottleneck here, unlike the diffusive hot square)
+        case = inputs.paper_beam_2d(n, lmax=levels[-1])
+        grid = m1.grid_from_case(case, stream=stream.cuda_stream)
+        state = [np.ascontiguousarray(case["state"][k]) for k in range(4)]
+        for name, shape in (("W", m1.CYCLE_W), ("F", m1.CYCLE_F)):
+            params = m1.m1_default_params(tol=case["tol"], cycle=shape)
+            grid.set_state(*state)
+            grid.implicit_step(case["dt"], params)
+            grid.set_state(*state)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = grid.implicit_step(case["dt"], params)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rows[f"L{levels[-1]}_{name}"] = {"cycles": st.cycles, "ms_per_step": a.elapsed_time(b)}
+        grid.close()
         out[f"{n}x{n}"] = rows
     return out
 
