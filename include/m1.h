@@ -302,6 +302,36 @@ m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt,
                       const double* state, const double* rhs, int mode, double dtau, double theta,
                       double* out, double* norm);
 
+/* ---- 3D single-level operators (the first GPU step of a 3D path) ----
+ * A 3D grid of nx x ny x nz cells on [0,lx] x [0,ly] x [0,lz]; walls bc[6] =
+ * (x low, x high, y low, y high, z low, z high), each periodic, reflecting or
+ * Neumann (no inflow walls in 3D).  States are planar [5][nz*ny*nx] doubles
+ * (E, Fx, Fy, Fz, T; index (k*ny + j)*nx + i), opacities [2][nz*ny*nx]
+ * (sigma_a, sigma_s).  The operator is the 2D one on three axes: the Rusanov
+ * faces of Eq. (6) with the 3x3 closure of Eq. (5), transport diagonal
+ * 1 + c dt (1/hx + 1/hy + 1/hz), the same sources and local E-T solve.
+ *   M1_OP3_APPLY     out = A(state)
+ *   M1_OP3_RESIDUAL  out = rhs - A(state)
+ *   M1_OP3_JACOBI    out = `sweeps` Jacobi sweeps of A(u) = rhs from u = state
+ *                    (Algorithm 1)
+ * on_device = 0: host arrays (copied in and out; the call returns when done);
+ * 1: device arrays, stream-ordered on cuda_stream (the call still waits for its
+ * own work).  Each call allocates its own device buffers.  ms (may be NULL):
+ * device time of the operator passes alone (closure + operator per sweep).
+ * INVALID_ARG: a size < 1 or above 2^31 cells, a non-positive length, dt or
+ * constant, an inflow or unknown wall, an unknown mode, sweeps < 1 for JACOBI,
+ * a NULL array the mode needs.  The state must be admissible. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+    m1_bc bc[6];
+    double c, a_r, c_v;
+} m1_grid3_desc;
+enum { M1_OP3_APPLY = 0, M1_OP3_RESIDUAL = 1, M1_OP3_JACOBI = 2 };
+m1_status m1_op_level3(const m1_grid3_desc* desc, double dt, const double* sig,
+                       const double* state, const double* rhs, int mode, int sweeps,
+                       double* out, int on_device, void* cuda_stream, double* ms);
+
 /* Full weighting (Section 4.2, Eq. (21)/(22)) of a fine state (STATE ghosts) and
  * a fine residual (DIFF ghosts: zero at inflow walls) to the coarse grid
  * (nx/2 x ny/2; ny stays 1 in 1D).  Outputs are planar [4][coarse cells]. */

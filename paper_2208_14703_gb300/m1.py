@@ -30,6 +30,7 @@ BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
 FP64, MIXED = 0, 1
 DTAU_ABS, DTAU_SIGNED = 0, 1
 CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
+OP3_APPLY, OP3_RESIDUAL, OP3_JACOBI = 0, 1, 2
 SMALL_CELLS = 65536          # servers: requests of at most this many cells take the small lane
 OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
 
@@ -40,7 +41,7 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
            "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
            "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy", "m1_autotune",
-           "m1_set_tuning", "m1_strip_rows"]
+           "m1_set_tuning", "m1_strip_rows", "m1_op_level3"]
 
 
 class M1Error(RuntimeError):
@@ -433,6 +434,45 @@ def m1_op_level(desc, dt, sig, state, rhs=None, mode=OP_APPLY, dtau=0.0, theta=0
                           mode, dtau, theta, _ptr(out), ctypes.byref(nrm))
     _check(st, "m1_op_level")
     return out.reshape(4, desc.ny, desc.nx), nrm.value
+
+
+class GridDesc3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("bc", ctypes.c_int * 6), ("c", ctypes.c_double), ("a_r", ctypes.c_double),
+                ("c_v", ctypes.c_double)]
+
+
+def make_desc3(nx, ny, nz, lx, ly, lz, bc=("periodic",) * 6, c=1.0, a_r=1.0, c_v=1.0):
+    d = GridDesc3()
+    d.nx, d.ny, d.nz, d.lx, d.ly, d.lz = nx, ny, nz, lx, ly, lz
+    for k, b in enumerate(bc):
+        d.bc[k] = BC[b]
+    d.c, d.a_r, d.c_v = c, a_r, c_v
+    return d
+
+
+_lib.m1_op_level3.argtypes = [ctypes.POINTER(GridDesc3), ctypes.c_double, _vp, _vp, _vp,
+                              ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _dp]
+
+
+def m1_op_level3(desc, dt, sig, state, rhs=None, mode=OP3_APPLY, sweeps=1, out=None,
+                 on_device=False, stream=None):
+    """3D single-level operators on planar [5][nz, ny, nx] states (host numpy
+    arrays, or device tensors with on_device=True).  Returns (out, ms)."""
+    n = desc.nx * desc.ny * desc.nz
+    if not on_device:
+        state = _host(state).reshape(5, n)
+        sig = _host(sig).reshape(2, n)
+        rhs = None if rhs is None else _host(rhs).reshape(5, n)
+        out = np.zeros((5, n))
+    ms = ctypes.c_double()
+    st = _lib.m1_op_level3(ctypes.byref(desc), dt, _ptr(sig), _ptr(state), _ptr(rhs), mode, sweeps,
+                           _ptr(out), int(on_device), stream, ctypes.byref(ms))
+    _check(st, "m1_op_level3")
+    if not on_device:
+        out = out.reshape(5, desc.nz, desc.ny, desc.nx)
+    return out, ms.value
 
 
 def m1_op_restrict(desc, state, resid, inflow=None):

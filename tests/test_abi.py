@@ -128,3 +128,25 @@ def test_invalid_batches_servers_and_parameters_rejected(lib):
     assert m1._lib.m1_serve_wait(None, 1, 1.0) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_server_destroy(None) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_implicit_step(None, 0.1, None, None) == m1.ERR_INVALID_ARG
+
+
+def test_invalid_3d_operator_arguments_rejected(lib):
+    """The 3D single-level entry point validates before any device work."""
+    from paper_2208_14703_gb300 import m1
+    import numpy as np
+    ok = m1.make_desc3(4, 4, 4, 1.0, 1.0, 1.0)
+    s = np.zeros(5 * 64)
+    sig = np.zeros(2 * 64)
+    ms = ctypes.c_double()
+    bad = [m1.make_desc3(0, 4, 4, 1.0, 1.0, 1.0), m1.make_desc3(4, 4, 4, 1.0, 0.0, 1.0),
+           m1.make_desc3(4, 4, 4, 1.0, 1.0, 1.0, bc=("inflow",) + ("periodic",) * 5)]
+    for d in bad:
+        assert m1._lib.m1_op_level3(ctypes.byref(d), 0.1, sig.ctypes.data, s.ctypes.data, None,
+                                    m1.OP3_APPLY, 1, s.ctypes.data, 0, None,
+                                    ctypes.byref(ms)) == m1.ERR_INVALID_ARG
+    for mode, rhs, sweeps, dt in ((7, None, 1, 0.1), (m1.OP3_RESIDUAL, None, 1, 0.1),
+                                  (m1.OP3_JACOBI, s.ctypes.data, 0, 0.1),
+                                  (m1.OP3_APPLY, None, 1, 0.0)):
+        assert m1._lib.m1_op_level3(ctypes.byref(ok), dt, sig.ctypes.data, s.ctypes.data, rhs,
+                                    mode, sweeps, s.ctypes.data, 0, None,
+                                    ctypes.byref(ms)) == m1.ERR_INVALID_ARG
