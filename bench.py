@@ -241,10 +241,13 @@ def bench_fp32_sweep_large(m1, stream, flush, hbm_peak, n=4096):
 # FP64 work of one 3D Jacobi update, counted as SWEEP_OPS is: the closure pass
 # (reciprocal 4, F/E 3, 4 - 3 f^2 and its clamp 5, square root 6, E (s - 1)/3 2,
 # 3/(c^2 (2 + s)) 6, q F/E 3, the six tensor entries 6) and the operator pass
-# (six face neighbours of 13 each, opacity products 3, right-hand sides 4,
-# local solve 43: one reciprocal for both denominators 9, flux 3, quartic setup
-# and conversions 8, one Halley step 18, E 5).
-SWEEP3D_OPS = 35 + 6 * 13 + 3 + 4 + 43
+# (six face neighbours of 9 each: the energy term c E + s F_d scaled and summed
+# in 3, each flux component's F_a + s c P_da scaled and summed in 2; opacity
+# products 3, right-hand sides 4, local solve 43: one reciprocal for both
+# denominators 9, flux 3, quartic setup and conversions 8, one Halley step 18,
+# E 5).  ncu counts about 35 + 116 issued FP64 operations per cell for the two
+# passes at 128^3.
+SWEEP3D_OPS = 35 + 6 * 9 + 3 + 4 + 43
 
 
 def bench_sweep3d(m1, stream, n=256, sweeps=2):
