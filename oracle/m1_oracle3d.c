@@ -13,19 +13,24 @@
  * larger gain in 3D.  This file extends the 2D reading axis by axis: the Rusanov
  * face flux of Eq. (6) on all three axes, the 3x3 pressure tensor of Eq. (5), the
  * tensor-product transfers of Eqs. (14)/(21) on three axes.  Walls are periodic,
- * reflecting (mirror, wall-normal flux negated) or Neumann (copy); inflow walls
- * are not part of this oracle.  Every other reading (sources, local solve,
- * pseudo-time smoother, damping, norm, dtau control, levels) is the one of the 2D
- * oracle, marked [READING] or [EXT] where it applies.
+ * reflecting (mirror, wall-normal flux negated), Neumann (copy) or inflow (the
+ * prescribed E, F of the wall's face profile, T copied; differences see zero
+ * there), as in 2D; coarse face profiles are the 1D full-weighting rule of the
+ * 2D oracle applied along both tangential axes.  Every other reading (sources,
+ * local solve, pseudo-time smoother, damping, norm, dtau control, levels) is the
+ * one of the 2D oracle, marked [READING] or [EXT] where it applies.
  *
  * Data layout: a state is 5 planes [E | Fx | Fy | Fz | T], each nz*ny*nx doubles,
- * index (k*ny + j)*nx + i.
+ * index (k*ny + j)*nx + i.  Inflow profiles: [6 walls][E, Fx, Fy, Fz][F] with
+ * F = the largest face (max of ny*nz, nx*nz, nx*ny); the face of a wall on axis d
+ * is indexed q_b * n_a + q_a over its two other axes a < b.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NEUMANN = 2 };
+enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NEUMANN = 2, BC_INFLOW = 3 };
+enum { KIND_STATE = 0, KIND_DIFF = 1 };
 /* walls: 0 W (x low), 1 E (x high), 2 S (y low), 3 N (y high), 4 B (z low), 5 T (z high) */
 
 #define NF 5                       /* fields per cell */
@@ -36,6 +41,8 @@ typedef struct {
     double h[3];                   /* hx, hy, hz */
     double c, a_r, c_v;
     int bc[6];
+    const double* in[6];           /* inflow face profile of each wall (4 fields), or NULL */
+    size_t fstride;                /* doubles per field of a profile: the largest face */
 } grid3_t;
 
 typedef struct { double E, F[3], T; } cell5_t;
@@ -50,12 +57,34 @@ static size_t idx(const grid3_t* g, int i, int j, int k)
     return ((size_t)k * g->n[1] + j) * g->n[0] + i;
 }
 
-static void grid_from_desc(grid3_t* g, const int* idesc, const double* ddesc)
+static size_t face_max(const int n[3])
+{
+    size_t a = (size_t)n[1] * n[2], b = (size_t)n[0] * n[2], c = (size_t)n[0] * n[1];
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+static void set_inflow(grid3_t* g, const double* inflow)
+{
+    g->fstride = face_max(g->n);
+    for (int w = 0; w < 6; ++w)
+        g->in[w] = (inflow && g->bc[w] == BC_INFLOW) ? inflow + (size_t)w * 4 * g->fstride : NULL;
+}
+
+static void grid_from_desc(grid3_t* g, const int* idesc, const double* ddesc, const double* inflow)
 {
     /* idesc = { nx, ny, nz, bc[6] }; ddesc = { hx, hy, hz, c, a_r, c_v } */
     for (int a = 0; a < 3; ++a) { g->n[a] = idesc[a]; g->h[a] = ddesc[a]; }
     for (int w = 0; w < 6; ++w) g->bc[w] = idesc[3 + w];
     g->c = ddesc[3]; g->a_r = ddesc[4]; g->c_v = ddesc[5];
+    set_inflow(g, inflow);
+}
+
+/* The two axes tangential to a wall on axis d, in increasing order. */
+static void tangential(int d, int* a, int* b)
+{
+    *a = d == 0 ? 1 : 0;
+    *b = d == 2 ? 1 : 2;
 }
 
 static cell5_t load(const grid3_t* g, const double* v, int i, int j, int k)
@@ -91,9 +120,11 @@ void ora3_closure(double E, const double* F, double c, double* P)
 
 /* ------------------------------------------------------------------------ */
 /* Ghost cells, one layer per wall [READING]: periodic wrap, reflecting = mirror
- * cell with the wall-normal flux component negated, Neumann = copy.  Corners and
- * edges resolve one axis after the other. */
-static cell5_t get_cell(const grid3_t* g, const double* v, int p[3])
+ * cell with the wall-normal flux component negated, Neumann = copy, inflow = the
+ * prescribed E, F of the face profile at the (clamped) tangential position with
+ * T copied from the mirror cell; differences (kind DIFF) see zero at an inflow
+ * wall.  Corners and edges resolve one axis after the other. */
+static cell5_t get_cell(const grid3_t* g, const double* v, int p[3], int kind)
 {
     for (int a = 0; a < 3; ++a) {
         if (p[a] >= 0 && p[a] < g->n[a]) continue;
@@ -101,11 +132,24 @@ static cell5_t get_cell(const grid3_t* g, const double* v, int p[3])
         int q[3] = { p[0], p[1], p[2] };
         if (g->bc[wall] == BC_PERIODIC) {
             q[a] = p[a] < 0 ? p[a] + g->n[a] : p[a] - g->n[a];
-            return get_cell(g, v, q);
+            return get_cell(g, v, q, kind);
         }
         q[a] = p[a] < 0 ? -1 - p[a] : 2 * g->n[a] - 1 - p[a];
-        cell5_t m = get_cell(g, v, q);
-        if (g->bc[wall] == BC_REFLECT) m.F[a] = -m.F[a];
+        cell5_t m = get_cell(g, v, q, kind);
+        if (g->bc[wall] == BC_REFLECT) { m.F[a] = -m.F[a]; return m; }
+        if (g->bc[wall] == BC_NEUMANN) return m;
+        if (kind == KIND_DIFF) {
+            m.E = m.F[0] = m.F[1] = m.F[2] = m.T = 0.0;
+            return m;
+        }
+        int ta, tb;
+        tangential(a, &ta, &tb);
+        int ia = p[ta] < 0 ? 0 : (p[ta] >= g->n[ta] ? g->n[ta] - 1 : p[ta]);
+        int ib = p[tb] < 0 ? 0 : (p[tb] >= g->n[tb] ? g->n[tb] - 1 : p[tb]);
+        size_t f = (size_t)ib * g->n[ta] + ia;
+        const double* prof = g->in[wall];
+        m.E = prof[f];
+        for (int c = 0; c < 3; ++c) m.F[c] = prof[(size_t)(1 + c) * g->fstride + f];
         return m;
     }
     return load(g, v, p[0], p[1], p[2]);
@@ -146,7 +190,7 @@ static void neighbour_sum(const grid3_t* g, double dt, const double* v, int i, i
             int p[3] = { i, j, k };
             p[d] += side;
             double t[4];
-            neighbour_term(g, dt, d, side < 0 ? +1.0 : -1.0, get_cell(g, v, p), t);
+            neighbour_term(g, dt, d, side < 0 ? +1.0 : -1.0, get_cell(g, v, p, KIND_STATE), t);
             for (int q = 0; q < 4; ++q) s[q] += t[q];
         }
 }
@@ -176,10 +220,10 @@ static cell5_t apply_A_cell(const grid3_t* g, double dt, const double* sa, const
     return out;
 }
 
-void ora3_apply_A(const int* idesc, const double* ddesc, double dt, const double* sa,
-                  const double* ss, const double* v, double* out)
+void ora3_apply_A(const int* idesc, const double* ddesc, const double* inflow, double dt,
+                  const double* sa, const double* ss, const double* v, double* out)
 {
-    grid3_t g; grid_from_desc(&g, idesc, ddesc);
+    grid3_t g; grid_from_desc(&g, idesc, ddesc, inflow);
     for (int k = 0; k < g.n[2]; ++k)
         for (int j = 0; j < g.n[1]; ++j)
             for (int i = 0; i < g.n[0]; ++i)
@@ -202,10 +246,10 @@ static void residual(const grid3_t* g, double dt, const double* sa, const double
 }
 
 /* Eq. (13): r = b - A(v). */
-void ora3_residual(const int* idesc, const double* ddesc, double dt, const double* sa,
-                   const double* ss, const double* b, const double* v, double* r)
+void ora3_residual(const int* idesc, const double* ddesc, const double* inflow, double dt,
+                   const double* sa, const double* ss, const double* b, const double* v, double* r)
 {
-    grid3_t g; grid_from_desc(&g, idesc, ddesc);
+    grid3_t g; grid_from_desc(&g, idesc, ddesc, inflow);
     residual(&g, dt, sa, ss, b, v, r);
 }
 
@@ -222,7 +266,7 @@ static double norm(const grid3_t* g, const double* r)
 
 double ora3_norm(const int* idesc, const double* ddesc, const double* r)
 {
-    grid3_t g; grid_from_desc(&g, idesc, ddesc);
+    grid3_t g; grid_from_desc(&g, idesc, ddesc, NULL);
     return norm(&g, r);
 }
 
@@ -286,11 +330,11 @@ static int jacobi_sweep(const grid3_t* g, double dt, const double* sa, const dou
     return worst;
 }
 
-int ora3_jacobi_sweep(const int* idesc, const double* ddesc, double dt, const double* sa,
-                      const double* ss, const double* rhs, const double* vin, double* vout,
-                      double w0, double w1)
+int ora3_jacobi_sweep(const int* idesc, const double* ddesc, const double* inflow, double dt,
+                      const double* sa, const double* ss, const double* rhs, const double* vin,
+                      double* vout, double w0, double w1)
 {
-    grid3_t g; grid_from_desc(&g, idesc, ddesc);
+    grid3_t g; grid_from_desc(&g, idesc, ddesc, inflow);
     return jacobi_sweep(&g, dt, sa, ss, rhs, vin, vout, w0, w1);
 }
 
@@ -360,11 +404,11 @@ static int pseudo_time_smooth(const grid3_t* g, double dt, const double* sa, con
     return worst;
 }
 
-int ora3_pseudo_time_smooth(const int* idesc, const double* ddesc, double dt, const double* sa,
-                            const double* ss, const double* f, double* u, double dtau, int m,
-                            int nu, double theta)
+int ora3_pseudo_time_smooth(const int* idesc, const double* ddesc, const double* inflow, double dt,
+                            const double* sa, const double* ss, const double* f, double* u,
+                            double dtau, int m, int nu, double theta)
 {
-    grid3_t g; grid_from_desc(&g, idesc, ddesc);
+    grid3_t g; grid_from_desc(&g, idesc, ddesc, inflow);
     return pseudo_time_smooth(&g, dt, sa, ss, f, u, dtau, m, nu, theta);
 }
 
@@ -375,9 +419,45 @@ static void coarse_desc(const grid3_t* gf, grid3_t* gc)
 {
     *gc = *gf;
     for (int a = 0; a < 3; ++a) { gc->n[a] = gf->n[a] / 2; gc->h[a] = 2.0 * gf->h[a]; }
+    set_inflow(gc, NULL);          /* a coarse grid's profiles come from restrict_faces */
 }
 
-static void restrict_state(const grid3_t* gf, const grid3_t* gc, const double* fine, double* coarse)
+/* The 2D oracle's 1D profile rule, 1/4, 1/2, 1/4 with the ends copied, along one
+ * tangential axis of a face. */
+static double profile_weighted(const double* f, int nf, int i, int stride)
+{
+    int a = 2 * i - 1 < 0 ? 0 : 2 * i - 1, b = 2 * i, c = 2 * i + 1 >= nf ? nf - 1 : 2 * i + 1;
+    return 0.25 * f[(size_t)a * stride] + 0.5 * f[(size_t)b * stride] + 0.25 * f[(size_t)c * stride];
+}
+
+/* Coarse face profiles of every inflow wall: the 1D rule along each tangential
+ * axis (a tensor product).  out: [6][4][face_max(gc)]. */
+static void restrict_faces(const grid3_t* gf, const grid3_t* gc, double* out)
+{
+    for (int w = 0; w < 6; ++w) {
+        if (gf->bc[w] != BC_INFLOW || !gf->in[w]) continue;
+        int d = w / 2, ta, tb;
+        tangential(d, &ta, &tb);
+        int nfa = gf->n[ta], nfb = gf->n[tb], nca = gc->n[ta], ncb = gc->n[tb];
+        double* tmp = malloc((size_t)nca * nfb * sizeof(double));
+        for (int fld = 0; fld < 4; ++fld) {
+            const double* f = gf->in[w] + (size_t)fld * gf->fstride;
+            double* o = out + ((size_t)w * 4 + fld) * gc->fstride;
+            for (int ib = 0; ib < nfb; ++ib)             /* along a */
+                for (int ia = 0; ia < nca; ++ia)
+                    tmp[(size_t)ib * nca + ia] = nca == nfa ? f[(size_t)ib * nfa + ia]
+                                                            : profile_weighted(f + (size_t)ib * nfa, nfa, ia, 1);
+            for (int ib = 0; ib < ncb; ++ib)             /* along b */
+                for (int ia = 0; ia < nca; ++ia)
+                    o[(size_t)ib * nca + ia] = ncb == nfb ? tmp[(size_t)ib * nca + ia]
+                                                          : profile_weighted(tmp + ia, nfb, ib, nca);
+        }
+        free(tmp);
+    }
+}
+
+static void restrict_state(const grid3_t* gf, const grid3_t* gc, const double* fine, double* coarse,
+                           int kind)
 {
     static const double w[3] = { 0.25, 0.5, 0.25 };
     for (int kc = 0; kc < gc->n[2]; ++kc)
@@ -389,7 +469,7 @@ static void restrict_state(const grid3_t* gf, const grid3_t* gc, const double* f
                         for (int ax = -1; ax <= 1; ++ax) {
                             double wt = w[ax + 1] * w[by + 1] * w[cz + 1];
                             int p[3] = { 2 * ic + ax, 2 * jc + by, 2 * kc + cz };
-                            cell5_t s = get_cell(gf, fine, p);
+                            cell5_t s = get_cell(gf, fine, p, kind);
                             acc.E += wt * s.E;
                             for (int a = 0; a < 3; ++a) acc.F[a] += wt * s.F[a];
                             acc.T += wt * s.T;
@@ -415,17 +495,17 @@ static void restrict_scalar(const grid3_t* gf, const grid3_t* gc, const double* 
             }
 }
 
-void ora3_restrict_state(const int* idesc_f, const double* ddesc_f, const double* fine,
-                         double* coarse)
+void ora3_restrict_state(const int* idesc_f, const double* ddesc_f, const double* inflow_f,
+                         int kind, const double* fine, double* coarse)
 {
-    grid3_t gf, gc; grid_from_desc(&gf, idesc_f, ddesc_f); coarse_desc(&gf, &gc);
-    restrict_state(&gf, &gc, fine, coarse);
+    grid3_t gf, gc; grid_from_desc(&gf, idesc_f, ddesc_f, inflow_f); coarse_desc(&gf, &gc);
+    restrict_state(&gf, &gc, fine, coarse, kind);
 }
 
 /* Section 4.2, Fig. 1 / Eq. (14) on each axis: fine 2i takes coarse i, fine
  * 2i + 1 takes (coarse i + coarse i+1)/2; the tensor product on three axes
  * (weights 1, 1/2, 1/4, 1/8).  Coarse cells past the grid are its ghosts. */
-static cell5_t prolong_cell(const grid3_t* gc, const double* coarse, int i, int j, int k)
+static cell5_t prolong_cell(const grid3_t* gc, const double* coarse, int i, int j, int k, int kind)
 {
     int base[3] = { i / 2, j / 2, k / 2 }, odd[3] = { i % 2, j % 2, k % 2 };
     cell5_t r = { 0.0, { 0.0, 0.0, 0.0 }, 0.0 };
@@ -434,7 +514,7 @@ static cell5_t prolong_cell(const grid3_t* gc, const double* coarse, int i, int 
             for (int ax = 0; ax <= odd[0]; ++ax) {
                 double wt = (odd[0] ? 0.5 : 1.0) * (odd[1] ? 0.5 : 1.0) * (odd[2] ? 0.5 : 1.0);
                 int p[3] = { base[0] + ax, base[1] + by, base[2] + cz };
-                cell5_t s = get_cell(gc, coarse, p);
+                cell5_t s = get_cell(gc, coarse, p, kind);
                 r.E += wt * s.E;
                 for (int a = 0; a < 3; ++a) r.F[a] += wt * s.F[a];
                 r.T += wt * s.T;
@@ -442,12 +522,17 @@ static cell5_t prolong_cell(const grid3_t* gc, const double* coarse, int i, int 
     return r;
 }
 
-void ora3_prolong(const int* idesc_f, const double* ddesc_f, const double* coarse, double* fine)
+/* Plain prolongation of a coarse state onto the fine grid (ghosts of kind
+ * `kind`; inflow_c: the coarse grid's face profiles, or NULL). */
+void ora3_prolong(const int* idesc_f, const double* ddesc_f, const double* inflow_c, int kind,
+                  const double* coarse, double* fine)
 {
-    grid3_t gf, gc; grid_from_desc(&gf, idesc_f, ddesc_f); coarse_desc(&gf, &gc);
+    grid3_t gf, gc; grid_from_desc(&gf, idesc_f, ddesc_f, NULL); coarse_desc(&gf, &gc);
+    set_inflow(&gc, inflow_c);
     for (int k = 0; k < gf.n[2]; ++k)
         for (int j = 0; j < gf.n[1]; ++j)
-            for (int i = 0; i < gf.n[0]; ++i) store(&gf, fine, i, j, k, prolong_cell(&gc, coarse, i, j, k));
+            for (int i = 0; i < gf.n[0]; ++i)
+                store(&gf, fine, i, j, k, prolong_cell(&gc, coarse, i, j, k, kind));
 }
 
 /* Algorithm 4's prolongation with Eq. (34): u += P(u_c - v_c), damped by
@@ -463,7 +548,7 @@ static int prolong_correct(const grid3_t* gc, const grid3_t* gf, const double* u
         for (int j = 0; j < gf->n[1]; ++j)
             for (int i = 0; i < gf->n[0]; ++i) {
                 cell5_t u = load(gf, uf, i, j, k);
-                cell5_t pe = prolong_cell(gc, e, i, j, k);
+                cell5_t pe = prolong_cell(gc, e, i, j, k, KIND_DIFF);
                 double th = 1.0;
                 cell5_t t;
                 t.E = u.E + pe.E;
@@ -487,14 +572,22 @@ static int prolong_correct(const grid3_t* gc, const grid3_t* gf, const double* u
  * opacities restricted by full weighting. */
 typedef struct {
     grid3_t g;
-    double *sa, *ss, *v, *u, *f, *r;
+    double *sa, *ss, *v, *u, *f, *r, *inflow;
 } level3_t;
 
 static void build_levels(level3_t* lv, int L, const grid3_t* g0, const double* sa, const double* ss)
 {
     for (int l = 0; l < L; ++l) {
         level3_t* q = &lv[l];
-        if (l == 0) q->g = *g0; else coarse_desc(&lv[l - 1].g, &q->g);
+        q->inflow = NULL;
+        if (l == 0) {
+            q->g = *g0;
+        } else {
+            coarse_desc(&lv[l - 1].g, &q->g);
+            q->inflow = calloc((size_t)6 * 4 * q->g.fstride, sizeof(double));
+            restrict_faces(&lv[l - 1].g, &q->g, q->inflow);
+            set_inflow(&q->g, q->inflow);
+        }
         size_t n = ncell(&q->g);
         q->sa = malloc(n * sizeof(double)); q->ss = malloc(n * sizeof(double));
         q->v = calloc(NF * n, sizeof(double)); q->u = calloc(NF * n, sizeof(double));
@@ -512,6 +605,7 @@ static void free_levels(level3_t* lv, int L)
 {
     for (int l = 0; l < L; ++l) {
         free(lv[l].sa); free(lv[l].ss); free(lv[l].v); free(lv[l].u); free(lv[l].f); free(lv[l].r);
+        free(lv[l].inflow);
     }
 }
 
@@ -579,8 +673,8 @@ static void coarse_visit(level3_t* lv, int l, int fresh, int shape, ctx3_t* c)
     if (l == c->L - 1) return;
     level3_t* p = &lv[l + 1];
     residual(&q->g, c->dt, q->sa, q->ss, q->f, q->u, q->r);
-    restrict_state(&q->g, &p->g, q->u, p->v);
-    restrict_state(&q->g, &p->g, q->r, p->r);
+    restrict_state(&q->g, &p->g, q->u, p->v, KIND_STATE);
+    restrict_state(&q->g, &p->g, q->r, p->r, KIND_DIFF);
     corrections(lv, l, shape, c);
     c->damped += prolong_correct(&p->g, &q->g, p->u, p->v, q->u, c->th_c);
     if (pseudo_time_smooth(&q->g, c->dt, q->sa, q->ss, q->f, q->u, c->dtau, c->m, c->nul, c->th_ex) < 0)
@@ -595,11 +689,11 @@ static void coarse_visit(level3_t* lv, int l, int fresh, int shape, ctx3_t* c)
  * stats = { cycles, res0, res, dtau, fine_sweeps, status, newton_fail, damped };
  * res_hist[kappa] for kappa = 0 .. cycles.  status: 0 converged, -4 not
  * converged, -2 inadmissible input, -1 invalid parameters. */
-int ora3_implicit_step(const int* idesc, const double* ddesc, double dt, const double* sa,
-                       const double* ss, const int* ip, const double* dp, double* v,
-                       double* stats, double* res_hist)
+int ora3_implicit_step(const int* idesc, const double* ddesc, const double* inflow, double dt,
+                       const double* sa, const double* ss, const int* ip, const double* dp,
+                       double* v, double* stats, double* res_hist)
 {
-    grid3_t g0; grid_from_desc(&g0, idesc, ddesc);
+    grid3_t g0; grid_from_desc(&g0, idesc, ddesc, inflow);
     int L = ip[0], nu0 = ip[1], nul = ip[2], m = ip[3], mc = ip[4], maxc = ip[5];
     int signed_rule = ip[6], shape = ip[7];
     double dtau = dp[0], grow = dp[1], shrink = dp[2], eps_i = dp[3], eps_d = dp[4], tol = dp[5];
@@ -634,8 +728,8 @@ int ora3_implicit_step(const int* idesc, const double* ddesc, double dt, const d
                 level3_t* p = &lv[1];
                 ctx3_t c = { dt, dtau, th_ex, th_c, m, mc, nul, L, 0, 0 };
                 residual(&g0, dt, sa, ss, b, q0->u, q0->r);
-                restrict_state(&g0, &p->g, q0->u, p->v);
-                restrict_state(&g0, &p->g, q0->r, p->r);
+                restrict_state(&g0, &p->g, q0->u, p->v, KIND_STATE);
+                restrict_state(&g0, &p->g, q0->r, p->r, KIND_DIFF);
                 corrections(lv, 0, shape, &c);
                 c.damped += prolong_correct(&p->g, &g0, p->u, p->v, q0->u, th_c);
                 if (fine_jacobi(q0, dt, b, q0->u, nu0) < 0) ++c.newton_fail;

@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY: the tests use it; the product path never imports,
 links or runs anything under oracle/.  States are float64 arrays of shape
 (5, nz, ny, nx): planes E, Fx, Fy, Fz, T.  Walls (W, E, S, N, B, T) are
-"periodic", "reflect" or "neumann".
+"periodic", "reflect", "neumann" or "inflow"; inflow profiles are an array
+(6 walls, 4 fields E/Fx/Fy/Fz, F) with F the largest face, a wall's face indexed
+q_b * n_a + q_a over its two other axes a < b.
 """
 from __future__ import annotations
 
@@ -17,7 +19,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "m1_oracle3d.c")
 LIB = os.path.join(HERE, "liboracle3d.so")
-BC = {"periodic": 0, "reflect": 1, "neumann": 2}
+BC = {"periodic": 0, "reflect": 1, "neumann": 2, "inflow": 3}
+KIND_STATE, KIND_DIFF = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -62,6 +65,19 @@ class Grid3:
     c: float = 1.0
     a_r: float = 1.0
     c_v: float = 1.0
+    inflow: np.ndarray | None = None
+
+    @property
+    def face(self):
+        """Doubles per field of an inflow profile: the largest face."""
+        return max(self.ny * self.nz, self.nx * self.nz, self.nx * self.ny)
+
+    def inflow_ptr(self):
+        if self.inflow is None:
+            return None
+        self.inflow = _f64(self.inflow)
+        assert self.inflow.shape == (6, 4, self.face)
+        return _d(self.inflow)
 
     def ip(self):
         self._ip = np.array([self.nx, self.ny, self.nz, *[BC[b] for b in self.bc]], dtype=np.int32)
@@ -75,9 +91,9 @@ class Grid3:
     def shape(self):
         return (5, self.nz, self.ny, self.nx)
 
-    def coarse(self) -> "Grid3":
+    def coarse(self, inflow_c=None) -> "Grid3":
         return Grid3(self.nx // 2, self.ny // 2, self.nz // 2, 2 * self.hx, 2 * self.hy,
-                     2 * self.hz, self.bc, self.c, self.a_r, self.c_v)
+                     2 * self.hz, self.bc, self.c, self.a_r, self.c_v, inflow_c)
 
 
 def closure(E, F, c=1.0):
@@ -90,14 +106,16 @@ def closure(E, F, c=1.0):
 def apply_A(g: Grid3, dt, sa, ss, v):
     v, sa, ss = _f64(v), _f64(sa), _f64(ss)
     out = np.zeros(g.shape)
-    lib().ora3_apply_A(g.ip(), g.dp(), ctypes.c_double(dt), _d(sa), _d(ss), _d(v), _d(out))
+    lib().ora3_apply_A(g.ip(), g.dp(), g.inflow_ptr(), ctypes.c_double(dt), _d(sa), _d(ss), _d(v),
+                       _d(out))
     return out
 
 
 def residual(g: Grid3, dt, sa, ss, b, v):
     b, v, sa, ss = _f64(b), _f64(v), _f64(sa), _f64(ss)
     r = np.zeros(g.shape)
-    lib().ora3_residual(g.ip(), g.dp(), ctypes.c_double(dt), _d(sa), _d(ss), _d(b), _d(v), _d(r))
+    lib().ora3_residual(g.ip(), g.dp(), g.inflow_ptr(), ctypes.c_double(dt), _d(sa), _d(ss), _d(b),
+                        _d(v), _d(r))
     return r
 
 
@@ -108,30 +126,34 @@ def norm(g: Grid3, r):
 def jacobi_sweep(g: Grid3, dt, sa, ss, rhs, v, w0=0.0, w1=1.0):
     rhs, v, sa, ss = _f64(rhs), _f64(v), _f64(sa), _f64(ss)
     out = np.zeros(g.shape)
-    it = lib().ora3_jacobi_sweep(g.ip(), g.dp(), ctypes.c_double(dt), _d(sa), _d(ss), _d(rhs),
-                                 _d(v), _d(out), ctypes.c_double(w0), ctypes.c_double(w1))
+    it = lib().ora3_jacobi_sweep(g.ip(), g.dp(), g.inflow_ptr(), ctypes.c_double(dt), _d(sa),
+                                 _d(ss), _d(rhs), _d(v), _d(out), ctypes.c_double(w0),
+                                 ctypes.c_double(w1))
     return out, it
 
 
 def pseudo_time_smooth(g: Grid3, dt, sa, ss, f, u, dtau, m=3, nu=1, theta=0.5):
     f, sa, ss = _f64(f), _f64(sa), _f64(ss)
     u = _f64(u).copy()
-    it = lib().ora3_pseudo_time_smooth(g.ip(), g.dp(), ctypes.c_double(dt), _d(sa), _d(ss), _d(f),
-                                       _d(u), ctypes.c_double(dtau), m, nu, ctypes.c_double(theta))
+    it = lib().ora3_pseudo_time_smooth(g.ip(), g.dp(), g.inflow_ptr(), ctypes.c_double(dt), _d(sa),
+                                       _d(ss), _d(f), _d(u), ctypes.c_double(dtau), m, nu,
+                                       ctypes.c_double(theta))
     return u, it
 
 
-def restrict_state(g: Grid3, fine):
+def restrict_state(g: Grid3, fine, kind=KIND_STATE):
     gc = g.coarse()
     out = np.zeros(gc.shape)
-    lib().ora3_restrict_state(g.ip(), g.dp(), _d(_f64(fine)), _d(out))
+    lib().ora3_restrict_state(g.ip(), g.dp(), g.inflow_ptr(), kind, _d(_f64(fine)), _d(out))
     return out
 
 
-def prolong(g: Grid3, coarse):
-    """Plain prolongation of a coarse state onto the fine grid g."""
+def prolong(g: Grid3, coarse, kind=KIND_STATE, inflow_c=None):
+    """Plain prolongation of a coarse state onto the fine grid g (coarse ghosts
+    of kind `kind`; inflow_c: the coarse grid's profiles)."""
     out = np.zeros(g.shape)
-    lib().ora3_prolong(g.ip(), g.dp(), _d(_f64(coarse)), _d(out))
+    lib().ora3_prolong(g.ip(), g.dp(), _d(None if inflow_c is None else _f64(inflow_c)), kind,
+                       _d(_f64(coarse)), _d(out))
     return out
 
 
@@ -167,7 +189,7 @@ def implicit_step(g: Grid3, dt, sa, ss, v, p: SolveParams3):
                    p.theta_ex, p.theta_c])
     stats = np.zeros(8)
     hist = np.zeros(p.max_cycles + 1)
-    lib().ora3_implicit_step(g.ip(), g.dp(), ctypes.c_double(dt), _d(sa), _d(ss),
+    lib().ora3_implicit_step(g.ip(), g.dp(), g.inflow_ptr(), ctypes.c_double(dt), _d(sa), _d(ss),
                              ip.ctypes.data_as(_ip), _d(dp), _d(v), _d(stats), _d(hist))
     cyc = int(stats[0])
     st = dict(cycles=cyc, res0=stats[1], res=stats[2], dtau=stats[3], fine_sweeps=int(stats[4]),

@@ -4,7 +4,9 @@ structure; states uniform along z (and y) reducing to the 2D (1D) oracle term by
 term and, for the whole step, at the fixed point; invariance under a cyclic
 permutation of the axes; conservation; equilibrium; R = 2^-3 P^T; admissibility
 after every sweep and pseudo-time step (Propositions 1 and 2); dense Newton on a
-4^3 grid; W- and F-cycles reaching the V-cycle's fixed point."""
+4^3 grid; W- and F-cycles reaching the V-cycle's fixed point; inflow walls
+reducing to the 2D oracle's, an f = 1 beam along z obeying the exact upwind
+recurrence, and dense Newton with an inflow wall."""
 import numpy as np
 import pytest
 
@@ -266,3 +268,120 @@ def test_w_and_f_cycles_reach_the_v_cycle_fixed_point(shape):
     out, _, hs = O3.implicit_step(g, 2.0, sa, ss, v0, O3.SolveParams3(cycle=shape, **p))
     assert hv[-1] <= 1e-14 * hv[0] and hs[-1] <= 1e-14 * hs[0]
     assert rel(out, ref) <= 1e-12
+
+
+# ---- inflow walls ----
+
+def _inflow3(g, wall, E, F):
+    """A (6, 4, F) profile array with wall `wall` set from per-face arrays."""
+    out = np.zeros((6, 4, g.face))
+    nf = E.size
+    out[wall, 0, :nf] = E.ravel()
+    for c in range(3):
+        out[wall, 1 + c, :nf] = F[c].ravel()
+    return out
+
+
+def _beam_2d(n):
+    y = (np.arange(n) + 0.5) / n
+    chan = (y >= 0.4) & (y <= 0.6)
+    inflow = np.zeros((4, 3, n))
+    inflow[0, 0] = 1.0
+    inflow[0, 1] = np.where(chan, 1.0, 0.0)
+    return inflow
+
+
+def test_z_uniform_inflow_operator_is_the_2d_operator():
+    """An x-low inflow wall whose profile does not vary along z: the 3D operator
+    of a z-uniform state equals the 2D oracle's with the same inflow wall."""
+    nx = ny = 16
+    nz, dt = 4, 0.3
+    s2 = random_state3(nx, ny, 1, 23, fmax=0.8)[[0, 1, 2, 4], 0]
+    sa2, ss2 = opacities((ny, nx), 24)
+    in2 = _beam_2d(ny)
+    bc2 = ("inflow", "reflect", "reflect", "neumann")
+    g2 = O.Grid(2, nx, ny, 1.0 / nx, 1.0 / ny, 1.0, 1.0, 1.0, bc2, in2)
+    a2 = O.apply_A(g2, dt, sa2, ss2, s2)
+    g3 = O3.Grid3(nx, ny, nz, 1.0 / nx, 1.0 / ny, 0.5, bc2 + ("periodic", "periodic"))
+    face_E = np.repeat(in2[0, 0][None], nz, 0)              # (nz, ny): index k*ny + j
+    face_F = [np.repeat(in2[0, 1][None], nz, 0), np.repeat(in2[0, 2][None], nz, 0),
+              np.zeros((nz, ny))]
+    g3.inflow = _inflow3(g3, 0, face_E, face_F)
+    s3 = np.zeros(g3.shape)
+    s3[[0, 1, 2, 4]] = s2[:, None]
+    a3 = O3.apply_A(g3, dt, np.repeat(sa2[None], nz, 0), np.repeat(ss2[None], nz, 0), s3)
+    for k in range(nz):
+        assert rel(a3[[0, 1, 2, 4], k], a2) <= 1e-13
+    assert np.abs(a3[3]).max() == 0.0
+
+
+def test_z_uniform_inflow_step_reaches_the_2d_fixed_point():
+    """The whole step with an inflow wall (coarse profiles restricted along the
+    wall) reaches the 2D oracle's fixed point."""
+    nx = ny = 16
+    s2 = random_state3(nx, ny, 1, 25, fmax=0.6)[[0, 1, 2, 4], 0]
+    sa2, ss2 = opacities((ny, nx), 26, -1.0, 1.0)
+    in2 = _beam_2d(ny)
+    bc2 = ("inflow", "neumann", "reflect", "reflect")
+    dt = 2.0 / nx
+    g2 = O.Grid(2, nx, ny, 1.0 / nx, 1.0 / ny, 1.0, 1.0, 1.0, bc2, in2)
+    ref, _, h2, _ = O.implicit_step(g2, dt, sa2, ss2, s2,
+                                    O.SolveParams(lmax=3, tol=0.0, max_cycles=600))
+    assert h2[-1] <= 1e-14 * h2[0]
+    nz = 4
+    g3 = O3.Grid3(nx, ny, nz, 1.0 / nx, 1.0 / ny, 0.25, bc2 + ("periodic", "periodic"))
+    g3.inflow = _inflow3(g3, 0, np.repeat(in2[0, 0][None], nz, 0),
+                         [np.repeat(in2[0, 1][None], nz, 0), np.repeat(in2[0, 2][None], nz, 0),
+                          np.zeros((nz, ny))])
+    s3 = np.zeros(g3.shape)
+    s3[[0, 1, 2, 4]] = s2[:, None]
+    out, _, h3 = O3.implicit_step(g3, dt, np.repeat(sa2[None], nz, 0), np.repeat(ss2[None], nz, 0),
+                                  s3, O3.SolveParams3(lmax=3, tol=0.0, max_cycles=600))
+    assert h3[-1] <= 1e-14 * h3[0]
+    for k in range(nz):
+        assert rel(out[[0, 1, 2, 4], k], ref) <= 1e-11
+
+
+def test_free_streaming_front_along_z_satisfies_upwind_recurrence():
+    """No matter, F = cE along z everywhere and an f = 1 beam entering through the
+    z-low wall: the x and y faces cancel their diagonal terms, and the step solves
+    (1 + alpha) E_k - alpha E_{k-1} = E^n_k exactly, with F = cE kept."""
+    nx = ny = 4
+    nz, c, cfl = 64, 1.0, 8.0
+    g = O3.Grid3(nx, ny, nz, 0.25, 0.25, 1.0 / nz,
+                 ("periodic",) * 4 + ("inflow", "neumann"), c=c)
+    face = g.nx * g.ny
+    g.inflow = _inflow3(g, 4, np.ones(face), [np.zeros(face), np.zeros(face), c * np.ones(face)])
+    v = np.zeros(g.shape)
+    v[0] = 1e-6
+    v[3] = c * 1e-6
+    v[4] = 1.0
+    z = np.zeros((nz, ny, nx))
+    out, st, _ = O3.implicit_step(g, cfl / nz, z, z, v, O3.SolveParams3(lmax=3, tol=1e-14,
+                                                                        max_cycles=2000))
+    assert st["status"] == 0
+    E = np.concatenate([[1.0], out[0][:, 0, 0]])
+    np.testing.assert_allclose((1 + cfl) * E[1:] - cfl * E[:-1], v[0][:, 0, 0], rtol=0,
+                               atol=1e-13)
+    np.testing.assert_allclose(out[3], c * out[0], rtol=1e-12)
+    assert np.abs(out[1:3]).max() <= 1e-14
+    assert np.ptp(out[0], axis=(1, 2)).max() <= 1e-14           # uniform across x, y
+
+
+def test_multigrid_step_matches_brute_force_newton_with_inflow():
+    g = O3.Grid3(4, 4, 4, 0.25, 0.25, 0.25,
+                 ("inflow", "reflect", "periodic", "periodic", "neumann", "reflect"))
+    rng = np.random.default_rng(27)
+    E_in = 10.0 ** rng.uniform(-0.5, 0.5, 16)
+    d = rng.standard_normal((3, 16))
+    d /= np.linalg.norm(d, axis=0)
+    F_in = 0.8 * E_in * d
+    g.inflow = _inflow3(g, 0, E_in, F_in)
+    v0 = random_state3(4, 4, 4, 28, fmax=0.7)
+    sa, ss = opacities((4, 4, 4), 29, -1.0, 1.0)
+    dt = 0.8
+    mg, st, hist = O3.implicit_step(g, dt, sa, ss, v0, O3.SolveParams3(lmax=2, tol=0.0,
+                                                                        max_cycles=1500))
+    assert hist[-1] <= 1e-15 * hist[0]
+    nw = _newton_solve3(g, dt, sa, ss, v0.copy(), mg * (1 + 1e-3 * rng.standard_normal(mg.shape)))
+    np.testing.assert_allclose(mg, nw, rtol=0, atol=1e-11 * np.abs(nw[0]).max())
