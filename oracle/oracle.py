@@ -43,37 +43,43 @@ _LIB = None
 def lib():
     global _LIB
     if _LIB is None:
-        _LIB = ctypes.CDLL(build())
-        L = _LIB
-        L.ora_closure.argtypes = [ctypes.c_double] * 4 + [_dp]
-        L.ora_eddington_factor.argtypes = [ctypes.c_double]
-        L.ora_eddington_factor.restype = ctypes.c_double
-        L.ora_apply_A.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
-        L.ora_residual.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
-        L.ora_norm.argtypes = [_ip, _dp, _dp]
-        L.ora_norm.restype = ctypes.c_double
-        L.ora_jacobi_sweep.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
-                                       ctypes.c_double, ctypes.c_double]
-        L.ora_jacobi_sweep.restype = ctypes.c_int
-        L.ora_local_solve.argtypes = [ctypes.c_double] * 7 + [_dp, _dp]
-        L.ora_local_solve.restype = ctypes.c_int
-        L.ora_max_admissible_step.argtypes = [ctypes.c_double] * 9
-        L.ora_max_admissible_step.restype = ctypes.c_double
-        L.ora_admissible.argtypes = [ctypes.c_double] * 5
-        L.ora_admissible.restype = ctypes.c_int
-        L.ora_pseudo_time_smooth.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp,
-                                             ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_double]
-        L.ora_pseudo_time_smooth.restype = ctypes.c_int
-        L.ora_restrict_state.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp, _dp]
-        L.ora_restrict_scalar.argtypes = [_ip, _dp, _dp, _dp]
-        L.ora_prolong.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp, _dp]
-        L.ora_prolong_correct.argtypes = [_ip, _dp, _dp, _dp, _dp, ctypes.c_double]
-        L.ora_prolong_correct.restype = ctypes.c_int
-        L.ora_implicit_step.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _ip, _dp, _dp,
-                                        _dp, _dp, _dp]
-        L.ora_implicit_step.restype = ctypes.c_int
+        _LIB = bind(ctypes.CDLL(build()))
     return _LIB
+
+
+def bind(L):
+    """Declare the argument and result types of the oracle's exported functions
+    on a loaded copy of the library (the tests also bind copies built with a
+    planted mistake, to show that the pins catch it)."""
+    L.ora_closure.argtypes = [ctypes.c_double] * 4 + [_dp]
+    L.ora_eddington_factor.argtypes = [ctypes.c_double]
+    L.ora_eddington_factor.restype = ctypes.c_double
+    L.ora_apply_A.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+    L.ora_residual.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
+    L.ora_norm.argtypes = [_ip, _dp, _dp]
+    L.ora_norm.restype = ctypes.c_double
+    L.ora_jacobi_sweep.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
+                                   ctypes.c_double, ctypes.c_double]
+    L.ora_jacobi_sweep.restype = ctypes.c_int
+    L.ora_local_solve.argtypes = [ctypes.c_double] * 7 + [_dp, _dp]
+    L.ora_local_solve.restype = ctypes.c_int
+    L.ora_max_admissible_step.argtypes = [ctypes.c_double] * 9
+    L.ora_max_admissible_step.restype = ctypes.c_double
+    L.ora_admissible.argtypes = [ctypes.c_double] * 5
+    L.ora_admissible.restype = ctypes.c_int
+    L.ora_pseudo_time_smooth.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double]
+    L.ora_pseudo_time_smooth.restype = ctypes.c_int
+    L.ora_restrict_state.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp, _dp]
+    L.ora_restrict_scalar.argtypes = [_ip, _dp, _dp, _dp]
+    L.ora_prolong.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp, _dp]
+    L.ora_prolong_correct.argtypes = [_ip, _dp, _dp, _dp, _dp, ctypes.c_double]
+    L.ora_prolong_correct.restype = ctypes.c_int
+    L.ora_implicit_step.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, _dp, _ip, _dp, _dp,
+                                    _dp, _dp, _dp]
+    L.ora_implicit_step.restype = ctypes.c_int
+    return L
 
 
 def _d(a):
