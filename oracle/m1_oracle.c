@@ -22,10 +22,19 @@
  *
  * Data layout: a state is 4 planes [E | Fx | Fy | T], each ny*nx doubles,
  * row-major (index j*nx+i).  In 1D, ny = 1 and the Fy plane stays zero.
+ *
+ * Threads.  The outer cell loops carry OpenMP pragmas.  The plain build ignores
+ * them (one core); the all-core build (-fopenmp) runs the same loops on every
+ * host core.  Every cell's arithmetic is the same in both, the loop reductions
+ * are over integers and the norm is summed serially, so both builds give
+ * bit-for-bit the same results.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NEUMANN = 2, BC_INFLOW = 3 };
 enum { KIND_STATE = 0, KIND_DIFF = 1 };
@@ -66,6 +75,16 @@ static void grid_from_desc(grid_t* g, const int* idesc, const double* ddesc, con
             g->in_E[w] = g->in_Fx[w] = g->in_Fy[w] = NULL;
         }
     }
+}
+
+/* Host threads the cell loops run on: 1 in the plain build. */
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */
@@ -228,6 +247,7 @@ void ora_apply_A(const int* idesc, const double* ddesc, const double* inflow, do
                  const double* sa, const double* ss, const double* v, double* out)
 {
     grid_t g; grid_from_desc(&g, idesc, ddesc, inflow);
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < g.ny; ++j)
         for (int i = 0; i < g.nx; ++i) store(&g, out, i, j, apply_A_cell(&g, dt, sa, ss, v, i, j));
 }
@@ -238,6 +258,7 @@ void ora_residual(const int* idesc, const double* ddesc, const double* inflow, d
 {
     grid_t g; grid_from_desc(&g, idesc, ddesc, inflow);
     size_t n = (size_t)g.nx * g.ny;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < g.ny; ++j)
         for (int i = 0; i < g.nx; ++i) {
             size_t k = (size_t)j * g.nx + i;
@@ -311,7 +332,8 @@ static int jacobi_sweep(const grid_t* g, double dt, const double* sa, const doub
                         const double* rhs, const double* vin, double* vout, double w0, double w1)
 {
     double diag = transport_diag(g, dt);
-    int worst = 0;
+    int fail = 0, maxit = 0;
+    #pragma omp parallel for collapse(2) schedule(static) reduction(|:fail) reduction(max:maxit)
     for (int j = 0; j < g->ny; ++j)
         for (int i = 0; i < g->nx; ++i) {
             size_t k = (size_t)j * g->nx + i;
@@ -324,11 +346,11 @@ static int jacobi_sweep(const grid_t* g, double dt, const double* sa, const doub
             beta[3] = b.T;
             int it = ora_local_solve(w0, w1, diag, g->c * dt * sa[k], g->c * dt * (sa[k] + ss[k]),
                                      g->c_v, g->a_r, beta, out);
-            if (it < 0) worst = -1; else if (worst >= 0 && it > worst) worst = it;
+            if (it < 0) fail = 1; else if (it > maxit) maxit = it;
             cell_t o = { out[0], out[1], out[2], out[3] };
             store(g, vout, i, j, o);
         }
-    return worst;
+    return fail ? -1 : maxit;
 }
 
 int ora_jacobi_sweep(const int* idesc, const double* ddesc, const double* inflow, double dt,
@@ -395,6 +417,7 @@ static int pseudo_time_smooth(const grid_t* g, double dt, const double* sa, cons
     double* w2 = malloc(4 * n * sizeof(double));
     int worst = 0;
     for (int it = 0; it < m; ++it) {
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
                 cell_t s = load(g, u, i, j), d = load(g, f, i, j), o;
@@ -433,6 +456,7 @@ static void restrict_state(const grid_t* gf, const grid_t* gc, const double* fin
                            int kind)
 {
     static const double w[3] = { 0.25, 0.5, 0.25 };
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int jc = 0; jc < gc->ny; ++jc)
         for (int ic = 0; ic < gc->nx; ++ic) {
             cell_t acc = { 0, 0, 0, 0 };
@@ -453,6 +477,7 @@ static void restrict_state(const grid_t* gf, const grid_t* gc, const double* fin
 static void restrict_scalar(const grid_t* gf, const grid_t* gc, const double* fine, double* coarse)
 {
     static const double w[3] = { 0.25, 0.5, 0.25 };
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int jc = 0; jc < gc->ny; ++jc)
         for (int ic = 0; ic < gc->nx; ++ic) {
             double acc = 0.0;
@@ -498,6 +523,7 @@ static int prolong_correct(const grid_t* gc, const grid_t* gf, const double* uc,
     double* e = malloc(4 * nc * sizeof(double));
     for (size_t k = 0; k < 4 * nc; ++k) e[k] = uc[k] - vc[k];
     int damped = 0;
+    #pragma omp parallel for collapse(2) schedule(static) reduction(+:damped)
     for (int j = 0; j < gf->ny; ++j)
         for (int i = 0; i < gf->nx; ++i) {
             cell_t u = load(gf, uf, i, j);
@@ -555,6 +581,7 @@ void ora_prolong(const int* idesc_f, const double* ddesc_f, const double* inflow
                 gc.in_Fy[w] = inflow_c + (size_t)(w * 3 + 2) * L;
             }
     }
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < gf.ny; ++j)
         for (int i = 0; i < gf.nx; ++i) store(&gf, fine, i, j, prolong_cell(&gc, coarse, i, j, gf.dim, kind));
 }
@@ -655,6 +682,7 @@ int ora_level_sizes(const int* idesc, int L, int* nx_out, int* ny_out)
 static void level_residual(level_t* q, double dt, const double* rhs, const double* u, double* r)
 {
     size_t n = (size_t)q->g.nx * q->g.ny;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < q->g.ny; ++j)
         for (int i = 0; i < q->g.nx; ++i) {
             size_t k = (size_t)j * q->g.nx + i;
@@ -668,6 +696,7 @@ static void level_residual(level_t* q, double dt, const double* rhs, const doubl
 static void fas_rhs(level_t* q, double dt)
 {
     size_t n = (size_t)q->g.nx * q->g.ny;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < q->g.ny; ++j)
         for (int i = 0; i < q->g.nx; ++i) {
             size_t k = (size_t)j * q->g.nx + i;

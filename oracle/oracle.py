@@ -28,23 +28,59 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+LIB_OMP = os.path.join(HERE, "liboracle_m1_omp.so")
+_FLAGS = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC"]
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, no contraction so x86 and Arm agree)."""
+    """Compile the oracle with gcc (plain C99, no contraction so x86 and Arm
+    agree): the one-core build, and the all-core build of the same source with
+    OpenMP when the compiler supports it (else only the one-core build)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC",
-               "-o", LIB, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        subprocess.run(_FLAGS + ["-o", LIB, SRC, "-lm"], check=True)
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(LIB_OMP) < os.path.getmtime(SRC):
+        subprocess.run(_FLAGS + ["-fopenmp", "-o", LIB_OMP, SRC, "-lm"], check=False,
+                       stderr=subprocess.DEVNULL)
     return LIB
 
 
 _LIB = None
+_LIBS = {}
+
+
+def _load(path):
+    if path not in _LIBS:
+        L = bind(ctypes.CDLL(path))
+        L.ora_threads.restype = ctypes.c_int
+        _LIBS[path] = L
+    return _LIBS[path]
 
 
 def lib():
     global _LIB
     if _LIB is None:
-        _LIB = bind(ctypes.CDLL(build()))
+        build()
+        _LIB = _load(LIB)
     return _LIB
+
+
+def have_all_cores() -> bool:
+    build()
+    return os.path.exists(LIB_OMP)
+
+
+def use_all_cores(on: bool = True) -> int:
+    """Route every call of this module to the all-core (OpenMP) build of the
+    same source (on) or the one-core build (off).  Returns the thread count."""
+    global _LIB
+    build()
+    _LIB = _load(LIB_OMP if on else LIB)
+    return threads()
+
+
+def threads() -> int:
+    """Host threads the oracle's cell loops run on (1 for the one-core build)."""
+    return int(lib().ora_threads())
 
 
 def bind(L):

@@ -230,19 +230,33 @@ def batched_instances(count: int = 512, seed: int = 5,
     return out
 
 
-def crop(case: dict, n: int) -> dict:
-    """The lower-left n x n corner of a 2D case (same generator, smaller grid)."""
+def crop(case: dict, n: int, j0: int = 0, i0: int = 0) -> dict:
+    """The n x n window of a 2D case starting at row j0, column i0 (same
+    generator, smaller grid, same cell size and time step; the walls and the
+    inflow profiles of the window's edges are the case's)."""
     c = dict(case)
     d = dict(case["desc"])
     h = d["lx"] / d["nx"]
     d.update(nx=n, ny=n, lx=n * h, ly=n * h)
     c["desc"] = d
-    c["state"] = np.ascontiguousarray(case["state"][:, :n, :n])
-    c["sa"] = np.ascontiguousarray(case["sa"][:n, :n])
-    c["ss"] = np.ascontiguousarray(case["ss"][:n, :n])
+    c["state"] = np.ascontiguousarray(case["state"][:, j0:j0 + n, i0:i0 + n])
+    c["sa"] = np.ascontiguousarray(case["sa"][j0:j0 + n, i0:i0 + n])
+    c["ss"] = np.ascontiguousarray(case["ss"][j0:j0 + n, i0:i0 + n])
     if case.get("inflow") is not None:
-        c["inflow"] = np.ascontiguousarray(case["inflow"][:, :, :n])
+        # west/east walls are indexed by row, south/north walls by column
+        fin = case["inflow"]
+        inflow = np.zeros((4, 3, n))
+        inflow[0:2] = fin[0:2, :, j0:j0 + n]
+        inflow[2:4] = fin[2:4, :, i0:i0 + n]
+        c["inflow"] = inflow
     return c
+
+
+def beam_channel_crop(n: int = 1024, full: int = 4096, lmax: int = 8, tol: float = 1e-8) -> dict:
+    """The n x n window of the full x full beam-in-a-channel case that holds the
+    beam: on the west wall, centred on the channel (rows full/2 - n/2 ...)."""
+    return dict(crop(beam_channel_2d(full, lmax=lmax, tol=tol), n, j0=(full - n) // 2, i0=0),
+                lmax=lmax)
 
 
 def bump_case(dim: int, n: int, seed: int, cfl: float, lmax: int, tol: float) -> dict:

@@ -138,3 +138,23 @@ def test_serving_stream_recipe():
             assert d["nx"] in (256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536)
         else:
             assert d["nx"] == d["ny"] and d["nx"] in (128, 256, 512, 1024, 2048)
+
+
+def test_beam_window_holds_the_beam():
+    # the 1024^2 window of the 4096^2 beam-in-a-channel grid, on the west wall and
+    # centred on the channel: same cell size and time step as the full grid, the
+    # channel rows (y in [0.45, 0.55] of the full grid) inside, the f = 1 beam on
+    # exactly those rows of the west wall
+    full = inputs.beam_channel_2d(4096)
+    win = inputs.beam_channel_crop(1024)
+    h = 1.0 / 4096
+    assert win["desc"]["nx"] == win["desc"]["ny"] == 1024
+    assert win["desc"]["lx"] == pytest.approx(1024 * h) and win["dt"] == full["dt"]
+    rows = 1536 + np.arange(1024)
+    y = (rows + 0.5) * h
+    chan = (y >= 0.45) & (y <= 0.55)
+    assert chan.sum() == 410
+    np.testing.assert_array_equal(win["inflow"][0, 1], np.where(chan, 1.0, 0.0))
+    np.testing.assert_array_equal(win["inflow"][0, 0], 1.0)
+    np.testing.assert_array_equal(win["sa"], full["sa"][1536:2560, :1024])
+    assert np.all(win["sa"][chan] == 1e-2)
