@@ -129,17 +129,88 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_sample(case, cycles):
-    """The FP64 oracle, as it stands, on `cycles` V-cycles of the workload
-    (1 host core).  Returns (cell-updates/s, seconds, fine sweeps)."""
+def cpu_sample(case, cycles, all_cores=False):
+    """The FP64 oracle, as it stands, on `cycles` V-cycles of the workload, on
+    one host core or on all of them (the OpenMP build of the same source, bit
+    for bit the same results).  Returns (cell-updates/s, seconds, fine sweeps,
+    threads)."""
     from oracle import oracle as O
-    g = O.Grid.from_case(case)
-    p = O.SolveParams(lmax=case["lmax"], tol=0.0, max_cycles=cycles)
-    t = time.perf_counter()
-    _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"], p)
-    dt = time.perf_counter() - t
+    threads = O.use_all_cores(all_cores and O.have_all_cores())
+    try:
+        g = O.Grid.from_case(case)
+        p = O.SolveParams(lmax=case["lmax"], tol=0.0, max_cycles=cycles)
+        t = time.perf_counter()
+        _, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"], p)
+        dt = time.perf_counter() - t
+    finally:
+        O.use_all_cores(False)
     cells = case["desc"]["nx"] * case["desc"]["ny"]
-    return cells * st["fine_sweeps"] / dt, dt, st["fine_sweeps"]
+    return cells * st["fine_sweeps"] / dt, dt, st["fine_sweeps"], threads
+
+
+def oracle_step_worker(path, threads):
+    """Child process (spawned): the oracle's full step of the FP64 workload on
+    `threads` host threads, saved to `path` (state, cycles, seconds)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_2208_14703_gb300 import inputs
+    case = inputs.hot_square_2d(N)
+    nthr = O.use_all_cores(O.have_all_cores())
+    g = O.Grid.from_case(case)
+    t = time.perf_counter()
+    v, st, _, _ = O.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"],
+                                  O.SolveParams(lmax=case["lmax"], tol=case["tol"]))
+    np.savez(path, state=v, cycles=st["cycles"], status=st["status"],
+             seconds=time.perf_counter() - t, threads=nthr)
+
+
+def start_oracle_step():
+    """Starts the oracle's full step of the FP64 workload in a spawned process
+    on all but two host cores (the GPU's host threads keep two).  Returns
+    (process, path)."""
+    import multiprocessing as mp
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    threads = max(1, (os.cpu_count() or 1) - 2)
+    proc = mp.get_context("spawn").Process(target=oracle_step_worker, args=(path, threads))
+    proc.start()
+    return proc, path
+
+
+def finish_oracle_step(proc, path, results, timeout_s=3600.0):
+    """Waits for the oracle's step and returns the relative L2 error per field of
+    each GPU result in `results` (name -> (4, ny, nx) state) against it."""
+    proc.join(timeout_s)
+    if proc.is_alive():
+        proc.terminate()
+        proc.join()
+        return {"error": f"the oracle step did not finish within {timeout_s:.0f} s"}
+    try:
+        d = np.load(path)
+        ref = d["state"]
+        out = {"oracle_cycles": int(d["cycles"]), "oracle_status": int(d["status"]),
+               "oracle_seconds": float(d["seconds"]), "oracle_threads": int(d["threads"])}
+    except (OSError, KeyError, ValueError) as e:
+        return {"error": f"the oracle step failed: {e}"}
+    finally:
+        if os.path.exists(path):
+            os.unlink(path)
+    for name, got in results.items():
+        out[name] = field_errors(got, ref)
+    return out
+
+
+def rounded(x, sig=4):
+    """A copy of a JSON-able structure with floats kept to `sig` significant
+    digits (keeps the printed line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{sig}g}")
+    if isinstance(x, dict):
+        return {k: rounded(v, sig) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [rounded(v, sig) for v in x]
+    return x
 
 
 def sweep_ms(grid, dt, stream, flush, reset, reps=20):
@@ -203,6 +274,7 @@ def bench_mixed(m1, case, stream, s0, flush, ref64, steps, hbm_peak):
     grid.close()
     gbs = SWEEP32_BYTES * cells / (sms * 1e-3) / 1e9
     units = cells * sum(x.sweeps for x in st)
+    bench_mixed.state = got
     return {"workload": WORKLOAD.replace("fp64", "mixed"), "value": units / (sum(ms) * 1e-3),
             "unit": UNIT, "ms_per_step": float(np.mean(ms)),
             "cycles_per_step": [x.cycles for x in st],
@@ -496,21 +568,23 @@ def run_reference(args, case):
     from oracle import oracle as O
     O.build()
     cyc = 2
+    threads = 1
     for _ in range(args.warmup):
-        cpu_sample(case, cyc)
+        cpu_sample(case, cyc, all_cores=True)
     vals, secs = [], []
     for _ in range(args.steps):
-        v, s, _ = cpu_sample(case, cyc)
+        v, s, _, threads = cpu_sample(case, cyc, all_cores=True)
         vals.append(v)
         secs.append(s)
     value = float(np.mean(vals))
-    sample = f"{cyc} V-cycles of the workload per step (fine sweeps x 1024^2 cells / time)"
+    sample = (f"{cyc} V-cycles of the workload per step (fine sweeps x 1024^2 cells / time), "
+              f"the oracle's OpenMP build on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -525,10 +599,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed, batched and serving measurements")
-    ap.add_argument("--batch-count", type=int, default=32,
-                    help="instances of the batched sample (512 = the full batched config)")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="instances of the batched configuration (default: all 512)")
     ap.add_argument("--serve-full", action="store_true",
-                    help="serve the full stream (64 requests, 10-100 steps, up to 2048^2)")
+                    help="serve 64 requests of the serving recipe instead of the 10-request sample")
+    ap.add_argument("--no-oracle-errors", action="store_true",
+                    help="skip the oracle's full step (per-field errors of the GPU results)")
     args = ap.parse_args()
 
     from paper_2208_14703_gb300 import inputs
@@ -607,10 +683,11 @@ def main():
     units = cells * sum(sweeps)
     ms_max, _, value = reduce_over_ranks(ms_total, units, dev, world)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers, over as many steps as the
+    # timed region: set_state from pinned host arrays, the step, get_state back
     pin = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).pin_memory() for k in range(4)]
     outp = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in range(4)]
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, args.steps)
     torch.cuda.synchronize()
     te = time.perf_counter()
     e2e_units = 0
@@ -622,14 +699,22 @@ def main():
     te = time.perf_counter() - te
     _, _, e2e_val = reduce_over_ranks(1e3 * te, e2e_units, dev, world)
 
+    # the FP64 pipe's ceiling on this GPU (the fine sweep's roof), measured
     pk = peaks()
+    try:
+        fp64_peak = m1.probe_fma_peak(m1.FP64, stream.cuda_stream, reps=5) / 1e12
+        peak_source = ("measured: m1_probe_fma_peak, DFMA instructions per second over lanes "
+                       "(independent chains, median of 5 launches), this GPU, this run")
+    except m1.M1Error as e:
+        fp64_peak = FP64_PEAK_TOPS
+        peak_source = f"derived 152 SMs x 2 FP64 ops/clk x 2.07 GHz (the probe failed: {e})"
     tops = SWEEP_OPS * cells / (sweep64_ms * 1e-3) / 1e12
     gbs = SWEEP_BYTES * cells / (sweep64_ms * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": tops, "peak": FP64_PEAK_TOPS, "unit": "Top/s",
-            "frac": tops / FP64_PEAK_TOPS, "traffic": SWEEP64_TRAFFIC_PER_CELL * cells,
+    roof = {"bound": "alu", "achieved": tops, "peak": fp64_peak, "unit": "Top/s",
+            "frac": tops / fp64_peak, "traffic": SWEEP64_TRAFFIC_PER_CELL * cells,
             "kernel": "k_sweep<double> (fine Jacobi sweep, FP64)", "kernel_ms": sweep64_ms,
-            "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (no measured FP64 "
-                           "peak in MEASURED_PEAKS.json)",
+            "peak_source": peak_source, "peak_derived": FP64_PEAK_TOPS,
+            "frac_of_derived": tops / FP64_PEAK_TOPS,
             "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL, DADD, FP64 compare or conversion)",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                               "2048^2 launch (457.2 MB), scaled to 1024^2 by cells",
@@ -640,32 +725,44 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
-        v, secs, fs = cpu_sample(case, 4)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"4 V-cycles of the same 1024^2 workload ({fs} fine sweeps, {secs:.1f} s)"}
+        v, secs, fs, thr = cpu_sample(case, 4, all_cores=True)
+        v1, secs1, fs1, _ = cpu_sample(case, 4, all_cores=False)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"4 V-cycles of the same 1024^2 workload ({fs} fine sweeps, {secs:.1f} s), "
+                         f"the oracle's OpenMP build on {thr} host threads (of {os.cpu_count()})",
+               "one_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same 4 V-cycles, one-core build ({secs1:.1f} s)"}}
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         from paper_2208_14703_gb300 import inputs
-        extras["mixed"] = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps,
-                                      pk["hbm_gbs"])
-        extras["mixed"]["roofline_fp32_sweep_4096"] = bench_fp32_sweep_large(m1, stream, flush,
-                                                                             pk["hbm_gbs"])
+        ora = None if args.no_oracle_errors else start_oracle_step()
         extras["cycle_shapes"] = bench_cycle_shapes(m1, case, stream, s0, flush)
         extras["sweep3d"] = bench_sweep3d(m1, stream)
         extras["paper_beam"] = bench_paper_beam(m1, stream)
         extras["paper_riemann"] = bench_paper_riemann(m1, stream)
+        mixed = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps, pk["hbm_gbs"])
+        mixed["roofline_fp32_sweep_4096"] = bench_fp32_sweep_large(m1, stream, flush,
+                                                                   pk["hbm_gbs"])
         extras["batched"] = bench_batched(m1, args.batch_count, stream)
         if args.serve_full:
             reqs = inputs.serving_stream(64)
+            sample = "64 requests of the serving recipe (seed 11)"
         else:
-            reqs = inputs.serving_stream(12, rate_hz=20.0, sizes_2d=(128, 256, 512),
-                                         steps=(10, 20))
+            reqs = inputs.serving_stream(10, seed=133)
+            sample = ("10 requests of the serving recipe (seed 133: 1D 256..65536, 2D "
+                      "128..2048, 10-100 steps each, 432 steps)")
         extras["serving"] = bench_serving(m1, reqs, stream, 32 << 30)
-        extras["serving"]["workload"] = ("poisson-stream-1d-256..65536-2d-128..2048-10..100-steps"
-                                         if args.serve_full else
-                                         "poisson-stream-sample-12-requests-1d-256..65536-"
-                                         "2d-128..512-10..20-steps")
+        extras["serving"]["workload"] = (
+            f"poisson-stream: {sample}, against the recipe's 2000 requests at 4 offered loads")
+        if ora is not None:
+            mixed["err_vs_oracle"] = finish_oracle_step(*ora, {"fp64": ref64,
+                                                               "mixed": bench_mixed.state})
+        extras["mixed"] = mixed
+        extras = {k: rounded(v) for k, v in extras.items()}
+        # the large blocks last: a reader of the line's tail sees them
+        for k in ("mixed", "batched", "serving"):
+            extras[k] = extras.pop(k)
 
     launches = sum(s.launches for s in stats) + 2 * args.steps
     if rank == 0:
@@ -687,7 +784,7 @@ def main():
             "wall_s": wall,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
-                    "d2h_bytes_per_step": 4 * 8 * cells},
+                    "d2h_bytes_per_step": 4 * 8 * cells, "steps": e2e_steps},
             "gpu_launches": launches, "clocks": sampler_out, **extras,
         }))
     grid.close()

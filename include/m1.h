@@ -281,6 +281,19 @@ m1_status m1_set_tuning(const m1_tune_entry* in, int n);
 /* The strip height a new nx x ny level of the given kind would take. */
 m1_status m1_strip_rows(int kind, int nx, int ny, int* rows);
 
+/* ---- arithmetic peak probe (a roofline denominator; not a step of the method) ----
+ * The FP64 kernels of this library are bound by the FP64 pipe, not by HBM; this
+ * call measures that pipe's ceiling on the current device.  A kernel of
+ * independent fused multiply-add chains (8 per thread, no chain waits on
+ * another; 152 x 8 blocks of 256 threads, 4096 rounds) runs `reps` timed
+ * launches after one untimed one, each timed with CUDA events on cuda_stream
+ * (NULL: the legacy default stream); *ops_per_s = FMA instructions per second
+ * summed over lanes (one FMA is one pipe operation, two flops) of the median
+ * launch.  precision M1_FP64: DFMA; M1_MIXED: FP32 FFMA.  Allocates and frees a
+ * small output buffer.  INVALID_ARG: NULL output, reps < 1 or an unknown
+ * precision; CUDA: a failed allocation, launch or event (m1_last_error). */
+m1_status m1_probe_fma_peak(int precision, void* cuda_stream, int reps, double* ops_per_s);
+
 /* ---- single-kernel entry points (one kernel on caller data, for checks) ----
  * Stateless: each call allocates its own device buffers for `desc` (lmax is
  * ignored; precision selects FP64 or FP32 arithmetic), runs one kernel on the
@@ -296,7 +309,9 @@ m1_status m1_strip_rows(int kind, int nx, int ny, int* rows);
  *                                                          (Algorithm 1)
  *   M1_OP_PSEUDO    out = one pseudo-time step with source f = rhs: explicit
  *                   limited half then one Jacobi sweep of u + dtau A(u) = u~
- *                   (Eq. (30), Algorithm 3), theta_ex = theta */
+ *                   (Eq. (30), Algorithm 3), theta_ex = theta
+ * For M1_OP_JACOBI and M1_OP_PSEUDO, *norm (if not NULL) receives the number of
+ * cells whose local E-T solve did not converge to a finite positive T. */
 enum { M1_OP_APPLY = 0, M1_OP_RESIDUAL = 1, M1_OP_FAS_RHS = 2, M1_OP_JACOBI = 3, M1_OP_PSEUDO = 4 };
 m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt, const double* sig,
                       const double* state, const double* rhs, int mode, double dtau, double theta,

@@ -936,7 +936,14 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
         M1_TRY(pack_planar(q.f, n, rhs));
         launch_sweep<R>(d, strips[0].view(), ctl, mode == M1_OP_PSEUDO, 0, 1, stream);
         M1_CK(cudaGetLastError());
-        return unpack_planar(q.u[1], n, out);
+        M1_TRY(unpack_planar(q.u[1], n, out));
+        if (norm) {
+            // cells whose local E-T solve did not converge to a finite positive T
+            Ctl c;
+            M1_CK(cudaMemcpy(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+            *norm = (double)c.newton_fail;
+        }
+        return M1_OK;
     default:
         return M1_ERR_INVALID_ARG;
     }

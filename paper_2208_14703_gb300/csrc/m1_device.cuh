@@ -6,6 +6,7 @@
 // FP32), row-major with index j*nx + i, and the opacities as Sig2 {sa, ss}.
 // In 1D ny = 1 and Fy stays zero.
 #pragma once
+#include <cfloat>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -243,40 +244,64 @@ template <> struct Quartic<float> {
         return newton_quartic_f32(C, K, Rr, ok);
     }
 };
+// FP64 Newton from T0 = min(R/C, (R/K)^(1/4)) with IEEE division and square
+// root: the path for cells where FP32 cannot seed the root (C, K or R outside
+// FP32's range, an FP32 iteration that overflowed, produced a NaN or did not
+// converge).  From T0, at or right of the root, Newton decreases monotonically.
+// ok: converged to |dT| <= 1e-15 T within 60 steps, with T finite and positive.
+static __device__ __noinline__ double newton_quartic_f64(double C, double K, double Rr, bool& ok)
+{
+    double T = Rr / C;
+    if (K > 0.0) T = fmin(T, ::sqrt(::sqrt(Rr / K)));
+    ok = false;
+    for (int it = 0; it < 60; ++it) {
+        const double T3 = T * T * T;
+        const double g = fma(K, T3 * T, C * T) - Rr;
+        const double dg = fma(4.0 * K, T3, C);
+        const double dT = g / dg;
+        T -= dT;
+        if (fabs(dT) <= 1e-15 * T) { ok = true; break; }
+    }
+    ok = ok && isfinite(T) && T > 0.0;
+    return T;
+}
+
 template <> struct Quartic<double> {
     __device__ static double solve(double C, double K, double Rr, bool& ok)
     {
         bool ok32;
-        double T = (double)newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
+        const float T32 = newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
+        // FP32 seeds only a finite positive root that its iteration reached;
+        // every comparison below is false for a NaN, which takes the FP64 path
+        if (!(ok32 && T32 > 0.0f && T32 <= FLT_MAX)) return newton_quartic_f64(C, K, Rr, ok);
+        double T = (double)T32;
         // One step of Halley's method (cubically convergent):
         // T <- T - 2 g g' / (2 g'^2 - g g'') = T - g g' / (g'^2 - 6 K T^2 g),
         // g' = C + 4 K T^3, g'' = 12 K T^2.  From the FP32 root (relative
         // error near 1e-7) it lands at FP64 rounding.  The quotient needs only
         // ~1e-14 relative accuracy (it multiplies a correction of ~1e-7 T):
-        // FP32 reciprocal estimate of the denominator plus one FP64 Newton step.
+        // FP32 reciprocal estimate of the denominator plus one FP64 Newton step,
+        // or an FP64 division where the denominator is outside FP32's normal
+        // range (g'^2 overflows FP32 for K T^3 above ~1e19).
         const double T2 = T * T;
         const double KT2 = K * T2;
         const double g = fma(KT2, T2, fma(C, T, -Rr));
         const double d1 = fma(4.0 * KT2, T, C);
         const double den = fma(d1, d1, -(6.0 * KT2) * g);
-        double r = (double)Fm<float>::rcp((float)den);
-        r = fma(r, fma(-den, r, 1.0), r);
-        double dT = g * d1 * r;
-        T -= dT;
-        if (fabs(dT) > 1e-6 * T) {
-            // the FP32 start was not close enough for one cubic step: Newton
-            for (int it = 0; it < 8; ++it) {
-                const double T3 = T * T * T;
-                const double gn = fma(K, T3 * T, C * T) - Rr;
-                const double dg = fma(4.0 * K, T3, C);
-                dT = gn * (double)Fm<float>::rcp((float)dg);
-                T -= dT;
-                if (fabs(dT) <= 1e-15 * T) break;
-            }
-            ok = fabs(dT) <= 1e-12 * T;
+        const float denf = fabsf((float)den);
+        double r;
+        if (denf >= FLT_MIN && denf <= FLT_MAX) {
+            r = (double)Fm<float>::rcp((float)den);
+            r = fma(r, fma(-den, r, 1.0), r);
         } else {
-            ok = true;
+            r = 1.0 / den;
         }
+        const double dT = g * d1 * r;
+        T -= dT;
+        // the FP32 start was not close enough for one cubic step (or the step
+        // is not a number): FP64 Newton from the FP64 start
+        if (!(fabs(dT) <= 1e-6 * T)) return newton_quartic_f64(C, K, Rr, ok);
+        ok = true;
         return T;
     }
 };

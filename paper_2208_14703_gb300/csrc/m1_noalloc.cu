@@ -158,7 +158,14 @@ m1_status scratch_for_current_device(double** out)
         set_error_text(msg);
         return M1_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return M1_ERR_INVALID_ARG;
+    if (dev < 0 || dev >= kMaxDevices) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg),
+                      "m1_residual_norm_noalloc: device %d is beyond the %d devices this "
+                      "library tracks", dev, kMaxDevices);
+        set_error_text(msg);
+        return M1_ERR_INVALID_ARG;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch[dev]) {
         void* p = nullptr;
@@ -191,14 +198,11 @@ extern "C" m1_status m1_residual_norm_noalloc(const m1_grid_desc* desc, double d
         if (desc->bc[w] < M1_BC_PERIODIC || desc->bc[w] > M1_BC_INFLOW) return M1_ERR_INVALID_ARG;
         if (desc->bc[w] == M1_BC_INFLOW && !inflow) return M1_ERR_INVALID_ARG;
     }
-    Level<double> L{};
-    L.dim = desc->dim; L.nx = desc->nx; L.ny = desc->dim == 2 ? desc->ny : 1;
-    L.n = L.nx * L.ny;
-    for (int w = 0; w < 4; ++w) L.bc[w] = desc->bc[w];
-    L.tx = desc->dim == 2 ? m1::kTx2 : m1::kTx1;
-    L.ty = desc->dim == 2 ? m1::kTy2 : 1;
-    L.tiles_x = (L.nx + L.tx - 1) / L.tx;
-    const long long tiles = (long long)L.tiles_x * ((L.ny + L.ty - 1) / L.ty);
+    // sizes in 64-bit first: the tile count is checked against the scratch
+    // before anything is narrowed to the kernels' int fields
+    const long long nx = desc->nx, ny = desc->dim == 2 ? desc->ny : 1;
+    const long long tx = desc->dim == 2 ? m1::kTx2 : m1::kTx1, ty = desc->dim == 2 ? m1::kTy2 : 1;
+    const long long tiles_x = (nx + tx - 1) / tx, tiles = tiles_x * ((ny + ty - 1) / ty);
     if (tiles > kNoallocPartials) {
         char msg[256];
         std::snprintf(msg, sizeof(msg),
@@ -207,6 +211,12 @@ extern "C" m1_status m1_residual_norm_noalloc(const m1_grid_desc* desc, double d
         set_error_text(msg);
         return M1_ERR_INVALID_ARG;
     }
+    Level<double> L{};
+    L.dim = desc->dim; L.nx = (int)nx; L.ny = (int)ny;
+    L.n = (int)(nx * ny);
+    for (int w = 0; w < 4; ++w) L.bc[w] = desc->bc[w];
+    L.tx = (int)tx; L.ty = (int)ty;
+    L.tiles_x = (int)tiles_x;
     L.tiles = (int)tiles;
     L.prof_len = L.nx > L.ny ? L.nx : L.ny;
     const double hx = desc->lx / desc->nx, hy = desc->dim == 2 ? desc->ly / desc->ny : 1.0;
@@ -221,12 +231,31 @@ extern "C" m1_status m1_residual_norm_noalloc(const m1_grid_desc* desc, double d
     m1_status st = scratch_for_current_device(&scratch);
     if (st != M1_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    k_residual_partials_planar<<<L.tiles, m1::kThreads, 0, s>>>(L, state, rhs, sig, inflow, scratch);
-    k_reduce_partials<<<1, m1::kThreads, 0, s>>>(scratch, L.tiles, norm_out);
-    cudaError_t e = cudaGetLastError();
+    // each launch reports its own error (cudaLaunchKernel returns it), so an
+    // earlier unrelated error pending on this thread is neither taken for this
+    // call's nor cleared
+    const double* p_state = state;
+    const double* p_rhs = rhs;
+    const double* p_sig = sig;
+    const double* p_inflow = inflow;
+    double* p_scratch = scratch;
+    void* args1[] = { &L, &p_state, &p_rhs, &p_sig, &p_inflow, &p_scratch };
+    cudaError_t e = cudaLaunchKernel((const void*)k_residual_partials_planar, dim3(L.tiles),
+                                     dim3(m1::kThreads), args1, 0, s);
+    const char* what = "k_residual_partials_planar";
+    if (e == cudaSuccess) {
+        const double* p_part = scratch;
+        int np = L.tiles;
+        double* p_out = norm_out;
+        void* args2[] = { &p_part, &np, &p_out };
+        e = cudaLaunchKernel((const void*)k_reduce_partials, dim3(1), dim3(m1::kThreads), args2, 0,
+                             s);
+        what = "k_reduce_partials";
+    }
     if (e != cudaSuccess) {
         char msg[256];
-        std::snprintf(msg, sizeof(msg), "m1_residual_norm_noalloc launch: %s", cudaGetErrorString(e));
+        std::snprintf(msg, sizeof(msg), "m1_residual_norm_noalloc launch of %s: %s", what,
+                      cudaGetErrorString(e));
         set_error_text(msg);
         return M1_ERR_CUDA;
     }

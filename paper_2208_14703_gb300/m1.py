@@ -41,7 +41,7 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
            "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
            "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy", "m1_autotune",
-           "m1_set_tuning", "m1_strip_rows", "m1_op_level3"]
+           "m1_set_tuning", "m1_strip_rows", "m1_op_level3", "m1_probe_fma_peak"]
 
 
 class M1Error(RuntimeError):
@@ -144,6 +144,7 @@ _lib.m1_autotune.argtypes = [_vp, ctypes.POINTER(TuneEntry), ctypes.c_int,
 _lib.m1_set_tuning.argtypes = [ctypes.POINTER(TuneEntry), ctypes.c_int]
 _lib.m1_strip_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
+_lib.m1_probe_fma_peak.argtypes = [ctypes.c_int, _vp, ctypes.c_int, _dp]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
@@ -434,6 +435,14 @@ def m1_op_level(desc, dt, sig, state, rhs=None, mode=OP_APPLY, dtau=0.0, theta=0
                           mode, dtau, theta, _ptr(out), ctypes.byref(nrm))
     _check(st, "m1_op_level")
     return out.reshape(4, desc.ny, desc.nx), nrm.value
+
+
+def probe_fma_peak(precision=FP64, stream=None, reps=5):
+    """FMA instructions per second summed over lanes (median of `reps` timed
+    launches): the FP64 (DFMA) or FP32 (FFMA) pipe ceiling of this GPU."""
+    out = ctypes.c_double()
+    _check(_lib.m1_probe_fma_peak(precision, stream, reps, ctypes.byref(out)), "m1_probe_fma_peak")
+    return out.value
 
 
 class GridDesc3(ctypes.Structure):

@@ -150,3 +150,11 @@ def test_invalid_3d_operator_arguments_rejected(lib):
         assert m1._lib.m1_op_level3(ctypes.byref(ok), dt, sig.ctypes.data, s.ctypes.data, rhs,
                                     mode, sweeps, s.ctypes.data, 0, None,
                                     ctypes.byref(ms)) == m1.ERR_INVALID_ARG
+
+
+def test_probe_rejects_bad_arguments_without_gpu(lib):
+    from paper_2208_14703_gb300 import m1
+    out = ctypes.c_double()
+    assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 0, ctypes.byref(out)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_probe_fma_peak(7, None, 3, ctypes.byref(out)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 3, None) == m1.ERR_INVALID_ARG

@@ -174,3 +174,62 @@ def test_full_size_sweep_matches_oracle():
     got, _ = m1.m1_op_level(desc, case["dt"], sig, v1, b, mode=m1.OP_JACOBI)
     ref, _ = O.jacobi_sweep(g, case["dt"], case["sa"], case["ss"], b, v1)
     _close(got, ref, 1e-12)
+
+
+def _extreme_case(kind, nx=40, ny=24, seed=17):
+    """Admissible states far outside the nondimensional range: a hot gas (T up
+    to 1e9, E = a_r T^4 up to 1e36, opacities up to 1e4: K T^3 and g'^2 of the
+    local quartic overflow FP32) or a cold one (T from 1e-44 to 1e-39, E from
+    1e-120 to 1e-100: the quartic's right-hand side and root are below FP32's
+    normal range; E stays where |F|^2 is an FP64 normal number, which the
+    oracle's closure needs)."""
+    rng = np.random.default_rng(seed)
+    if kind == "hot":
+        T = 10.0 ** rng.uniform(5.0, 9.0, (ny, nx))
+        E = T ** 4 * rng.uniform(0.5, 2.0, (ny, nx))
+    else:
+        T = 10.0 ** rng.uniform(-44.0, -39.0, (ny, nx))
+        E = 10.0 ** rng.uniform(-120.0, -100.0, (ny, nx))
+    th = rng.uniform(0, 2 * np.pi, (ny, nx))
+    f = rng.uniform(0, 0.9, (ny, nx))
+    state = np.stack([E, f * E * np.cos(th), f * E * np.sin(th), T * rng.uniform(0.8, 1.2, (ny, nx))])
+    sa = 10.0 ** rng.uniform(0.0, 4.0, (ny, nx))
+    ss = 10.0 ** rng.uniform(-2.0, 2.0, (ny, nx))
+    desc = dict(dim=2, nx=nx, ny=ny, lx=1.0, ly=ny / nx, bc=["reflect"] * 4, c=1.0, a_r=1.0,
+                c_v=1.0)
+    return dict(desc=desc, dt=10.0 / nx, state=state, sa=sa, ss=ss, inflow=None, lmax=1, tol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["hot", "cold"])
+def test_local_solve_outside_fp32_range(kind):
+    """The FP64 local solve seeds Newton in FP32 only where FP32 can represent the
+    quartic; elsewhere it solves in FP64.  One Jacobi sweep matches the oracle
+    cell by cell and no local solve is reported as failed."""
+    case = _extreme_case(kind)
+    g = O.Grid.from_case(case)
+    desc = m1.desc_from_case(case, lmax=1)
+    sig = np.stack([case["sa"], case["ss"]])
+    b = O.rhs_of(g, case["state"])
+    v1, it = O.jacobi_sweep(g, case["dt"], case["sa"], case["ss"], b, case["state"])
+    assert it >= 0
+    ref, it = O.jacobi_sweep(g, case["dt"], case["sa"], case["ss"], b, v1)
+    assert it >= 0
+    got, fails = m1.m1_op_level(desc, case["dt"], sig, v1, b, mode=m1.OP_JACOBI)
+    assert fails == 0
+    assert np.all(np.isfinite(got))
+    # per cell: E and T relative to themselves, the flux relative to E
+    errE = np.abs(got[0] - ref[0]) / ref[0]
+    errF = np.hypot(got[1] - ref[1], got[2] - ref[2]) / ref[0]
+    errT = np.abs(got[3] - ref[3]) / ref[3]
+    assert max(errE.max(), errF.max(), errT.max()) <= 1e-12, (errE.max(), errF.max(), errT.max())
+
+
+def test_fma_peak_probe():
+    """The FP64 FMA probe measures a rate below the nominal pipe ceiling (152 SMs
+    x 2 DFMA per clock x the maximum SM clock, 2.07 GHz on GB300) and well above a
+    tenth of it; the FP32 rate is many times the FP64 one."""
+    f64 = m1.probe_fma_peak(m1.FP64, reps=3)
+    f32 = m1.probe_fma_peak(m1.MIXED, reps=3)
+    nominal = 152 * 2 * 2.07e9
+    assert 0.1 * nominal < f64 <= 1.02 * nominal, f64
+    assert f32 > 20 * f64, (f32, f64)
