@@ -24,10 +24,27 @@
  * index (k*ny + j)*nx + i.  Inflow profiles: [6 walls][E, Fx, Fy, Fz][F] with
  * F = the largest face (max of ny*nz, nx*nz, nx*ny); the face of a wall on axis d
  * is indexed q_b * n_a + q_a over its two other axes a < b.
+ *
+ * Threads: as in the 2D oracle, the outer cell loops carry OpenMP pragmas that
+ * the plain build ignores; the all-core build (-fopenmp) gives bit-for-bit the
+ * same results (integer reductions only, the norm summed serially).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads the cell loops run on: 1 in the plain build. */
+int ora3_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NEUMANN = 2, BC_INFLOW = 3 };
 enum { KIND_STATE = 0, KIND_DIFF = 1 };
@@ -224,6 +241,7 @@ void ora3_apply_A(const int* idesc, const double* ddesc, const double* inflow, d
                   const double* sa, const double* ss, const double* v, double* out)
 {
     grid3_t g; grid_from_desc(&g, idesc, ddesc, inflow);
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int k = 0; k < g.n[2]; ++k)
         for (int j = 0; j < g.n[1]; ++j)
             for (int i = 0; i < g.n[0]; ++i)
@@ -234,6 +252,7 @@ static void residual(const grid3_t* g, double dt, const double* sa, const double
                      const double* b, const double* v, double* r)
 {
     size_t n = ncell(g);
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
@@ -310,7 +329,8 @@ static int jacobi_sweep(const grid3_t* g, double dt, const double* sa, const dou
                         const double* rhs, const double* vin, double* vout, double w0, double w1)
 {
     double diag = transport_diag(g, dt);
-    int worst = 0;
+    int fail = 0, maxit = 0;
+    #pragma omp parallel for collapse(3) schedule(static) reduction(|:fail) reduction(max:maxit)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
@@ -323,11 +343,11 @@ static int jacobi_sweep(const grid3_t* g, double dt, const double* sa, const dou
                 beta[4] = b.T;
                 int it = local_solve(w0, w1, diag, g->c * dt * sa[q], g->c * dt * (sa[q] + ss[q]),
                                      g->c_v, g->a_r, beta, out);
-                if (it < 0) worst = -1; else if (worst >= 0 && it > worst) worst = it;
+                if (it < 0) fail = 1; else if (it > maxit) maxit = it;
                 cell5_t o = { out[0], { out[1], out[2], out[3] }, out[4] };
                 store(g, vout, i, j, k, o);
             }
-    return worst;
+    return fail ? -1 : maxit;
 }
 
 int ora3_jacobi_sweep(const int* idesc, const double* ddesc, const double* inflow, double dt,
@@ -383,6 +403,7 @@ static int pseudo_time_smooth(const grid3_t* g, double dt, const double* sa, con
     double* w2 = malloc(NF * n * sizeof(double));
     int worst = 0;
     for (int it = 0; it < m; ++it) {
+        #pragma omp parallel for collapse(3) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -460,6 +481,7 @@ static void restrict_state(const grid3_t* gf, const grid3_t* gc, const double* f
                            int kind)
 {
     static const double w[3] = { 0.25, 0.5, 0.25 };
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int kc = 0; kc < gc->n[2]; ++kc)
         for (int jc = 0; jc < gc->n[1]; ++jc)
             for (int ic = 0; ic < gc->n[0]; ++ic) {
@@ -481,6 +503,7 @@ static void restrict_state(const grid3_t* gf, const grid3_t* gc, const double* f
 static void restrict_scalar(const grid3_t* gf, const grid3_t* gc, const double* fine, double* coarse)
 {
     static const double w[3] = { 0.25, 0.5, 0.25 };
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int kc = 0; kc < gc->n[2]; ++kc)
         for (int jc = 0; jc < gc->n[1]; ++jc)
             for (int ic = 0; ic < gc->n[0]; ++ic) {
@@ -529,6 +552,7 @@ void ora3_prolong(const int* idesc_f, const double* ddesc_f, const double* inflo
 {
     grid3_t gf, gc; grid_from_desc(&gf, idesc_f, ddesc_f, NULL); coarse_desc(&gf, &gc);
     set_inflow(&gc, inflow_c);
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int k = 0; k < gf.n[2]; ++k)
         for (int j = 0; j < gf.n[1]; ++j)
             for (int i = 0; i < gf.n[0]; ++i)
@@ -544,6 +568,7 @@ static int prolong_correct(const grid3_t* gc, const grid3_t* gf, const double* u
     double* e = malloc(NF * nc * sizeof(double));
     for (size_t q = 0; q < NF * nc; ++q) e[q] = uc[q] - vc[q];
     int damped = 0;
+    #pragma omp parallel for collapse(3) schedule(static) reduction(+:damped)
     for (int k = 0; k < gf->n[2]; ++k)
         for (int j = 0; j < gf->n[1]; ++j)
             for (int i = 0; i < gf->n[0]; ++i) {
@@ -614,6 +639,7 @@ static void fas_rhs(level3_t* q, double dt)
 {
     size_t n = ncell(&q->g);
     double* a = malloc(NF * n * sizeof(double));
+    #pragma omp parallel for collapse(3) schedule(static)
     for (int k = 0; k < q->g.n[2]; ++k)
         for (int j = 0; j < q->g.n[1]; ++j)
             for (int i = 0; i < q->g.n[0]; ++i)

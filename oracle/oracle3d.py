@@ -26,23 +26,54 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+LIB_OMP = os.path.join(HERE, "liboracle3d_omp.so")
+_FLAGS = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC"]
+
+
 def build(force: bool = False) -> str:
-    """Compile the 3D oracle with gcc (plain C99, no contraction so x86 and Arm agree)."""
+    """Compile the 3D oracle with gcc (plain C99, no contraction so x86 and Arm
+    agree), and its all-core OpenMP build when the compiler supports it."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC",
-                        "-o", LIB, SRC, "-lm"], check=True)
+        subprocess.run(_FLAGS + ["-o", LIB, SRC, "-lm"], check=True)
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(LIB_OMP) < os.path.getmtime(SRC):
+        subprocess.run(_FLAGS + ["-fopenmp", "-o", LIB_OMP, SRC, "-lm"], check=False,
+                       stderr=subprocess.DEVNULL)
     return LIB
 
 
 _LIB = None
+_LIBS = {}
+
+
+def _load(path):
+    if path not in _LIBS:
+        L = ctypes.CDLL(path)
+        L.ora3_norm.restype = ctypes.c_double
+        L.ora3_threads.restype = ctypes.c_int
+        _LIBS[path] = L
+    return _LIBS[path]
 
 
 def lib():
     global _LIB
     if _LIB is None:
-        _LIB = ctypes.CDLL(build())
-        _LIB.ora3_norm.restype = ctypes.c_double
+        build()
+        _LIB = _load(LIB)
     return _LIB
+
+
+def have_all_cores() -> bool:
+    build()
+    return os.path.exists(LIB_OMP)
+
+
+def use_all_cores(on: bool = True) -> int:
+    """Route every call of this module to the all-core (OpenMP) build of the
+    same source (on) or the one-core build (off).  Returns the thread count."""
+    global _LIB
+    build()
+    _LIB = _load(LIB_OMP if on and os.path.exists(LIB_OMP) else LIB)
+    return int(_LIB.ora3_threads())
 
 
 def _f64(a):

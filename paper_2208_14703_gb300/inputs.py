@@ -111,6 +111,75 @@ def hot_square_2d(n: int = 1024, cfl: float = 100.0, lmax: int = 8, tol: float =
                 ss=lognormal_opacity(n, n, seed_s), inflow=None, lmax=lmax, tol=tol)
 
 
+def gaussian_field_3d(nx: int, ny: int, nz: int, seed: int, corr: float = 8.0) -> np.ndarray:
+    """Unit-variance, zero-mean Gaussian random field on a periodic 3D grid
+    (white noise smoothed by a Gaussian filter by FFT), shape (nz, ny, nx)."""
+    w = normal(seed, nx * ny * nz).reshape(nz, ny, nx)
+    kx, ky, kz = np.fft.fftfreq(nx), np.fft.fftfreq(ny), np.fft.fftfreq(nz)
+    k2 = kx[None, None, :] ** 2 + ky[None, :, None] ** 2 + kz[:, None, None] ** 2
+    g = np.real(np.fft.ifftn(np.fft.fftn(w) * np.exp(-0.5 * (2 * np.pi * corr) ** 2 * k2)))
+    g -= g.mean()
+    s = g.std()
+    return g / s if s > 0 else g
+
+
+def lognormal_opacity_3d(nx: int, ny: int, nz: int, seed: int, corr: float = 8.0,
+                         lo: float = -2.0, hi: float = 4.0) -> np.ndarray:
+    return 10.0 ** np.clip(1.0 + 3.0 * gaussian_field_3d(nx, ny, nz, seed, corr), lo, hi)
+
+
+def _desc3(nx, ny, nz, lx, ly, lz, bc, c=1.0, a_r=1.0, c_v=1.0):
+    return dict(dim=3, nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz, bc=list(bc), c=c, a_r=a_r,
+                c_v=c_v)
+
+
+def hot_cube_3d(n: int = 128, cfl: float = 100.0, lmax: int = 5, tol: float = 1e-8,
+                seed_a: int = 21, seed_s: int = 22, bc=("reflect",) * 6) -> dict:
+    """3D counterpart of the 2D plain-FP64 workload: n^3 cells on [0,1]^3,
+    lognormal sigma_a, sigma_s (the 2D recipe on a 3D random field), T_g = 1 with
+    a centred hot cube of side 1/8 at T_g = 4, E = a_r T_g^4, F = 0, reflecting
+    walls (x low, x high, y low, y high, z low, z high), dt = cfl * h / c.
+    State: float64 (5, n, n, n) planes E, Fx, Fy, Fz, T; opacities (n, n, n)."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    hot = (np.abs(X - 0.5) < 1 / 16) & (np.abs(Y - 0.5) < 1 / 16) & (np.abs(Z - 0.5) < 1 / 16)
+    T = np.where(hot, 4.0, 1.0)
+    state = np.zeros((5, n, n, n))
+    state[0] = T ** 4
+    state[4] = T
+    return dict(desc=_desc3(n, n, n, 1.0, 1.0, 1.0, bc), dt=cfl * h, state=state,
+                sa=lognormal_opacity_3d(n, n, n, seed_a), ss=lognormal_opacity_3d(n, n, n, seed_s),
+                inflow=None, lmax=lmax, tol=tol)
+
+
+def beam_3d(n: int = 32, cfl: float = 100.0, lmax: int = 3, tol: float = 1e-8,
+            seed_a: int = 23, seed_s: int = 24) -> dict:
+    """3D beam: an f = 1 beam (E = 1, F = (c, 0, 0)) enters through the x-low
+    wall into a square channel |y - 1/2|, |z - 1/2| <= 1/16 (sigma = 1e-2) cut
+    through the lognormal medium; the rest of that wall holds E = 1, F = 0;
+    the other walls reflect.  Background T_g = 1, E = 1, F = 0.  inflow: float64
+    (6 walls, 4 fields E, Fx, Fy, Fz, largest face) with the x-low face indexed
+    z * n + y."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    chan = np.abs(x - 0.5) <= 1 / 16
+    sa = lognormal_opacity_3d(n, n, n, seed_a)
+    ss = lognormal_opacity_3d(n, n, n, seed_s)
+    box = chan[None, :, None] & chan[:, None, None]          # (z, y, any x)
+    box = np.broadcast_to(box, (n, n, n))
+    sa[box] = 1e-2
+    ss[box] = 1e-2
+    face = np.zeros((6, 4, n * n))
+    face[0, 0] = 1.0
+    face[0, 1] = (chan[:, None] & chan[None, :]).reshape(-1).astype(float)   # (z, y) -> z * n + y
+    state = np.zeros((5, n, n, n))
+    state[0] = 1.0
+    state[4] = 1.0
+    return dict(desc=_desc3(n, n, n, 1.0, 1.0, 1.0, ["inflow"] + ["reflect"] * 5), dt=cfl * h,
+                state=state, sa=sa, ss=ss, inflow=face, lmax=lmax, tol=tol)
+
+
 def beam_channel_2d(n: int = 4096, cfl: float = 100.0, lmax: int = 10, tol: float = 1e-8,
                     seed_a: int = 3, seed_s: int = 4) -> dict:
     """2D beam: an f = 1 beam (E = 1, F = (c, 0)) enters through the west wall

@@ -68,3 +68,21 @@ def test_kernels_bitwise_equal(both):
     a, b2, _ = both(run)
     for x, y in zip(a, b2):
         np.testing.assert_array_equal(x, y)
+
+
+def test_3d_step_bitwise_equal():
+    from oracle import oracle3d as O3
+    case = inputs.beam_3d(16, lmax=3)
+    n = 16
+    g = O3.Grid3(n, n, n, 1 / n, 1 / n, 1 / n, tuple(case["desc"]["bc"]), inflow=case["inflow"])
+    p = O3.SolveParams3(lmax=3, tol=1e-8, cycle=1)
+    O3.use_all_cores(False)
+    a = O3.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"], p)
+    assert O3.use_all_cores(True) >= 1
+    try:
+        b = O3.implicit_step(g, case["dt"], case["sa"], case["ss"], case["state"], p)
+    finally:
+        O3.use_all_cores(False)
+    assert a[1] == b[1]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2], b[2])
