@@ -363,6 +363,43 @@ def bench_sweep3d(m1, stream, n=256, sweeps=2):
                          "frac": tops / FP64_PEAK_TOPS, "ops_per_cell": SWEEP3D_OPS}}
 
 
+def bench_step3d(m1, stream, n=128, lmax=5, fp64_peak=None):
+    """One implicit step in 3D (Algorithm 4 on a 3D hierarchy): the n^3 hot cube
+    (lognormal opacities, reflecting walls, CFL 100, L_max = 5, tol 1e-8),
+    one untimed then one timed step (the state reset in between), and the fine
+    Jacobi sweep of that grid (closure pass + operator pass) against the FP64
+    pipe's ceiling (SWEEP3D_OPS per cell-update)."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    case = inputs.hot_cube_3d(n, lmax=lmax)
+    g = m1.grid3_from_case(case, stream=stream.cuda_stream)
+    params = m1.m1_default_params(tol=case["tol"])
+    sig = np.stack([case["sa"], case["ss"]])
+    g.implicit_step(case["dt"], params)
+    g.set_state(case["state"], sig)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    st = g.implicit_step(case["dt"], params)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = g.get_state()
+    g.close()
+    cells = n ** 3
+    sweep = bench_sweep3d(m1, stream, n=n)
+    peak = fp64_peak or FP64_PEAK_TOPS
+    tops = SWEEP3D_OPS * cells / (sweep["ms_per_sweep"] * 1e-3) / 1e12
+    return {"workload": f"m1-implicit-step-3d-fp64-{n}^3-lmax{lmax}-tol1e-8", "cells": cells,
+            "cycles": st.cycles, "ms_per_step": ms, "ms_per_cycle": ms / max(st.cycles, 1),
+            "cell_updates_per_s": cells * st.sweeps / (ms * 1e-3),
+            "launches_per_cycle": (st.launches - 5) / max(st.cycles, 1),
+            "admissible": bool(np.all(out[0] > 0) and np.all(out[4] > 0)),
+            "fine_sweep": {"ms": sweep["ms_per_sweep"], "bound": "alu", "achieved": tops,
+                           "peak": peak, "unit": "Top/s", "frac": tops / peak,
+                           "ops_per_cell": SWEEP3D_OPS}}
+
+
 def bench_cycle_shapes(m1, case, stream, s0, flush):
     """Cycles to tolerance and step time of the same workload with V-, W- and
     F-cycles (Section 6.3 names W and F as the alternatives), FP64 and mixed:
@@ -739,6 +776,7 @@ def main():
         ora = None if args.no_oracle_errors else start_oracle_step()
         extras["cycle_shapes"] = bench_cycle_shapes(m1, case, stream, s0, flush)
         extras["sweep3d"] = bench_sweep3d(m1, stream)
+        extras["step3d"] = bench_step3d(m1, stream, fp64_peak=fp64_peak)
         extras["paper_beam"] = bench_paper_beam(m1, stream)
         extras["paper_riemann"] = bench_paper_riemann(m1, stream)
         mixed = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps, pk["hbm_gbs"])

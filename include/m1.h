@@ -317,10 +317,10 @@ m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt,
                       const double* state, const double* rhs, int mode, double dtau, double theta,
                       double* out, double* norm);
 
-/* ---- 3D single-level operators (the first GPU step of a 3D path) ----
+/* ---- 3D single-level operators (one pass on caller data, for checks) ----
  * A 3D grid of nx x ny x nz cells on [0,lx] x [0,ly] x [0,lz]; walls bc[6] =
  * (x low, x high, y low, y high, z low, z high), each periodic, reflecting or
- * Neumann (no inflow walls in 3D).  States are planar [5][nz*ny*nx] doubles
+ * Neumann (m1_op_level3 takes no inflow wall; the 3D grids below do).  States are planar [5][nz*ny*nx] doubles
  * (E, Fx, Fy, Fz, T; index (k*ny + j)*nx + i), opacities [2][nz*ny*nx]
  * (sigma_a, sigma_s).  The operator is the 2D one on three axes: the Rusanov
  * faces of Eq. (6) with the 3x3 closure of Eq. (5), transport diagonal
@@ -346,6 +346,49 @@ enum { M1_OP3_APPLY = 0, M1_OP3_RESIDUAL = 1, M1_OP3_JACOBI = 2 };
 m1_status m1_op_level3(const m1_grid3_desc* desc, double dt, const double* sig,
                        const double* state, const double* rhs, int mode, int sweeps,
                        double* out, int on_device, void* cuda_stream, double* ms);
+
+/* ---- 3D grids: one implicit step of Algorithm 4 (Appendix A) in three
+ * dimensions.  Section 4.2 writes the transfers for d = 1, 2, 3 (R = 2^-d P^T);
+ * the operator, closure, sources, local solve, pseudo-time smoother, damping,
+ * norm and dtau_im control are those of the 2D grid on three axes (Rusanov
+ * faces of Eq. (6) on x, y and z, the 3x3 closure of Eq. (5), 27-point full
+ * weighting, tensor-product prolongation with the damping of Eq. (34)).  FP64.
+ *
+ * m1_create_grid3: levels 0 .. lmax-1 of `desc` (lmax counts the grids; nx, ny
+ *   and nz divisible by 2^(lmax-1)) on the current device; every wall periodic
+ *   (in pairs), reflecting, Neumann or inflow; cuda_stream NULL: a stream of its
+ *   own.  INVALID_ARG: sizes, lengths or constants out of range, an unknown or
+ *   unpaired periodic wall, more than 2^31 cells; OOM.
+ * m1_grid3_set_state: v^n from planar [5][nz*ny*nx] doubles (E, Fx, Fy, Fz, T;
+ *   index (k*ny + j)*nx + i) and opacities [2][nz*ny*nx] (sigma_a, sigma_s),
+ *   host arrays (on_device = 0) or device arrays on the grid's stream (1); both
+ *   are copied.  NONADMISSIBLE_INPUT: some E <= 0, T <= 0, |F| > c E, negative
+ *   opacity or non-finite value (the state is then not usable for a step).
+ * m1_grid3_set_inflow: the prescribed E, Fx, Fy, Fz of every inflow wall's face
+ *   cells, host array [6 walls][4 fields][F], F = max(ny*nz, nx*nz, nx*ny), the
+ *   face of a wall on axis d indexed b * n_a + a over its two other axes a < b;
+ *   T of an inflow ghost is the mirror cell's.  Coarse levels take the
+ *   full-weighting restriction of the face (1/4, 1/2, 1/4, ends copied) along
+ *   each tangential axis.  Required before a step when a wall is an inflow wall;
+ *   INVALID_ARG when none is.
+ * m1_grid3_get_state: the current state into planar [5][nz*ny*nx] (host or device).
+ * m1_grid3_implicit_step: v^n -> v^{n+1} in place, V-, W- or F-cycles to
+ *   ||r|| <= tol ||r_0|| (params NULL: the defaults of m1_default_params;
+ *   nu_l must be 1); stats as for m1_implicit_step.  NOT_CONVERGED after
+ *   max_cycles (the last iterate kept); INVALID_ARG: dt <= 0, bad parameters,
+ *   no state set, or a missing inflow profile.
+ * m1_grid3_step_history: ||r_kappa|| for kappa = 0 .. cycles and the dtau_im of
+ *   each cycle of the last step (first `len` entries).
+ * A grid is used by one thread and stream at a time. */
+typedef struct m1_grid3* m1_grid3_t;
+m1_status m1_create_grid3(const m1_grid3_desc* desc, int lmax, void* cuda_stream, m1_grid3_t* out);
+m1_status m1_destroy_grid3(m1_grid3_t g);
+m1_status m1_grid3_set_state(m1_grid3_t g, const double* state, const double* sig, int on_device);
+m1_status m1_grid3_set_inflow(m1_grid3_t g, const double* faces);
+m1_status m1_grid3_get_state(m1_grid3_t g, double* state, int on_device);
+m1_status m1_grid3_implicit_step(m1_grid3_t g, double dt, const m1_solve_params* params,
+                                 m1_step_stats* stats);
+m1_status m1_grid3_step_history(m1_grid3_t g, double* hist, double* dtau, int len);
 
 /* Full weighting (Section 4.2, Eq. (21)/(22)) of a fine state (STATE ghosts) and
  * a fine residual (DIFF ghosts: zero at inflow walls) to the coarse grid

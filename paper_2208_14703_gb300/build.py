@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libm1.so")
 
 SOURCES = ["m1_kernels.cu", "m1_api.cu", "m1_serve.cu", "m1_tune.cu", "m1_noalloc.cu", "m1_3d.cu",
-           "m1_probe.cu"]
+           "m1_probe.cu", "m1_grid3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]

@@ -41,7 +41,9 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_batch_set_state", "m1_batch_set_inflow", "m1_batch_get_state",
            "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
            "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy", "m1_autotune",
-           "m1_set_tuning", "m1_strip_rows", "m1_op_level3", "m1_probe_fma_peak"]
+           "m1_set_tuning", "m1_strip_rows", "m1_op_level3", "m1_probe_fma_peak",
+           "m1_create_grid3", "m1_destroy_grid3", "m1_grid3_set_state", "m1_grid3_set_inflow",
+           "m1_grid3_get_state", "m1_grid3_implicit_step", "m1_grid3_step_history"]
 
 
 class M1Error(RuntimeError):
@@ -463,6 +465,14 @@ def make_desc3(nx, ny, nz, lx, ly, lz, bc=("periodic",) * 6, c=1.0, a_r=1.0, c_v
 
 _lib.m1_op_level3.argtypes = [ctypes.POINTER(GridDesc3), ctypes.c_double, _vp, _vp, _vp,
                               ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _dp]
+_lib.m1_create_grid3.argtypes = [ctypes.POINTER(GridDesc3), ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.m1_destroy_grid3.argtypes = [_vp]
+_lib.m1_grid3_set_state.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_lib.m1_grid3_set_inflow.argtypes = [_vp, _vp]
+_lib.m1_grid3_get_state.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.m1_grid3_implicit_step.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(SolveParams),
+                                        ctypes.POINTER(StepStats)]
+_lib.m1_grid3_step_history.argtypes = [_vp, _vp, _vp, ctypes.c_int]
 
 
 def m1_op_level3(desc, dt, sig, state, rhs=None, mode=OP3_APPLY, sweeps=1, out=None,
@@ -482,6 +492,73 @@ def m1_op_level3(desc, dt, sig, state, rhs=None, mode=OP3_APPLY, sweeps=1, out=N
     if not on_device:
         out = out.reshape(5, desc.nz, desc.ny, desc.nx)
     return out, ms.value
+
+
+class Grid3:
+    """Owner of one m1_grid3_t: the implicit step in 3D (m1_create_grid3 ...)."""
+
+    def __init__(self, desc: GridDesc3, lmax: int, stream=None):
+        h = _vp()
+        _check(_lib.m1_create_grid3(ctypes.byref(desc), lmax, stream, ctypes.byref(h)),
+               "m1_create_grid3")
+        self.h = h
+        self.desc = desc
+        self.lmax = lmax
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.m1_destroy_grid3(self.h)
+            self.h = None
+
+    __del__ = close
+
+    @property
+    def shape(self):
+        return (5, self.desc.nz, self.desc.ny, self.desc.nx)
+
+    def set_state(self, state, sig, on_device=False):
+        """state: planar (5, nz, ny, nx) E, Fx, Fy, Fz, T; sig: (2, nz, ny, nx)."""
+        if not on_device:
+            state, sig = _host(state), _host(sig)
+        return _check(_lib.m1_grid3_set_state(self.h, _ptr(state), _ptr(sig), int(on_device)),
+                      "m1_grid3_set_state")
+
+    def set_inflow(self, faces):
+        """faces: (6 walls, 4 fields E, Fx, Fy, Fz, largest face) host array."""
+        return _check(_lib.m1_grid3_set_inflow(self.h, _ptr(_host(faces))), "m1_grid3_set_inflow")
+
+    def get_state(self, out=None, on_device=False):
+        if out is None:
+            out = np.zeros(self.shape)
+        _check(_lib.m1_grid3_get_state(self.h, _ptr(out), int(on_device)), "m1_grid3_get_state")
+        return out
+
+    def implicit_step(self, dt, params: SolveParams | None = None, allow_not_converged=False):
+        stats = StepStats()
+        st = _lib.m1_grid3_implicit_step(self.h, dt, ctypes.byref(params) if params else None,
+                                         ctypes.byref(stats))
+        _check(st, "m1_grid3_implicit_step",
+               allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return stats
+
+    def step_history(self, length):
+        hist = np.zeros(length)
+        dtau = np.zeros(length)
+        _check(_lib.m1_grid3_step_history(self.h, _ptr(hist), _ptr(dtau), length),
+               "m1_grid3_step_history")
+        return hist, dtau
+
+
+def grid3_from_case(case, lmax=None, stream=None):
+    """A Grid3 holding a 3D case of inputs.py (state, opacities and inflow set)."""
+    d = case["desc"]
+    g = Grid3(make_desc3(d["nx"], d["ny"], d["nz"], d["lx"], d["ly"], d["lz"], tuple(d["bc"]),
+                         d["c"], d["a_r"], d["c_v"]),
+              case["lmax"] if lmax is None else lmax, stream)
+    g.set_state(case["state"], np.stack([case["sa"], case["ss"]]))
+    if case.get("inflow") is not None:
+        g.set_inflow(case["inflow"])
+    return g
 
 
 def m1_op_restrict(desc, state, resid, inflow=None):

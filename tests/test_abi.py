@@ -158,3 +158,19 @@ def test_probe_rejects_bad_arguments_without_gpu(lib):
     assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 0, ctypes.byref(out)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_probe_fma_peak(7, None, 3, ctypes.byref(out)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 3, None) == m1.ERR_INVALID_ARG
+
+
+def test_grid3_validation_without_gpu(lib):
+    from paper_2208_14703_gb300 import m1
+    h = ctypes.c_void_p()
+    ok = m1.make_desc3(16, 16, 16, 1.0, 1.0, 1.0, ("reflect",) * 6)
+    for lmax in (0, 6, 21):          # 16 is not divisible by 2^5; out of range
+        assert m1._lib.m1_create_grid3(ctypes.byref(ok), lmax, None, ctypes.byref(h)) == \
+            m1.ERR_INVALID_ARG
+    bad = m1.make_desc3(16, 16, 16, 1.0, 1.0, 1.0, ("periodic", "reflect") + ("reflect",) * 4)
+    assert m1._lib.m1_create_grid3(ctypes.byref(bad), 2, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    bad = m1.make_desc3(16, 16, 16, 0.0, 1.0, 1.0, ("reflect",) * 6)
+    assert m1._lib.m1_create_grid3(ctypes.byref(bad), 2, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_create_grid3(None, 2, None, ctypes.byref(h)) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_destroy_grid3(None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_grid3_implicit_step(None, 0.1, None, None) == m1.ERR_INVALID_ARG
