@@ -47,10 +47,12 @@ __global__ void __launch_bounds__(kThreads3) k_closure3(G3 g, const EF* __restri
 
 // One cell-parallel pass: the neighbour terms of Eq. (9) on the three axes, then
 // A(u) = D(u) - N (APPLY), b - A(u) (RESID, with the cell's norm contribution),
-// A(u) + b (FAS, Eq. (24)), the Jacobi update D^{-1}(b + N) (JACOBI, Eq. (10)),
-// or one pseudo-time step with source f = b (PSEUDO, Eq. (30)): the explicit
-// half u~ = u + tau f, tau = min(dtau, theta tau*) (tau* the largest admissible
-// step along f), then one Jacobi sweep of u' + dtau A(u') = u~ from u.
+// A(u) + b (FAS, Eq. (24)), the Jacobi update D^{-1}(b + N) (JACOBI, Eq. (10);
+// JACOBI_NORM also forms the norm contribution of b - A(u) = (b + N) - D(u) of
+// its input, with the residual's expressions), or one pseudo-time step with
+// source f = b (PSEUDO, Eq. (30)): the explicit half u~ = u + tau f,
+// tau = min(dtau, theta tau*) (tau* the largest admissible step along f), then
+// one Jacobi sweep of u' + dtau A(u') = u~ from u.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads3) k_op3(G3 g, const EF* __restrict__ u,
                                                    const double* __restrict__ T,
@@ -116,10 +118,22 @@ __global__ void __launch_bounds__(kThreads3) k_op3(G3 g, const EF* __restrict__ 
             bool ok;
             EF o;
             double oT;
-            if (MODE == OP3K_JACOBI) {
+            if (MODE == OP3K_JACOBI || MODE == OP3K_JACOBI_NORM) {
                 bE = bb.E + N[0];
                 for (int m = 0; m < 3; ++m) bF[m] = bb.F[m] + N[1 + m];
                 bTq = bT[q];
+                if (MODE == OP3K_JACOBI_NORM) {
+                    const double T2 = Tc * Tc;
+                    const double src = ka * (uc.E - g.a_r * T2 * T2);
+                    const double rE = bb.E - (g.diag * uc.E + src - N[0]);
+                    double rF2 = 0.0;
+                    for (int m = 0; m < 3; ++m) {
+                        const double rF = bb.F[m] - ((g.diag + kt) * uc.F[m] - N[1 + m]);
+                        rF2 += rF * rF;
+                    }
+                    const double rT = bTq - (g.c_v * Tc - src);
+                    nrm += rE * rE + rF2 * g.ic2 + rT * rT;
+                }
                 local_solve3(0.0, 1.0, g, ka, kt, bE, bF, bTq, o, oT, ok);
             } else {
                 const double fT = bT[q];
@@ -134,9 +148,9 @@ __global__ void __launch_bounds__(kThreads3) k_op3(G3 g, const EF* __restrict__ 
             outT[q] = oT;
         }
     }
-    if ((MODE == OP3K_JACOBI || MODE == OP3K_PSEUDO) && fails && ctl)
+    if ((MODE == OP3K_JACOBI || MODE == OP3K_JACOBI_NORM || MODE == OP3K_PSEUDO) && fails && ctl)
         atomicAdd(&ctl->newton_fail, fails);
-    if (MODE == OP3K_RESID && part) {
+    if ((MODE == OP3K_RESID || MODE == OP3K_JACOBI_NORM) && part) {
         const double s = block_sum3(nrm, red);
         if (threadIdx.x == 0) part[blockIdx.x] = s * g.vol;
     }
@@ -322,7 +336,9 @@ __device__ void mark_done3(Ctl* ctl, BatchCtl* bctl, int status)
 // One block: the fixed-order sum of the norm partials, then the control logic
 // of Algorithm 4 (the rules of the 2D path): INIT records ||r_0|| and ||b|| and
 // stops at once below the rounding floor; CYCLE counts the cycle, records the
-// residual, stops at tol ||r_0|| or max_cycles, else updates dtau_im.
+// residual, stops at tol ||r_0|| or max_cycles, else updates dtau_im.  DEFER is
+// CYCLE for a norm formed by the next cycle's first sweep: the first one of a
+// step (the norm of v^n again, flagged by INIT) is skipped.
 __global__ void __launch_bounds__(kThreads3) k_finalize3(Ctl* __restrict__ ctl,
                                                          BatchCtl* __restrict__ bctl,
                                                          const double* __restrict__ part,
@@ -331,6 +347,14 @@ __global__ void __launch_bounds__(kThreads3) k_finalize3(Ctl* __restrict__ ctl,
 {
     __shared__ double red[kThreads3];
     if (mode != FIN3_INIT && ctl->done) return;
+    if (mode == FIN3_DEFER) {
+        const int first = ctl->pending_r0;
+        __syncthreads();
+        if (first) {
+            if (threadIdx.x == 0) ctl->pending_r0 = 0;
+            return;
+        }
+    }
     double a = 0.0, b = 0.0;
     for (int k = threadIdx.x; k < np; k += blockDim.x) a += part[k];
     const double s = block_sum3(a, red);
@@ -348,6 +372,7 @@ __global__ void __launch_bounds__(kThreads3) k_finalize3(Ctl* __restrict__ ctl,
         ctl->dtau = ctl->dtau0;
         ctl->kappa = 0;
         ctl->status = CTL_NOT_CONVERGED;
+        ctl->pending_r0 = 1;
         if (ctl->hist_len > 0) ctl->hist[0] = res;
         if (res <= ctl->res0_floor * ctl->bnorm) mark_done3(ctl, bctl, CTL_OK);
         return;
@@ -443,6 +468,10 @@ void launch3_op(int mode, const G3& g, const EF* u, const double* uT, const P6* 
         break;
     case OP3K_JACOBI:
         k_op3<OP3K_JACOBI><<<nb, kThreads3, 0, s>>>(g, u, uT, P, sig, b, bT, out, outT, n, ctl, part);
+        break;
+    case OP3K_JACOBI_NORM:
+        k_op3<OP3K_JACOBI_NORM><<<nb, kThreads3, 0, s>>>(g, u, uT, P, sig, b, bT, out, outT, n, ctl,
+                                                         part);
         break;
     case OP3K_FAS:
         k_op3<OP3K_FAS><<<nb, kThreads3, 0, s>>>(g, u, uT, P, sig, b, bT, out, outT, n, ctl, part);

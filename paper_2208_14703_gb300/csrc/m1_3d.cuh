@@ -260,13 +260,15 @@ __device__ __forceinline__ bool admissible3(const EF& s, double T, double c)
 // ---------------------------------------------------------------------------
 // Launchers (m1_3d.cu).  Every kernel of a cycle returns at once when the
 // control block says done (ctl may be null outside a step).
-enum Op3 { OP3K_APPLY = 0, OP3K_RESID = 1, OP3K_JACOBI = 2, OP3K_FAS = 3, OP3K_PSEUDO = 4 };
+enum Op3 { OP3K_APPLY = 0, OP3K_RESID = 1, OP3K_JACOBI = 2, OP3K_FAS = 3, OP3K_PSEUDO = 4,
+            OP3K_JACOBI_NORM = 5 };
 
 void launch3_closure(const G3& g, const EF* u, P6* P, size_t n, const Ctl* ctl, cudaStream_t s);
 // APPLY: out = A(u); RESID: out = b - A(u) (+ per-block norm partials when part
 // is not null); JACOBI: one sweep of A(u) = b; FAS: out = A(u) + b; PSEUDO: one
 // pseudo-time step with source b (explicit limited half, then one Jacobi sweep
-// of u + dtau A(u) = u~; dtau and theta from the control block).
+// of u + dtau A(u) = u~; dtau and theta from the control block); JACOBI_NORM:
+// a Jacobi sweep that also writes the norm partials of b - A(u) of its input.
 void launch3_op(int mode, const G3& g, const EF* u, const double* uT, const P6* P,
                 const Sig2<double>* sig, const EF* b, const double* bT, EF* out, double* outT,
                 size_t n, Ctl* ctl, double* part, cudaStream_t s);
@@ -283,7 +285,7 @@ void launch3_rhs(const G3& g, const EF* u, const double* uT, EF* b, double* bT, 
                  cudaStream_t s);
 void launch3_norm_state(const G3& g, const EF* x, const double* xT, double* part, size_t n,
                         cudaStream_t s);
-enum { FIN3_INIT = 0, FIN3_CYCLE = 1 };
+enum { FIN3_INIT = 0, FIN3_CYCLE = 1, FIN3_DEFER = 2 };
 void launch3_finalize(Ctl* ctl, BatchCtl* bctl, const double* part, const double* partb, int np,
                       int mode, cudaStream_t s);
 void launch3_pack(const double* planes, EF* ef, double* T, size_t n, cudaStream_t s);

@@ -13,7 +13,11 @@
 //
 // Fine level: nu0 Jacobi sweeps (closure pass + operator pass each), the
 // residual and its restriction, the coarse-grid corrections, the damped
-// prolongation (Eq. (34)), nu0 sweeps, then v <- u and the residual norm.
+// prolongation (Eq. (34)), nu0 sweeps, then v <- u.  The norm of b - A(v) that
+// ends a cycle is formed by the first sweep of the next one, which reads v and
+// evaluates b + N(v) anyway (one closure and one operator pass fewer per
+// cycle); if that cycle converged the rest of the launch returns at once and v
+// is the result.
 // Coarse level l: on a fresh visit f_l = A(v_l) + r_l and u_l = v_l; m
 // pseudo-time steps (Eq. (30), Algorithm 3; the coarsest level m_coarse and
 // nothing else), the residual, restriction, corrections, prolongation and m
@@ -185,17 +189,25 @@ void Grid3::set_dt(double dt)
 }
 
 // ---- the cycle, emitted into a graph --------------------------------------------
+// nsweeps fine Jacobi sweeps; the first one of a cycle (reading v) also forms
+// the norm of b - A(v), the stop test of the previous cycle (a deferred
+// finalize follows it).
 void Grid3::emit_sweeps_fine(int nsweeps, cudaStream_t s)
 {
     Lev3& q = lv[0];
     for (int k = 0; k < nsweeps; ++k) {
-        const EF* src = cur[0] < 0 ? q.v : q.u[cur[0]];
-        const double* srcT = cur[0] < 0 ? q.vT : q.uT[cur[0]];
+        const bool first = cur[0] < 0;
+        const EF* src = first ? q.v : q.u[cur[0]];
+        const double* srcT = first ? q.vT : q.uT[cur[0]];
         const int dst = cur[0] == 0 ? 1 : 0;
         launch3_closure(q.g, src, q.P, q.n, ctl, s);
-        launch3_op(OP3K_JACOBI, q.g, src, srcT, q.P, q.sig, q.f, q.fT, q.u[dst], q.uT[dst], q.n,
-                   ctl, nullptr, s);
+        launch3_op(first ? OP3K_JACOBI_NORM : OP3K_JACOBI, q.g, src, srcT, q.P, q.sig, q.f, q.fT,
+                   q.u[dst], q.uT[dst], q.n, ctl, first ? part : nullptr, s);
         kernels_per_cycle += 2;
+        if (first) {
+            launch3_finalize(ctl, bctl, part, nullptr, blocks3(q.n), FIN3_DEFER, s);
+            kernels_per_cycle += 1;
+        }
         cur[0] = dst;
     }
 }
@@ -272,12 +284,11 @@ void Grid3::emit_cycle(const Params& p, cudaStream_t s)
         kernels_per_cycle += 1;
         emit_sweeps_fine(p.nu0, s);
     }
-    // end of the cycle: v <- u, r = b - A(v) and its norm, stop test, dtau_im
+    // end of the cycle: v <- u; its residual norm, stop test and dtau_im update
+    // come with the next cycle's first sweep (a step takes one graph launch
+    // more than it has cycles)
     launch3_copy(q.u[cur[0]], q.uT[cur[0]], q.v, q.vT, q.n, ctl, s);
-    launch3_closure(q.g, q.v, q.P, q.n, ctl, s);
-    launch3_op(OP3K_RESID, q.g, q.v, q.vT, q.P, q.sig, q.f, q.fT, q.r, q.rT, q.n, ctl, part, s);
-    launch3_finalize(ctl, bctl, part, nullptr, blocks3(q.n), FIN3_CYCLE, s);
-    kernels_per_cycle += 4;
+    kernels_per_cycle += 1;
 }
 
 m1_status Grid3::build_graph(const Params& p, double dt)

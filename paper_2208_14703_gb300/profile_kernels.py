@@ -13,13 +13,16 @@ CFL 100, at n x n cells):
   sweep3d   3D: one Jacobi sweep (closure pass + operator pass) of an n^3 grid with
             reflecting walls, admissible random states and lognormal opacities
             generated on the device
+  step3d    3D: one implicit step of the n^3 hot cube (lognormal opacities,
+            reflecting walls, CFL 100) with L_max = --lmax
 The state and opacities are set once; each case runs its launches once after one
 untimed warm-up of the same launches, so `ncu -s` skips the warm-up.
 
 --tune-file PATH: the strip shapes of the sweep kernels.  If PATH exists its
 table is installed (no tuning launches, so a profiled run sees only the case's
 kernels); otherwise the autotuner runs and its table is written to PATH (run the
-command once without ncu first).
+command once without ncu first).  tune_gb300.json beside this file is the table
+the autotuner wrote on a GB300; the committed profiles use it.
 """
 from __future__ import annotations
 
@@ -31,7 +34,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
-                    choices=["sweep64", "sweep32", "step64", "stepmixed", "sweep3d"])
+                    choices=["sweep64", "sweep32", "step64", "stepmixed", "sweep3d", "step3d"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--lmax", type=int, default=6)
     ap.add_argument("--cycles", type=int, default=50, help="max_cycles of the step cases")
@@ -41,6 +44,9 @@ def main():
     from paper_2208_14703_gb300 import inputs, m1
     if args.case == "sweep3d":
         sweep3d(m1, args.n)
+        return
+    if args.case == "step3d":
+        step3d(m1, inputs, args.n, args.lmax, args.cycles)
         return
     if args.tune_file:
         import json
@@ -67,6 +73,18 @@ def main():
             st = g.implicit_step(dt, params, allow_not_converged=True)
     if not args.case.startswith("sweep"):
         print(f"cycles {st.cycles} sweeps {st.sweeps} ms {st.ms:.3f}")
+    g.close()
+
+
+def step3d(m1, inputs, n, lmax, cycles):
+    case = inputs.hot_cube_3d(n, lmax=lmax)
+    g = m1.grid3_from_case(case)
+    sig = np.stack([case["sa"], case["ss"]])
+    params = m1.m1_default_params(tol=case["tol"], max_cycles=cycles)
+    for _ in range(2):                       # warm-up, then the profiled pass
+        g.set_state(case["state"], sig)
+        st = g.implicit_step(case["dt"], params, allow_not_converged=True)
+    print(f"cycles {st.cycles} sweeps {st.sweeps} ms {st.ms:.3f}")
     g.close()
 
 
