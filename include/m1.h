@@ -253,7 +253,8 @@ m1_status m1_server_destroy(m1_server_t s);
  * give each warp a strip of 30 columns and `strip_rows` rows.  m1_autotune
  * times one sweep of a synthetic admissible n x n level (n = 16 .. 2048; the
  * FP32 correction form also 4096) for
- * strip heights 1, 2, 4, 8, 12, 16, 24, 32, for FP64 (kind 0) and for the FP32
+ * strip heights 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128 (at most n), for
+ * FP64 (kind 0) and for the FP32
  * correction form of the mixed path (kind 1, also both row stagings), and keeps
  * the fastest shape per size class (grids of about the same cell count) in a
  * process-wide table that grids, batches and servers created afterwards use.
@@ -276,7 +277,8 @@ typedef struct {
 } m1_tune_entry;
 m1_status m1_autotune(void* cuda_stream, m1_tune_entry* out, int max_entries, int* n_entries);
 /* Installs entries (e.g. restored from an earlier m1_autotune); strip_rows = 0
- * restores the default for that kind and size class. */
+ * restores the default for that kind and size class; INVALID_ARG for a height
+ * above 256, an unknown kind or staging. */
 m1_status m1_set_tuning(const m1_tune_entry* in, int n);
 /* The strip height a new nx x ny level of the given kind would take. */
 m1_status m1_strip_rows(int kind, int nx, int ny, int* rows);
@@ -310,9 +312,14 @@ m1_status m1_probe_fma_peak(int precision, void* cuda_stream, int reps, double* 
  *   M1_OP_PSEUDO    out = one pseudo-time step with source f = rhs: explicit
  *                   limited half then one Jacobi sweep of u + dtau A(u) = u~
  *                   (Eq. (30), Algorithm 3), theta_ex = theta
+ *   M1_OP_RESIDUAL_DW  as M1_OP_RESIDUAL, evaluated in double-word FP32 (pairs
+ *                   hi + lo of FP32 numbers, about 48 bits; FP64 descriptors
+ *                   only): the arithmetic of the mixed path's defect when its
+ *                   tolerance lies far above that format's noise floor
  * For M1_OP_JACOBI and M1_OP_PSEUDO, *norm (if not NULL) receives the number of
  * cells whose local E-T solve did not converge to a finite positive T. */
-enum { M1_OP_APPLY = 0, M1_OP_RESIDUAL = 1, M1_OP_FAS_RHS = 2, M1_OP_JACOBI = 3, M1_OP_PSEUDO = 4 };
+enum { M1_OP_APPLY = 0, M1_OP_RESIDUAL = 1, M1_OP_FAS_RHS = 2, M1_OP_JACOBI = 3, M1_OP_PSEUDO = 4,
+       M1_OP_RESIDUAL_DW = 5 };
 m1_status m1_op_level(const m1_grid_desc* desc, const double* inflow, double dt, const double* sig,
                       const double* state, const double* rhs, int mode, double dtau, double theta,
                       double* out, double* norm);

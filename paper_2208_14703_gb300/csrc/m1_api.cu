@@ -12,6 +12,8 @@
 #include <memory>
 #include <vector>
 
+#include <type_traits>
+
 #include "m1_engine.h"
 
 namespace m1 {
@@ -108,6 +110,9 @@ Ctl make_ctl(const m1_solve_params& sp, double diag0)
     c.theta_ex = sp.theta_ex; c.theta_c = sp.theta_c; c.max_cycles = sp.max_cycles;
     c.dtau_rule = sp.dtau_rule;
     c.res0_floor = 1e-14 * diag0;   // rounding floor of evaluating A
+    // double words carry ~48 bits: the defect they form has a noise floor of a
+    // few 1e-14 diag ||b||; the cycles take it only with 1000x of margin
+    c.dw_floor = 1e-10 * diag0;
     c.active = 1;
     return c;
 }
@@ -924,6 +929,24 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
         }
         return M1_OK;
     }
+    case M1_OP_RESIDUAL_DW:
+        if constexpr (std::is_same<R, double>::value) {
+            M1_TRY(pack_planar(q.u[0], n, state));
+            M1_TRY(pack_planar(q.f, n, rhs));
+            launch_residual_dw(d, t0, part, stream);
+            M1_CK(cudaGetLastError());
+            M1_TRY(unpack_planar(q.r, n, out));
+            if (norm) {
+                std::vector<double> p(q.strips);
+                M1_CK(cudaMemcpy(p.data(), part, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
+                double sum = 0.0;
+                for (double x : p) sum += x;
+                *norm = std::sqrt(sum);
+            }
+            return M1_OK;
+        } else {
+            return M1_ERR_INVALID_ARG;
+        }
     case M1_OP_FAS_RHS:
         M1_TRY(pack_planar(q.v, n, state));
         M1_TRY(pack_planar(q.r, n, rhs));
@@ -1252,7 +1275,10 @@ void MixedModel::record_cycle(const Params& p, cudaStream_t s)
     int cur0 = 0;
     lo.record_cycle(p, cur0, s, false);
     launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s);
+    // each instance's defect comes from one of the two: FP64, or double-word FP32
+    // where its tolerance lies far above the double-word noise floor (FIN_INIT)
     launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
+    launch_defect_dw(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, nullptr, FIN_CYCLE, 0, hi.bctl, s);
 }
 
@@ -1318,7 +1344,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
             o.status = c.status;
             o.newton_fail = c.newton_fail;
             o.damped = c.damped;
-            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 3);   // accumulate, defect, finalize
+            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 4);   // accumulate, defects, finalize
         }
         ++k;
     }

@@ -77,6 +77,9 @@ struct Ctl {
     int max_cycles, hist_len;
     int dtau_rule;                // 0: |change| of the residual norm; 1: its decrease
     int active;                   // the instance takes part in the batch
+    double dw_floor;              // mixed path: the defect of the cycles is formed in
+                                  // double-word FP32 when tol ||r_0|| > dw_floor ||b||
+    int defect_dw;                // (state) set by FIN_INIT from that rule
     // state
     double res0, res, res_prev, bnorm, dtau;
     int kappa, done, status, result_buf;

@@ -1,0 +1,107 @@
+// Double-word FP32 arithmetic ("float-float"): a value is the unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2, about 48 bits of
+// significand.  The operations follow the double-word algorithms analysed by
+// Joldes, Muller & Popescu, "Tight and rigorous error bounds for basic building
+// blocks of double-word arithmetic", ACM TOMS 44(2), 2017, built on the
+// error-free transforms TwoSum (Knuth), Fast2Sum (Dekker) and TwoProd by a fused
+// multiply-add.  Relative error bounds, with u = 2^-24: sum of two double words
+// (their accurate algorithm) 3u^2 + 13u^3; product of two double words (the FMA
+// algorithm) 5u^2; product by an FP32 number 2u^2; sum with an FP32 number 2u^2.
+// The reciprocal and square root here are one Newton-Raphson correction of the
+// correctly rounded FP32 result, computed with these operations (relative error
+// a few u^2).
+//
+// GB300 runs FP32 at 64 times its FP64 rate, so a computation needing about 48
+// bits costs fewer FP32 issue slots as double words than FP64 slots: the
+// mixed-precision defect uses this when its tolerance allows (m1_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace m1 {
+
+struct DW {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DW two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return DW{ s, (a - (s - bb)) + (b - bb) };
+}
+
+// |a| >= |b| (or a = 0)
+__device__ __forceinline__ DW fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return DW{ s, b - (s - a) };
+}
+
+__device__ __forceinline__ DW two_prod(float a, float b)
+{
+    const float p = a * b;
+    return DW{ p, fmaf(a, b, -p) };
+}
+
+__device__ __forceinline__ DW dw_from(double x)
+{
+    const float h = (float)x;
+    return DW{ h, (float)(x - (double)h) };
+}
+
+__device__ __forceinline__ double dw_to_double(DW x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ DW operator-(DW x) { return DW{ -x.hi, -x.lo }; }
+
+__device__ __forceinline__ DW operator+(DW x, DW y)
+{
+    const DW s = two_sum(x.hi, y.hi);
+    const DW t = two_sum(x.lo, y.lo);
+    const DW v = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(v.hi, t.lo + v.lo);
+}
+
+__device__ __forceinline__ DW operator-(DW x, DW y) { return x + (-y); }
+
+__device__ __forceinline__ DW operator+(DW x, float y)
+{
+    const DW s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, x.lo + s.lo);
+}
+
+__device__ __forceinline__ DW operator*(DW x, DW y)
+{
+    const DW c = two_prod(x.hi, y.hi);
+    const float t = fmaf(x.lo, y.hi, fmaf(x.hi, y.lo, x.lo * y.lo));
+    return fast_two_sum(c.hi, c.lo + t);
+}
+
+__device__ __forceinline__ DW operator*(DW x, float y)
+{
+    const DW c = two_prod(x.hi, y);
+    return fast_two_sum(c.hi, fmaf(x.lo, y, c.lo));
+}
+
+__device__ __forceinline__ bool operator>(DW x, float y) { return x.hi > y || (x.hi == y && x.lo > 0.f); }
+
+// 1/x: r0 = the correctly rounded FP32 reciprocal of x.hi, then
+// r = r0 + r0 e with e = 1 - x r0 formed in double words (|e| ~ u).
+__device__ __forceinline__ DW dw_rcp(DW x)
+{
+    const float r0 = __frcp_rn(x.hi);
+    const DW xr = x * r0;
+    const DW e = DW{ 1.f, 0.f } - xr;
+    return fast_two_sum(r0, r0 * e.hi);
+}
+
+// sqrt(a): s0 = the correctly rounded FP32 square root of a.hi, then
+// s = s0 + (a - s0^2) / (2 s0), the difference formed exactly by TwoProd.
+__device__ __forceinline__ DW dw_sqrt(DW a)
+{
+    const float s0 = __fsqrt_rn(a.hi);
+    const DW p = two_prod(s0, s0);
+    const float d = ((a.hi - p.hi) - p.lo) + a.lo;
+    return fast_two_sum(s0, d * (0.5f * __frcp_rn(s0)));
+}
+
+}  // namespace m1

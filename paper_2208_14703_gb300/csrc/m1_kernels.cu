@@ -20,6 +20,7 @@
 // registers, so each staged cell's closure is evaluated once per strip.
 #include <type_traits>
 
+#include "m1_dw.cuh"
 #include "m1_kernels.cuh"
 
 namespace m1 {
@@ -1000,6 +1001,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* __restrict__ ctls,
         ctl->result_buf = cur;
         ctl->status = CTL_NOT_CONVERGED;
         ctl->pending_r0 = 1;
+        ctl->defect_dw = ctl->tol * res > ctl->dw_floor * ctl->bnorm;
         if (res <= ctl->res0_floor * ctl->bnorm) mark_done(ctl, bctl, CTL_OK);
         return;
     }
@@ -1098,6 +1100,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
             const unsigned long long wm =
                 lane < nm ? reinterpret_cast<const unsigned long long*>(lv32 + it.x)[lane] : 0ull;
             if (!enter_item(L, lv64 + it.x, ctls, it.x, lane)) continue;
+            if (ctls[it.x].defect_dw) continue;   // k_defect_dw forms this instance's defect
             if (lane < nm) reinterpret_cast<unsigned long long*>(&M)[lane] = wm;
             __syncwarp();
         }
@@ -1126,6 +1129,201 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
         });
         const double sum = warp_sum(nrm);
         if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The defect in double-word FP32 (m1_dw.cuh): the same expressions as the FP64
+// residual, each operation on hi + lo pairs of FP32 numbers (about 48 bits).
+// The FP64 state, right-hand side and opacities are read and split into double
+// words; constants of the level are split once per item.
+
+struct StagedDW {
+    DW E, Fx, Fy, Pxx, Pxy, Pyy, T;
+};
+
+struct LevelDW {
+    DW c, bx, by, diag, a_r, c_v, m3ic2, q3ic2, third;
+};
+
+__device__ __forceinline__ LevelDW level_dw(const Level<double>& L)
+{
+    return LevelDW{ dw_from(L.c), dw_from(L.bx), dw_from(L.by), dw_from(L.diag), dw_from(L.a_r),
+                    dw_from(L.c_v), dw_from(-3.0 * L.ic2), dw_from(3.0 * L.ic2),
+                    dw_from(1.0 / 3.0) };
+}
+
+// The closure of Eq. (5) in the form of closure(): s = sqrt(4 - 3 f^2) (f^2
+// clamped to 1), P = (s - 1)/3 E I + 3/(2 + s) F F^T / (c^2 E).
+__device__ __forceinline__ StagedDW stage_dw(const LevelDW& D, const Cell4<double>& c)
+{
+    StagedDW o;
+    o.E = dw_from(c.E); o.Fx = dw_from(c.Fx); o.Fy = dw_from(c.Fy); o.T = dw_from(c.T);
+    const DW iE = dw_rcp(o.E);
+    const DW fx = o.Fx * iE, fy = o.Fy * iE;
+    DW a = (fy * fy + fx * fx) * D.m3ic2 + 4.f;
+    if (!(a > 1.f)) a = DW{ 1.f, 0.f };
+    const DW s = dw_sqrt(a);
+    const DW Eiso = o.E * ((s + (-1.f)) * D.third);
+    const DW q = dw_rcp(s + 2.f) * D.q3ic2;
+    const DW qx = q * fx, qy = q * fy;
+    o.Pxx = qx * o.Fx + Eiso;
+    o.Pxy = qx * o.Fy;
+    o.Pyy = qy * o.Fy + Eiso;
+    return o;
+}
+
+__device__ __forceinline__ DW shfl_dw(DW v, int from)
+{
+    return DW{ __shfl_sync(0xffffffffu, v.hi, from), __shfl_sync(0xffffffffu, v.lo, from) };
+}
+
+__device__ __forceinline__ StagedDW shfl_staged_dw(const StagedDW& v, int from)
+{
+    StagedDW o;
+    o.E = shfl_dw(v.E, from); o.Fx = shfl_dw(v.Fx, from); o.Fy = shfl_dw(v.Fy, from);
+    o.Pxx = shfl_dw(v.Pxx, from); o.Pxy = shfl_dw(v.Pxy, from); o.Pyy = shfl_dw(v.Pyy, from);
+    o.T = v.T;
+    return o;
+}
+
+// r = b - A(u) of one strip cell in double words (Eq. (13) with the [EXT]
+// sources), from the staged neighbours and the cell's own state.
+__device__ __forceinline__ void residual_dw(const Level<double>& L, const LevelDW& D,
+                                            const StagedDW& wv, const StagedDW& ev,
+                                            const StagedDW& prev, const StagedDW& next,
+                                            const StagedDW& cur, bool two_d,
+                                            const Cell4<double>& b, const Sig2<double>& sg,
+                                            DW& rE, DW& rFx, DW& rFy, DW& rT)
+{
+    const DW cbx = D.c * D.bx;
+    DW NE = D.bx * (D.c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
+    DW NFx = cbx * ((wv.Fx + ev.Fx) + D.c * (wv.Pxx - ev.Pxx));
+    DW NFy = cbx * ((wv.Fy + ev.Fy) + D.c * (wv.Pxy - ev.Pxy));
+    if (two_d) {
+        const DW cby = D.c * D.by;
+        NE = NE + D.by * (D.c * (prev.E + next.E) + (prev.Fy - next.Fy));
+        NFx = NFx + cby * ((prev.Fx + next.Fx) + D.c * (prev.Pxy - next.Pxy));
+        NFy = NFy + cby * ((prev.Fy + next.Fy) + D.c * (prev.Pyy - next.Pyy));
+    }
+    const DW ka = dw_from(L.cdt * sg.sa), dk = dw_from(L.diag + L.cdt * (sg.sa + sg.ss));
+    const DW T2 = cur.T * cur.T;
+    const DW se = ka * (cur.E - D.a_r * (T2 * T2));
+    rE = dw_from(b.E) - ((D.diag * cur.E + se) - NE);
+    rFx = dw_from(b.Fx) - (dk * cur.Fx - NFx);
+    rFy = dw_from(b.Fy) - (dk * cur.Fy - NFy);
+    rT = dw_from(b.T) - (D.c_v * cur.T - se);
+}
+
+// The warp-strip march of strip_march with FP64 rows staged as double words.
+template <typename F>
+__device__ __forceinline__ void strip_march_dw(const Level<double>& L, const LevelDW& D, int2 it,
+                                               int lane, const Cell4<double>* __restrict__ src,
+                                               F&& cell)
+{
+    const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
+    const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
+    const int i = min(x0 - 1 + lane, nx);
+    const bool colfast = x0 >= 1 && x0 + kStripW + 1 <= nx;
+    const bool own = lane >= 1 && lane <= kStripW && i < nx;
+    const int rows = min(L.sh, ny - y0);
+    StagedDW prev{}, cur, next{};
+    Raw<double> rn{};
+    if (two_d) {
+        prev = stage_dw(D, load_raw<double, false>(L, src, i, y0 - 1, colfast && y0 >= 1).c);
+        rn = load_raw<double, false>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
+    }
+    cur = stage_dw(D, load_raw<double, false>(L, src, i, y0, colfast).c);
+    size_t k = (size_t)y0 * nx + i;
+    for (int r = 0; r < rows; ++r, k += nx) {
+        const int j = y0 + r;
+        if (two_d) {
+            next = stage_dw(D, rn.c);
+            if (r + 1 < rows) rn = load_raw<double, false>(L, src, i, j + 2, colfast && j + 2 < ny);
+        }
+        const StagedDW wv = shfl_staged_dw(cur, (lane + 31) & 31);
+        const StagedDW ev = shfl_staged_dw(cur, (lane + 1) & 31);
+        if (own) cell(k, wv, ev, prev, next, cur);
+        prev = cur;
+        cur = next;
+    }
+}
+
+// k_defect in double words: the same outputs (norm partials, and the FP32
+// problem w = fl32(v), e = 0, g = fl32(r)) for the instances whose control
+// block selected it (tol ||r_0|| far above the double-word noise floor).
+__global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<double>* __restrict__ lv64,
+                                                                const Level<float>* __restrict__ lv32,
+                                                                WorkList wl, Ctl* __restrict__ ctls,
+                                                                double* __restrict__ partials)
+{
+    __shared__ Level<double> Ls[kStripWarps];
+    __shared__ Level<float> Ms[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<double>& L = Ls[wib];
+    Level<float>& M = Ms[wib];
+    const int nw = *wl.count;
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
+        const int2 it = wl.items[w];
+        {
+            constexpr int nm = (int)(sizeof(Level<float>) / 8);
+            const unsigned long long wm =
+                lane < nm ? reinterpret_cast<const unsigned long long*>(lv32 + it.x)[lane] : 0ull;
+            if (!enter_item(L, lv64 + it.x, ctls, it.x, lane)) continue;
+            if (!ctls[it.x].defect_dw) continue;   // k_defect forms this instance's defect
+            if (lane < nm) reinterpret_cast<unsigned long long*>(&M)[lane] = wm;
+            __syncwarp();
+        }
+        const LevelDW D = level_dw(L);
+        const bool two_d = L.dim == 2;
+        double nrm = 0.0;
+        strip_march_dw(L, D, it, lane, L.u[0], [&](size_t k, const StagedDW& wv, const StagedDW& ev,
+                                                    const StagedDW& prev, const StagedDW& next,
+                                                    const StagedDW& cur) {
+            DW rE, rFx, rFy, rT;
+            residual_dw(L, D, wv, ev, prev, next, cur, two_d, L.f[k], L.sig[k], rE, rFx, rFy, rT);
+            const double e = dw_to_double(rE), fx = dw_to_double(rFx), fy = dw_to_double(rFy),
+                         t = dw_to_double(rT);
+            nrm += e * e + (fx * fx + fy * fy) * L.ic2 + t * t;
+            M.w[k] = Cell4<float>{ cur.E.hi, cur.Fx.hi, cur.Fy.hi, cur.T.hi };
+            M.f[k] = Cell4<float>{ rE.hi, rFx.hi, rFy.hi, rT.hi };
+            M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
+        });
+        const double sum = warp_sum(nrm);
+        if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
+        __syncwarp();
+    }
+}
+
+// The double-word residual alone, r = b - A(u) written in FP64 (hi + lo) with
+// its norm partials: a check of k_defect_dw's arithmetic (m1_op_level).
+__global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<double>* __restrict__ lv,
+                                                                  WorkList wl,
+                                                                  double* __restrict__ partials)
+{
+    __shared__ Level<double> Ls[kStripWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Level<double>& L = Ls[wib];
+    const int nw = *wl.count;
+    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
+        const int2 it = wl.items[w];
+        if (!enter_item(L, lv + it.x, nullptr, it.x, lane)) continue;
+        const LevelDW D = level_dw(L);
+        const bool two_d = L.dim == 2;
+        double nrm = 0.0;
+        strip_march_dw(L, D, it, lane, L.u[0], [&](size_t k, const StagedDW& wv, const StagedDW& ev,
+                                                    const StagedDW& prev, const StagedDW& next,
+                                                    const StagedDW& cur) {
+            DW rE, rFx, rFy, rT;
+            residual_dw(L, D, wv, ev, prev, next, cur, two_d, L.f[k], L.sig[k], rE, rFx, rFy, rT);
+            const Cell4<double> r = { dw_to_double(rE), dw_to_double(rFx), dw_to_double(rFy),
+                                      dw_to_double(rT) };
+            L.r[k] = r;
+            nrm += r.E * r.E + (r.Fx * r.Fx + r.Fy * r.Fy) * L.ic2 + r.T * r.T;
+        });
+        const double sum = warp_sum(nrm);
+        if (lane == 0 && partials) partials[L.part_off + it.y] = sum * L.vol;
         __syncwarp();
     }
 }
@@ -1325,6 +1523,17 @@ void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList
                    double* partials, cudaStream_t s)
 {
     k_defect<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
+}
+
+void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
+                      double* partials, cudaStream_t s)
+{
+    k_defect_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
+}
+
+void launch_residual_dw(const Level<double>* lv, WorkList wl, double* partials, cudaStream_t s)
+{
+    k_residual_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv, wl, partials);
 }
 
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,

@@ -53,6 +53,11 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 void launch_fas_aw32(const Level<float>* lv, WorkList wl, Ctl* ctls, cudaStream_t s);
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
                    double* partials, cudaStream_t s);
+// the defect in double-word FP32, for the instances whose control block chose it
+void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
+                      double* partials, cudaStream_t s);
+// the double-word residual r = b - A(u) alone (written in FP64), for checks
+void launch_residual_dw(const Level<double>* lv, WorkList wl, double* partials, cudaStream_t s);
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,
                        Ctl* ctls, int buf, cudaStream_t s);
 

@@ -32,7 +32,7 @@ DTAU_ABS, DTAU_SIGNED = 0, 1
 CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
 OP3_APPLY, OP3_RESIDUAL, OP3_JACOBI = 0, 1, 2
 SMALL_CELLS = 65536          # servers: requests of at most this many cells take the small lane
-OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO = 0, 1, 2, 3, 4
+OP_APPLY, OP_RESIDUAL, OP_FAS_RHS, OP_JACOBI, OP_PSEUDO, OP_RESIDUAL_DW = 0, 1, 2, 3, 4, 5
 
 EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_state",
            "m1_set_inflow", "m1_get_state", "m1_implicit_step", "m1_residual_norm",

@@ -233,3 +233,21 @@ def test_fma_peak_probe():
     nominal = 152 * 2 * 2.07e9
     assert 0.1 * nominal < f64 <= 1.02 * nominal, f64
     assert f32 > 20 * f64, (f32, f64)
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_double_word_residual(name, kw):
+    """The residual in double-word FP32 (the mixed path's defect arithmetic)
+    against the oracle: about 48 bits per operation (relative error a few
+    2^-48 per step, Joldes, Muller & Popescu 2017) through the closure and the
+    neighbour sums, so within 1e-11 of each field's scale (the FP64 kernel's
+    1e-12 with a margin for the shorter significand) and the norm within 1e-11."""
+    case, g, desc, sig = _setup(kw)
+    b = O.rhs_of(g, case["state"]) * 1.01
+    got, nrm = m1.m1_op_level(desc, case["dt"], sig, case["state"], b, mode=m1.OP_RESIDUAL_DW,
+                              inflow=case["inflow"])
+    ref = O.residual(g, case["dt"], case["sa"], case["ss"], b, case["state"])
+    err = np.abs(got - ref) / _scale(ref)
+    print(name, "double-word residual max rel error", err.max())
+    _close(got, ref, 1e-11)
+    assert nrm == pytest.approx(O.norm(g, ref), rel=1e-11)

@@ -124,3 +124,27 @@ def test_mixed_beam_4096_configuration():
     assert st.cycles == st64.cycles
     assert max(err.values()) <= BOUND, err
     assert np.all(out[0] > 0) and np.all(np.hypot(out[1], out[2]) <= out[0] * (1 + 1e-12))
+
+
+# tol 1e-8: tol ||r_0|| lies far above the double-word noise floor, so the
+# cycles form their defect in double-word FP32 (m1_kernels.cu, k_defect_dw)
+DW_CASES = [
+    ("2d-hot-square-128", lambda: inputs.hot_square_2d(128, lmax=5), 5),
+    ("2d-beam-64", lambda: inputs.beam_channel_2d(64, lmax=4), 4),
+    ("1d-gaussian-256", lambda: inputs.gaussian_1d(256, tol=1e-8), 4),
+]
+
+
+@pytest.mark.parametrize("name,make,lmax", DW_CASES, ids=[c[0] for c in DW_CASES])
+def test_mixed_step_with_double_word_defect_matches_oracle(name, make, lmax):
+    """At tol 1e-8 the mixed path takes the same cycles as the oracle's FP64 step
+    and lands within 1e-8 of it per field (step parity of the mixed path)."""
+    case = make()
+    og = O.Grid.from_case(case)
+    ref, ost, _, _ = O.implicit_step(og, case["dt"], case["sa"], case["ss"], case["state"],
+                                     O.SolveParams(lmax=lmax, tol=1e-8))
+    out, st = mixed_step(case, 1e-8, lmax)
+    assert st.status == 0 and st.cycles == ost["cycles"], (st.cycles, ost["cycles"])
+    err = field_errors(out, ref, case["desc"]["c"])
+    print(name, st.cycles, "cycles", err)
+    assert max(err.values()) <= BOUND, err
