@@ -208,6 +208,18 @@ m1_status Engine<R>::init(int capacity, int levels, bool correction_form, cudaSt
     return M1_OK;
 }
 
+// Keep double-word copies of every slot's level-0 iterate, right-hand side and
+// opacities (slots added afterwards get them).
+template <typename R>
+m1_status Engine<R>::enable_dw()
+{
+    dw = true;
+    dwh.assign(cap, DwLevel{ nullptr, nullptr, nullptr });
+    M1_TRY(calloc_common((void**)&dwd, sizeof(DwLevel) * cap));
+    M1_CK(cudaMemsetAsync(dwd, 0, sizeof(DwLevel) * cap, stream));
+    return M1_OK;
+}
+
 template <typename R>
 m1_status Engine<R>::slot_alloc(int i, void** p, size_t bytes)
 {
@@ -258,6 +270,13 @@ m1_status Engine<R>::add_slot(const m1_grid_desc& dsc, int* out)
         M1_CK(cudaMemsetAsync(q.inflow, 0, sizeof(R) * 12 * q.prof_len, stream));
         M1_CK(cudaMemsetAsync(q.sig, 0, sizeof(Sig2<R>) * q.n, stream));
         prof[(size_t)l * cap + i].assign((size_t)12 * q.prof_len, 0.0);
+        if (dw && l == 0) {
+            DwLevel& D = dwh[i];
+            M1_TRY(slot_alloc(i, (void**)&D.v, sizeof(DW4) * q.n));
+            M1_TRY(slot_alloc(i, (void**)&D.b, sizeof(DW4) * q.n));
+            M1_TRY(slot_alloc(i, (void**)&D.sig, sizeof(DW2) * q.n));
+            M1_CK(cudaMemcpyAsync(dwd + i, &D, sizeof(DwLevel), cudaMemcpyHostToDevice, stream));
+        }
         nx /= 2; if (g.dim == 2) ny /= 2;
         hx *= 2; if (g.dim == 2) hy *= 2;
     }
@@ -281,6 +300,10 @@ m1_status Engine<R>::remove_slot(int i)
     for (void* p : mem[i]) cudaFree(p);
     mem[i].clear();
     used[i] = 0;
+    if (dw) {
+        dwh[i] = DwLevel{ nullptr, nullptr, nullptr };
+        M1_CK(cudaMemcpyAsync(dwd + i, &dwh[i], sizeof(DwLevel), cudaMemcpyHostToDevice, stream));
+    }
     for (int l = 0; l < L; ++l) std::memset(&h[(size_t)l * cap + i], 0, sizeof(Level<R>));
     ctl_h[i] = Ctl{};
     M1_CK(cudaMemcpyAsync(ctl + i, ctl_h + i, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
@@ -933,7 +956,9 @@ m1_status Engine<R>::op_level(double dt, const double* sig, const double* state,
         if constexpr (std::is_same<R, double>::value) {
             M1_TRY(pack_planar(q.u[0], n, state));
             M1_TRY(pack_planar(q.f, n, rhs));
-            launch_residual_dw(d, t0, part, stream);
+            DW4* scratch = nullptr;
+            M1_TRY(calloc_common((void**)&scratch, sizeof(DW4) * n));
+            launch_residual_dw(d, q.u[0], scratch, n, t0, part, stream);
             M1_CK(cudaGetLastError());
             M1_TRY(unpack_planar(q.r, n, out));
             if (norm) {
@@ -1017,6 +1042,7 @@ size_t Engine<R>::slot_bytes(const m1_grid_desc& g) const
         const long long n = nx * ny;
         b += (size_t)n * (states * sizeof(Cell4<R>) + sizeof(Sig2<R>));
         b += sizeof(R) * 12 * (size_t)std::max(nx, ny) + 8 * 256;
+        if (dw && l == 0) b += (size_t)n * (2 * sizeof(DW4) + sizeof(DW2));
         nx /= 2; if (g.dim == 2) ny /= 2;
     }
     return b;
@@ -1140,6 +1166,7 @@ m1_status PlainModel::sv_cycles(const Params& p, int n)
 m1_status MixedModel::sv_init(int cap, int L, cudaStream_t s)
 {
     M1_TRY(hi.init(cap, 1, false, s, 0));
+    M1_TRY(hi.enable_dw());
     M1_TRY(lo.init(cap, L, true, hi.stream, 0));
     lo.ctl = hi.ctl;
     return M1_OK;
@@ -1206,6 +1233,7 @@ m1_status MixedModel::sv_begin(const std::vector<int>& slots, const std::vector<
     }
     M1_TRY(hi.set_init_lists(slots));
     launch_make_rhs<double>(hi.d, hi.init_chunks.view(), hi.ctl, 0, hi.stream);
+    launch_dw_split(hi.d, hi.dwd, hi.init_chunks.view(), hi.stream);
     launch_norm_state<double>(hi.d, hi.init_strips.view(), hi.ctl, hi.partb, hi.stream);
     launch_defect(hi.d, lo.d, hi.init_strips.view(), hi.ctl, hi.part, hi.stream);
     launch_finalize<double>(hi.ctl, hi.d, (int)slots.size(), hi.part, hi.partb, FIN_INIT, 0, hi.bctl,
@@ -1239,6 +1267,7 @@ m1_status MixedModel::create(const std::vector<m1_grid_desc>& descs, cudaStream_
     const int L = descs[0].lmax;
     const int n = (int)descs.size();
     M1_TRY(hi.init(n, 1, false, s, n == 1 ? 20001 : 0));
+    M1_TRY(hi.enable_dw());
     M1_TRY(lo.init(n, L, true, hi.stream, 0));
     for (const auto& d : descs) {
         m1_grid_desc g = d;
@@ -1274,11 +1303,11 @@ void MixedModel::record_cycle(const Params& p, cudaStream_t s)
 {
     int cur0 = 0;
     lo.record_cycle(p, cur0, s, false);
-    launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s);
+    launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s, hi.dwd);
     // each instance's defect comes from one of the two: FP64, or double-word FP32
     // where its tolerance lies far above the double-word noise floor (FIN_INIT)
     launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
-    launch_defect_dw(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
+    launch_defect_dw(hi.d, lo.d, hi.dwd, hi.strips[0].view(), hi.ctl, hi.part, s);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, nullptr, FIN_CYCLE, 0, hi.bctl, s);
 }
 
@@ -1313,6 +1342,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
     M1_CK(cudaEventRecord(hi.ev0, s));
     const WorkList t0 = hi.strips[0].view(), c0 = hi.chunks[0].view();
     launch_make_rhs<double>(hi.d, c0, hi.ctl, 0, s);
+    launch_dw_split(hi.d, hi.dwd, c0, s);
     launch_norm_state<double>(hi.d, t0, hi.ctl, hi.partb, s);
     launch_defect(hi.d, lo.d, t0, hi.ctl, hi.part, s);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, hi.partb, FIN_INIT, 0, hi.bctl, s);

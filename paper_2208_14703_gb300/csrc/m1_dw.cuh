@@ -23,6 +23,21 @@ struct DW {
     float hi, lo;
 };
 
+// A cell's state (E, Fx, Fy, T) and opacities as double words, and the
+// per-slot double-word copies the mixed path's defect reads (fine level: the
+// iterate v, the right-hand side b, the opacities).
+struct alignas(32) DW4 {
+    DW E, Fx, Fy, T;
+};
+struct alignas(16) DW2 {
+    DW sa, ss;
+};
+struct DwLevel {
+    DW4* v;
+    DW4* b;
+    DW2* sig;
+};
+
 __device__ __forceinline__ DW two_sum(float a, float b)
 {
     const float s = a + b;
@@ -50,6 +65,11 @@ __device__ __forceinline__ DW dw_from(double x)
 }
 
 __device__ __forceinline__ double dw_to_double(DW x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ DW4 dw4_from(double E, double Fx, double Fy, double T)
+{
+    return DW4{ dw_from(E), dw_from(Fx), dw_from(Fy), dw_from(T) };
+}
 
 __device__ __forceinline__ DW operator-(DW x) { return DW{ -x.hi, -x.lo }; }
 

@@ -111,12 +111,18 @@ struct Engine {
     bool graph_dirty = true;
     std::vector<char> ring;                 // per level: the sweeps take the cp.async kernel
     std::vector<char> list_sig;             // which work lists were non-empty at capture
+    // double-word copies of each slot's level-0 iterate, right-hand side and
+    // opacities (the mixed path's FP64 level: its defect in double words)
+    bool dw = false;
+    DwLevel* dwd = nullptr;                 // device table [cap]
+    std::vector<DwLevel> dwh;               // host mirror
 
     ~Engine();
     std::vector<DevList*> all_lists();
     m1_status calloc_common(void** p, size_t bytes);
     m1_status slot_alloc(int i, void** p, size_t bytes);
     m1_status init(int capacity, int levels, bool correction_form, cudaStream_t s, int history_len);
+    m1_status enable_dw();
     m1_status add_slot(const m1_grid_desc& dsc, int* out);
     m1_status remove_slot(int i);
     m1_status ensure_stage(size_t n);

@@ -1144,22 +1144,22 @@ struct StagedDW {
 };
 
 struct LevelDW {
-    DW c, bx, by, diag, a_r, c_v, m3ic2, q3ic2, third;
+    DW c, bx, by, diag, a_r, c_v, cdt, m3ic2, q3ic2, third;
 };
 
 __device__ __forceinline__ LevelDW level_dw(const Level<double>& L)
 {
     return LevelDW{ dw_from(L.c), dw_from(L.bx), dw_from(L.by), dw_from(L.diag), dw_from(L.a_r),
-                    dw_from(L.c_v), dw_from(-3.0 * L.ic2), dw_from(3.0 * L.ic2),
+                    dw_from(L.c_v), dw_from(L.cdt), dw_from(-3.0 * L.ic2), dw_from(3.0 * L.ic2),
                     dw_from(1.0 / 3.0) };
 }
 
 // The closure of Eq. (5) in the form of closure(): s = sqrt(4 - 3 f^2) (f^2
 // clamped to 1), P = (s - 1)/3 E I + 3/(2 + s) F F^T / (c^2 E).
-__device__ __forceinline__ StagedDW stage_dw(const LevelDW& D, const Cell4<double>& c)
+__device__ __forceinline__ StagedDW stage_dw(const LevelDW& D, const DW4& c)
 {
     StagedDW o;
-    o.E = dw_from(c.E); o.Fx = dw_from(c.Fx); o.Fy = dw_from(c.Fy); o.T = dw_from(c.T);
+    o.E = c.E; o.Fx = c.Fx; o.Fy = c.Fy; o.T = c.T;
     const DW iE = dw_rcp(o.E);
     const DW fx = o.Fx * iE, fy = o.Fy * iE;
     DW a = (fy * fy + fx * fx) * D.m3ic2 + 4.f;
@@ -1189,13 +1189,13 @@ __device__ __forceinline__ StagedDW shfl_staged_dw(const StagedDW& v, int from)
 }
 
 // r = b - A(u) of one strip cell in double words (Eq. (13) with the [EXT]
-// sources), from the staged neighbours and the cell's own state.
-__device__ __forceinline__ void residual_dw(const Level<double>& L, const LevelDW& D,
-                                            const StagedDW& wv, const StagedDW& ev,
-                                            const StagedDW& prev, const StagedDW& next,
-                                            const StagedDW& cur, bool two_d,
-                                            const Cell4<double>& b, const Sig2<double>& sg,
-                                            DW& rE, DW& rFx, DW& rFy, DW& rT)
+// sources), from the staged neighbours, the cell's own state, its right-hand
+// side and opacities (double words).
+__device__ __forceinline__ void residual_dw(const LevelDW& D, const StagedDW& wv,
+                                            const StagedDW& ev, const StagedDW& prev,
+                                            const StagedDW& next, const StagedDW& cur, bool two_d,
+                                            const DW4& b, const DW2& sg, DW& rE, DW& rFx, DW& rFy,
+                                            DW& rT)
 {
     const DW cbx = D.c * D.bx;
     DW NE = D.bx * (D.c * (wv.E + ev.E) + (wv.Fx - ev.Fx));
@@ -1207,20 +1207,61 @@ __device__ __forceinline__ void residual_dw(const Level<double>& L, const LevelD
         NFx = NFx + cby * ((prev.Fx + next.Fx) + D.c * (prev.Pxy - next.Pxy));
         NFy = NFy + cby * ((prev.Fy + next.Fy) + D.c * (prev.Pyy - next.Pyy));
     }
-    const DW ka = dw_from(L.cdt * sg.sa), dk = dw_from(L.diag + L.cdt * (sg.sa + sg.ss));
+    const DW ka = D.cdt * sg.sa, dk = D.diag + D.cdt * (sg.sa + sg.ss);
     const DW T2 = cur.T * cur.T;
     const DW se = ka * (cur.E - D.a_r * (T2 * T2));
-    rE = dw_from(b.E) - ((D.diag * cur.E + se) - NE);
-    rFx = dw_from(b.Fx) - (dk * cur.Fx - NFx);
-    rFy = dw_from(b.Fy) - (dk * cur.Fy - NFy);
-    rT = dw_from(b.T) - (D.c_v * cur.T - se);
+    rE = b.E - ((D.diag * cur.E + se) - NE);
+    rFx = b.Fx - (dk * cur.Fx - NFx);
+    rFy = b.Fy - (dk * cur.Fy - NFy);
+    rT = b.T - (D.c_v * cur.T - se);
 }
 
-// The warp-strip march of strip_march with FP64 rows staged as double words.
+// A cell of a double-word state with the ghost rules of fetch(): periodic wrap,
+// reflecting mirror with the wall-normal flux negated, Neumann copy, inflow the
+// prescribed E, Fx, Fy (split from the FP64 profile) with T from the mirror
+// cell; a corner resolves the y wall first, the x wall on top.
+__device__ __forceinline__ DW4 fetch_dw(const Level<double>& L, const DW4* __restrict__ s, int i,
+                                        int j)
+{
+    const int jo = j;
+    int xrule = -1, xwall = 0, yrule = -1, ywall = 0;
+    if (i < 0 || i >= L.nx) {
+        xwall = i < 0 ? WALL_W : WALL_E;
+        const int bc = L.bc[xwall];
+        if (bc == BC_PERIODIC) i = i < 0 ? i + L.nx : i - L.nx;
+        else { i = i < 0 ? -1 - i : 2 * L.nx - 1 - i; xrule = bc; }
+    }
+    if (j < 0 || j >= L.ny) {
+        ywall = j < 0 ? WALL_S : WALL_N;
+        const int bc = L.bc[ywall];
+        if (bc == BC_PERIODIC) j = j < 0 ? j + L.ny : j - L.ny;
+        else { j = j < 0 ? -1 - j : 2 * L.ny - 1 - j; yrule = bc; }
+    }
+    DW4 c = s[(size_t)j * L.nx + i];
+    if (yrule == BC_REFLECT) c.Fy = -c.Fy;
+    if (yrule == BC_INFLOW) {
+        const double* p = L.inflow + (size_t)(ywall * 3) * L.prof_len;
+        c.E = dw_from(p[i]); c.Fx = dw_from(p[L.prof_len + i]); c.Fy = dw_from(p[2 * L.prof_len + i]);
+    }
+    if (xrule == BC_REFLECT) c.Fx = -c.Fx;
+    if (xrule == BC_INFLOW) {
+        const int jj = jo < 0 ? 0 : (jo >= L.ny ? L.ny - 1 : jo);
+        const double* p = L.inflow + (size_t)(xwall * 3) * L.prof_len;
+        c.E = dw_from(p[jj]); c.Fx = dw_from(p[L.prof_len + jj]); c.Fy = dw_from(p[2 * L.prof_len + jj]);
+    }
+    return c;
+}
+
+__device__ __forceinline__ DW4 load_dw(const Level<double>& L, const DW4* __restrict__ s, int i,
+                                       int j, bool fast)
+{
+    return fast ? s[(size_t)j * L.nx + i] : fetch_dw(L, s, i, j);
+}
+
+// The warp-strip march of strip_march over a double-word state.
 template <typename F>
 __device__ __forceinline__ void strip_march_dw(const Level<double>& L, const LevelDW& D, int2 it,
-                                               int lane, const Cell4<double>* __restrict__ src,
-                                               F&& cell)
+                                               int lane, const DW4* __restrict__ src, F&& cell)
 {
     const int nx = L.nx, ny = L.ny, two_d = L.dim == 2;
     const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
@@ -1229,18 +1270,18 @@ __device__ __forceinline__ void strip_march_dw(const Level<double>& L, const Lev
     const bool own = lane >= 1 && lane <= kStripW && i < nx;
     const int rows = min(L.sh, ny - y0);
     StagedDW prev{}, cur, next{};
-    Raw<double> rn{};
+    DW4 rn{};
     if (two_d) {
-        prev = stage_dw(D, load_raw<double, false>(L, src, i, y0 - 1, colfast && y0 >= 1).c);
-        rn = load_raw<double, false>(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
+        prev = stage_dw(D, load_dw(L, src, i, y0 - 1, colfast && y0 >= 1));
+        rn = load_dw(L, src, i, y0 + 1, colfast && y0 + 1 < ny);
     }
-    cur = stage_dw(D, load_raw<double, false>(L, src, i, y0, colfast).c);
+    cur = stage_dw(D, load_dw(L, src, i, y0, colfast));
     size_t k = (size_t)y0 * nx + i;
     for (int r = 0; r < rows; ++r, k += nx) {
         const int j = y0 + r;
         if (two_d) {
-            next = stage_dw(D, rn.c);
-            if (r + 1 < rows) rn = load_raw<double, false>(L, src, i, j + 2, colfast && j + 2 < ny);
+            next = stage_dw(D, rn);
+            if (r + 1 < rows) rn = load_dw(L, src, i, j + 2, colfast && j + 2 < ny);
         }
         const StagedDW wv = shfl_staged_dw(cur, (lane + 31) & 31);
         const StagedDW ev = shfl_staged_dw(cur, (lane + 1) & 31);
@@ -1250,11 +1291,44 @@ __device__ __forceinline__ void strip_march_dw(const Level<double>& L, const Lev
     }
 }
 
+// Double-word copies of one slot's fine-level iterate, right-hand side and
+// opacities (at the start of a step; the FP64 arrays stay the reference).
+__global__ void __launch_bounds__(kThreads) k_dw_split(const Level<double>* __restrict__ lv,
+                                                       const DwLevel* __restrict__ dwd, WorkList wl)
+{
+    __shared__ Level<double> L;
+    const int nw = *wl.count;
+    int inst = -1;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl.items[w];
+        if (it.x != inst) {
+            __syncthreads();
+            load_level(L, lv + it.x);
+            __syncthreads();
+            inst = it.x;
+        }
+        const int k = it.y * kThreads + threadIdx.x;
+        if (k < L.n) {
+            const DwLevel D = dwd[it.x];
+            const Cell4<double> u = L.u[0][k], b = L.f[k];
+            const Sig2<double> g = L.sig[k];
+            D.v[k] = dw4_from(u.E, u.Fx, u.Fy, u.T);
+            D.b[k] = dw4_from(b.E, b.Fx, b.Fy, b.T);
+            D.sig[k] = DW2{ dw_from(g.sa), dw_from(g.ss) };
+        }
+    }
+}
+
 // k_defect in double words: the same outputs (norm partials, and the FP32
 // problem w = fl32(v), e = 0, g = fl32(r)) for the instances whose control
-// block selected it (tol ||r_0|| far above the double-word noise floor).
+// block selected it (tol ||r_0|| far above the double-word noise floor).  It
+// reads only the double-word copies of the iterate (kept by k_accumulate), the
+// right-hand side and the opacities, so no FP64 operation is left per cell;
+// the norm is summed in FP32 from the leading words (about 1e-7 relative, far
+// inside what the stop test and the dtau_im control resolve).
 __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<double>* __restrict__ lv64,
                                                                 const Level<float>* __restrict__ lv32,
+                                                                const DwLevel* __restrict__ dwd,
                                                                 WorkList wl, Ctl* __restrict__ ctls,
                                                                 double* __restrict__ partials)
 {
@@ -1276,30 +1350,31 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<doub
             __syncwarp();
         }
         const LevelDW D = level_dw(L);
+        const DwLevel S = dwd[it.x];
         const bool two_d = L.dim == 2;
-        double nrm = 0.0;
-        strip_march_dw(L, D, it, lane, L.u[0], [&](size_t k, const StagedDW& wv, const StagedDW& ev,
-                                                    const StagedDW& prev, const StagedDW& next,
-                                                    const StagedDW& cur) {
+        const float ic2 = (float)L.ic2;
+        float nrm = 0.f;
+        strip_march_dw(L, D, it, lane, S.v, [&](size_t k, const StagedDW& wv, const StagedDW& ev,
+                                                 const StagedDW& prev, const StagedDW& next,
+                                                 const StagedDW& cur) {
             DW rE, rFx, rFy, rT;
-            residual_dw(L, D, wv, ev, prev, next, cur, two_d, L.f[k], L.sig[k], rE, rFx, rFy, rT);
-            const double e = dw_to_double(rE), fx = dw_to_double(rFx), fy = dw_to_double(rFy),
-                         t = dw_to_double(rT);
-            nrm += e * e + (fx * fx + fy * fy) * L.ic2 + t * t;
+            residual_dw(D, wv, ev, prev, next, cur, two_d, S.b[k], S.sig[k], rE, rFx, rFy, rT);
+            nrm += rE.hi * rE.hi + (rFx.hi * rFx.hi + rFy.hi * rFy.hi) * ic2 + rT.hi * rT.hi;
             M.w[k] = Cell4<float>{ cur.E.hi, cur.Fx.hi, cur.Fy.hi, cur.T.hi };
             M.f[k] = Cell4<float>{ rE.hi, rFx.hi, rFy.hi, rT.hi };
             M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
         });
-        const double sum = warp_sum(nrm);
+        const double sum = warp_sum((double)nrm);
         if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
         __syncwarp();
     }
 }
 
 // The double-word residual alone, r = b - A(u) written in FP64 (hi + lo) with
-// its norm partials: a check of k_defect_dw's arithmetic (m1_op_level).
+// FP64 norm partials: a check of k_defect_dw's arithmetic (m1_op_level).  It
+// splits the FP64 state, right-hand side and opacities as it reads them.
 __global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<double>* __restrict__ lv,
-                                                                  WorkList wl,
+                                                                  WorkList wl, DW4* __restrict__ sv,
                                                                   double* __restrict__ partials)
 {
     __shared__ Level<double> Ls[kStripWarps];
@@ -1312,11 +1387,14 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<do
         const LevelDW D = level_dw(L);
         const bool two_d = L.dim == 2;
         double nrm = 0.0;
-        strip_march_dw(L, D, it, lane, L.u[0], [&](size_t k, const StagedDW& wv, const StagedDW& ev,
-                                                    const StagedDW& prev, const StagedDW& next,
-                                                    const StagedDW& cur) {
+        strip_march_dw(L, D, it, lane, sv, [&](size_t k, const StagedDW& wv, const StagedDW& ev,
+                                                const StagedDW& prev, const StagedDW& next,
+                                                const StagedDW& cur) {
+            const Cell4<double> b = L.f[k];
+            const Sig2<double> g = L.sig[k];
             DW rE, rFx, rFy, rT;
-            residual_dw(L, D, wv, ev, prev, next, cur, two_d, L.f[k], L.sig[k], rE, rFx, rFy, rT);
+            residual_dw(D, wv, ev, prev, next, cur, two_d, dw4_from(b.E, b.Fx, b.Fy, b.T),
+                        DW2{ dw_from(g.sa), dw_from(g.ss) }, rE, rFx, rFy, rT);
             const Cell4<double> r = { dw_to_double(rE), dw_to_double(rFx), dw_to_double(rFy),
                                       dw_to_double(rT) };
             L.r[k] = r;
@@ -1328,11 +1406,21 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<do
     }
 }
 
+// The double-word copy of a level-0 state (for k_residual_dw).
+__global__ void k_split_state_dw(const Cell4<double>* __restrict__ u, DW4* __restrict__ out, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = dw4_from(u[k].E, u[k].Fx, u[k].Fy, u[k].T);
+}
+
 // k_accumulate: v64 += e in FP64 (e = the FP32 cycle's correction in buffer
 // `buf`); a cell whose update leaves the admissible set takes
-// v64 + theta_c min(1, tau*) e instead (the damping rule of Eq. (34)).
+// v64 + theta_c min(1, tau*) e instead (the damping rule of Eq. (34)).  For an
+// instance whose defect is formed in double words, it also writes the
+// double-word copy of the new iterate (dwd: per-slot copies, or null).
 __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __restrict__ lv64,
                                                          const Level<float>* __restrict__ lv32,
+                                                         const DwLevel* __restrict__ dwd,
                                                          WorkList wl, Ctl* __restrict__ ctls,
                                                          int buf)
 {
@@ -1369,6 +1457,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
                 atomicAdd(&ctl->damped, 1u);
             }
             L.u[0][k] = tg;
+            if (dwd && ctl->defect_dw) dwd[it.x].v[k] = dw4_from(tg.E, tg.Fx, tg.Fy, tg.T);
         }
     }
 }
@@ -1525,21 +1614,28 @@ void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList
     k_defect<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
 }
 
-void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
-                      double* partials, cudaStream_t s)
+void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, const DwLevel* dwd,
+                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s)
 {
-    k_defect_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
+    k_defect_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, dwd, wl, ctls, partials);
 }
 
-void launch_residual_dw(const Level<double>* lv, WorkList wl, double* partials, cudaStream_t s)
+void launch_dw_split(const Level<double>* lv, const DwLevel* dwd, WorkList wl, cudaStream_t s)
 {
-    k_residual_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv, wl, partials);
+    k_dw_split<<<pgrid(wl), kThreads, 0, s>>>(lv, dwd, wl);
+}
+
+void launch_residual_dw(const Level<double>* lv, const Cell4<double>* u, DW4* scratch, int n,
+                        WorkList wl, double* partials, cudaStream_t s)
+{
+    k_split_state_dw<<<cdiv(n, kThreads), kThreads, 0, s>>>(u, scratch, n);
+    k_residual_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv, wl, scratch, partials);
 }
 
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,
-                       Ctl* ctls, int buf, cudaStream_t s)
+                       Ctl* ctls, int buf, cudaStream_t s, const DwLevel* dwd)
 {
-    k_accumulate<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, wl, ctls, buf);
+    k_accumulate<<<pgrid(wl), kThreads, 0, s>>>(lv64, lv32, dwd, wl, ctls, buf);
 }
 
 #define M1_INSTANTIATE(R)                                                                          \

@@ -3,6 +3,7 @@
 // instance), a work list over that level and the instances' control blocks.
 #pragma once
 #include "m1_device.cuh"
+#include "m1_dw.cuh"
 
 namespace m1 {
 
@@ -54,11 +55,15 @@ void launch_fas_aw32(const Level<float>* lv, WorkList wl, Ctl* ctls, cudaStream_
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
                    double* partials, cudaStream_t s);
 // the defect in double-word FP32, for the instances whose control block chose it
-void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
-                      double* partials, cudaStream_t s);
-// the double-word residual r = b - A(u) alone (written in FP64), for checks
-void launch_residual_dw(const Level<double>* lv, WorkList wl, double* partials, cudaStream_t s);
+void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, const DwLevel* dwd,
+                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s);
+// double-word copies of the fine level's iterate, right-hand side and opacities
+void launch_dw_split(const Level<double>* lv, const DwLevel* dwd, WorkList wl, cudaStream_t s);
+// the double-word residual r = b - A(u) of level-0 state u alone (written in FP64),
+// for checks; scratch: n double-word cells
+void launch_residual_dw(const Level<double>* lv, const Cell4<double>* u, DW4* scratch, int n,
+                        WorkList wl, double* partials, cudaStream_t s);
 void launch_accumulate(const Level<double>* lv64, const Level<float>* lv32, WorkList wl,
-                       Ctl* ctls, int buf, cudaStream_t s);
+                       Ctl* ctls, int buf, cudaStream_t s, const DwLevel* dwd = nullptr);
 
 }  // namespace m1

@@ -29,7 +29,7 @@ namespace m1 {
 namespace {
 
 constexpr int kClasses = 16;                 // size classes 2^0 .. 2^15 (sqrt of the cell count)
-constexpr int kCandidates[] = { 1, 2, 4, 8, 12, 16, 24, 32 };
+constexpr int kCandidates[] = { 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128 };
 
 std::mutex g_tune_mu;
 int g_rows[2][kClasses] = {};                // [kind][class], 0 = untuned
@@ -193,7 +193,7 @@ m1_status m1_set_tuning(const m1_tune_entry* in, int n)
     if (n < 0 || (n > 0 && !in)) return M1_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k)
         if ((in[k].kind != 0 && in[k].kind != 1) || in[k].n < 1 || in[k].strip_rows < 0 ||
-            in[k].strip_rows > 64 || in[k].staging < 0 || in[k].staging > 1 ||
+            in[k].strip_rows > 256 || in[k].staging < 0 || in[k].staging > 1 ||
             (in[k].kind == 0 && in[k].staging != 0))
             return M1_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(m1::g_tune_mu);

@@ -38,6 +38,10 @@ def test_installed_entries_and_reset(restore_tuning):
         m1.set_tuning([{"kind": 2, "n": 256, "strip_rows": 8}])
     with pytest.raises(m1.M1Error):
         m1.set_tuning([{"kind": 0, "n": 256, "strip_rows": 8, "staging": 1}])
+    m1.set_tuning([{"kind": 1, "n": 4096, "strip_rows": 128, "staging": 1}])
+    assert m1.strip_rows(1, 4096, 4096) == 128
+    with pytest.raises(m1.M1Error):
+        m1.set_tuning([{"kind": 1, "n": 4096, "strip_rows": 257}])
 
 
 @pytest.mark.gpu
@@ -46,7 +50,8 @@ def test_autotune_entries(restore_tuning):
     assert {(e["kind"], e["n"]) for e in ent} == (
         {(0, 1 << c) for c in range(4, 12)} | {(1, 1 << c) for c in range(4, 13)})
     for e in ent:
-        assert e["strip_rows"] in (1, 2, 4, 8, 12, 16, 24, 32) and e["strip_rows"] <= e["n"]
+        assert e["strip_rows"] in (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128)
+        assert e["strip_rows"] <= e["n"]
         assert e["staging"] in ((0,) if e["kind"] == 0 else (0, 1))
         assert e["ms"] > 0 and (np.isnan(e["ms_default"]) or e["ms"] <= e["ms_default"])
         assert m1.strip_rows(e["kind"], e["n"], e["n"]) == e["strip_rows"]
