@@ -54,8 +54,8 @@ def peaks():
 # Bytes: read the iterate u, the right-hand side b and (sigma_a, sigma_s); write u'.
 SWEEP_BYTES = 4 * 8 + 4 * 8 + 2 * 8 + 4 * 8
 # DRAM bytes per cell of the FP64 sweep kernel measured by ncu on one 2048^2
-# launch (dram__bytes_read.sum + dram__bytes_write.sum = 457.2 MB / 4,194,304 cells)
-SWEEP64_TRAFFIC_PER_CELL = 457.2e6 / (2048 * 2048)
+# launch (dram__bytes_read.sum + dram__bytes_write.sum = 458.3 MB / 4,194,304 cells)
+SWEEP64_TRAFFIC_PER_CELL = 458.3e6 / (2048 * 2048)
 # FP64 work of one fine Jacobi update (2D), counted in FP64-pipe operations
 # (each DFMA, DMUL, DADD, FP64 compare or FP32<->FP64 conversion is one issue
 # slot; a reciprocal = hardware estimate + 3 DFMA of third-order refinement = 4;
@@ -761,7 +761,7 @@ def main():
             "frac_of_derived": tops / FP64_PEAK_TOPS,
             "ops_per_cell": SWEEP_OPS, "op": "FP64-pipe operation (DFMA, DMUL, DADD, FP64 compare or conversion)",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                              "2048^2 launch (457.2 MB), scaled to 1024^2 by cells",
+                              "2048^2 launch (458.3 MB), scaled to 1024^2 by cells",
             "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / pk["hbm_gbs"], "bytes_per_cell": SWEEP_BYTES}}
 
