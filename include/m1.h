@@ -296,6 +296,41 @@ m1_status m1_strip_rows(int kind, int nx, int ny, int* rows);
  * precision; CUDA: a failed allocation, launch or event (m1_last_error). */
 m1_status m1_probe_fma_peak(int precision, void* cuda_stream, int reps, double* ops_per_s);
 
+/* ---- FP64 <-> double-word FP32 conversions (host runs of the device code) ----
+ * The mixed path keeps double-word copies (hi + lo, two FP32 numbers) of its
+ * fine-level FP64 arrays and widens the FP32 cycle's correction to FP64.  It
+ * does both with integer and FP32 operations on the bit patterns instead of
+ * conversion instructions, which GB300 issues at the FP64 rate (1/64 of FP32).
+ * These entry points run the same inline functions on the host, so that they
+ * can be checked without a GPU:
+ *   m1_dw_split:  hi[i] = fl32(x[i]), lo[i] = fl32(x[i] - hi[i]), both rounded
+ *                 to nearest even (x[i] - hi[i] is exact in FP64);
+ *   m1_f32_widen: y[i] = (double)x[i].
+ * Host pointers to n >= 0 elements; nothing is allocated.  INVALID_ARG: n < 0,
+ * or a NULL pointer with n > 0. */
+m1_status m1_dw_split(const double* x, long long n, float* hi, float* lo);
+m1_status m1_f32_widen(const float* x, long long n, double* y);
+
+/* ---- the kernels' per-element arithmetic on the device (for checks) ----
+ * y[i] = f(x[i]) for 0 <= i < n, computed on the device by the inline functions
+ * the kernels call, so that tests can hold them against correctly rounded
+ * results (IEEE division and square root, IEEE conversions):
+ *   M1_FN_RCP64     double -> double: 1/x, the hardware estimate with one
+ *                   third-order correction (positive normal x);
+ *   M1_FN_SQRT64    double -> double: sqrt(x), the same construction;
+ *   M1_FN_RCP32     float -> float: the approximate FP32 reciprocal;
+ *   M1_FN_SQRT32    float -> float: the approximate FP32 square root;
+ *   M1_FN_DW_SPLIT  double -> float pairs: y[2i] = hi, y[2i+1] = lo (as m1_dw_split);
+ *   M1_FN_WIDEN     float -> double (as m1_f32_widen).
+ * x and y are device pointers (y holds n results, 2n floats for the split);
+ * one launch on cuda_stream (NULL: the legacy default stream), and the call
+ * returns after synchronising that stream.  INVALID_ARG: n < 0, a NULL pointer
+ * with n > 0, or an unknown fn; CUDA: the launch or the kernel failed
+ * (m1_last_error). */
+enum { M1_FN_RCP64 = 0, M1_FN_SQRT64 = 1, M1_FN_RCP32 = 2, M1_FN_SQRT32 = 3, M1_FN_DW_SPLIT = 4,
+       M1_FN_WIDEN = 5 };
+m1_status m1_op_elementwise(int fn, const void* x, long long n, void* y, void* cuda_stream);
+
 /* ---- single-kernel entry points (one kernel on caller data, for checks) ----
  * Stateless: each call allocates its own device buffers for `desc` (lmax is
  * ignored; precision selects FP64 or FP32 arithmetic), runs one kernel on the

@@ -1634,4 +1634,22 @@ m1_status m1_op_prolong_correct(const m1_grid_desc* fine, const double* uc, cons
     return e->op_prolong(uc, vc, uf, theta, out, damped);
 }
 
+m1_status m1_dw_split(const double* x, long long n, float* hi, float* lo)
+{
+    if (n < 0 || (n > 0 && (!x || !hi || !lo))) return M1_ERR_INVALID_ARG;
+    for (long long i = 0; i < n; ++i) {
+        const m1::DW d = m1::dw_split(x[i]);
+        hi[i] = d.hi;
+        lo[i] = d.lo;
+    }
+    return M1_OK;
+}
+
+m1_status m1_f32_widen(const float* x, long long n, double* y)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return M1_ERR_INVALID_ARG;
+    for (long long i = 0; i < n; ++i) y[i] = m1::widen(x[i]);
+    return M1_OK;
+}
+
 }  // extern "C"

@@ -8,6 +8,7 @@
 #pragma once
 #include <cfloat>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace m1 {
@@ -108,6 +109,71 @@ struct WorkList {
 
 // Blocks of a persistent launch: 4 resident CTAs on each of the 152 SMs.
 constexpr int kPersistentBlocks = 152 * 4;
+
+// ---------------------------------------------------------------------------
+// FP32 <-> FP64 conversions without conversion instructions.  GB300 issues
+// FP64 instructions, the conversions between FP64 and FP32 among them, at 1/64
+// of the FP32 rate, and the FP64 kernels are bound by that pipe; these forms
+// use integer and FP32 operations on the bit patterns and give exactly the
+// IEEE results (round to nearest even).  Values outside the ranges they cover
+// call the conversion out of line, so that the compiler branches around it
+// instead of evaluating it for every value and selecting.
+__host__ __device__ __forceinline__ float float_of_bits(unsigned u)
+{
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+__host__ __device__ __forceinline__ unsigned bits_of_float(float f)
+{
+    unsigned u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+// An integer 0 <= m < 2^23 as an FP32 number: 2^23 + m is exact in FP32 and
+// the subtraction of 2^23 is exact.
+__host__ __device__ __forceinline__ float small_uint_to_float(unsigned m)
+{
+    return float_of_bits(0x4b000000u | m) - 8388608.0f;
+}
+
+static __host__ __device__ __noinline__ double widen_call(float x) { return (double)x; }
+static __host__ __device__ __noinline__ float narrow_call(double x) { return (float)x; }
+
+// (double)x: for x normal or zero the exponent is rebiased by 1023 - 127 and
+// the significand moved to the top of FP64's 52 bits; subnormals, infinities
+// and NaN take the conversion.
+__host__ __device__ __forceinline__ double widen(float x)
+{
+    const unsigned u = bits_of_float(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned long long b = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e - 1u <= 253u)
+        b |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    else if ((u & 0x7fffffffu) != 0)
+        return widen_call(x);
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+// (float)x: with x = M 2^(e-1075) (M the 53-bit significand, e the biased
+// exponent), M rounded to nearest-even at bit 29 (a carry into the exponent
+// field is the correct rounding, up to infinity past FLT_MAX) and rebiased.
+// Covers e in [897, 1150], the x whose FP32 rounding is normal or infinite;
+// zero, subnormal results, infinities and NaN take the conversion.
+__host__ __device__ __forceinline__ float narrow(double x)
+{
+    unsigned long long b;
+    memcpy(&b, &x, sizeof b);
+    const unsigned long long a = b & 0x7fffffffffffffffull;
+    const unsigned e = (unsigned)(a >> 52);
+    if (e - 897u > 1150u - 897u) return narrow_call(x);
+    const unsigned long long q = (a + 0x0fffffffull + ((a >> 29) & 1ull)) >> 29;
+    return float_of_bits(((unsigned)q - (896u << 23)) | ((unsigned)(b >> 32) & 0x80000000u));
+}
 
 // ---------------------------------------------------------------------------
 // Reciprocal and square root of the per-cell arithmetic.
@@ -273,11 +339,11 @@ template <> struct Quartic<double> {
     __device__ static double solve(double C, double K, double Rr, bool& ok)
     {
         bool ok32;
-        const float T32 = newton_quartic_f32((float)C, (float)K, (float)Rr, ok32);
+        const float T32 = newton_quartic_f32(narrow(C), narrow(K), narrow(Rr), ok32);
         // FP32 seeds only a finite positive root that its iteration reached;
         // every comparison below is false for a NaN, which takes the FP64 path
         if (!(ok32 && T32 > 0.0f && T32 <= FLT_MAX)) return newton_quartic_f64(C, K, Rr, ok);
-        double T = (double)T32;
+        double T = widen(T32);
         // One step of Halley's method (cubically convergent):
         // T <- T - 2 g g' / (2 g'^2 - g g'') = T - g g' / (g'^2 - 6 K T^2 g),
         // g' = C + 4 K T^3, g'' = 12 K T^2.  From the FP32 root (relative
@@ -291,10 +357,11 @@ template <> struct Quartic<double> {
         const double g = fma(KT2, T2, fma(C, T, -Rr));
         const double d1 = fma(4.0 * KT2, T, C);
         const double den = fma(d1, d1, -(6.0 * KT2) * g);
-        const float denf = fabsf((float)den);
+        const float den32 = narrow(den);
+        const float denf = fabsf(den32);
         double r;
         if (denf >= FLT_MIN && denf <= FLT_MAX) {
-            r = (double)Fm<float>::rcp((float)den);
+            r = widen(Fm<float>::rcp(den32));
             r = fma(r, fma(-den, r, 1.0), r);
         } else {
             r = 1.0 / den;

@@ -15,7 +15,10 @@
 // bits costs fewer FP32 issue slots as double words than FP64 slots: the
 // mixed-precision defect uses this when its tolerance allows (m1_kernels.cu).
 #pragma once
+#include <cstring>
 #include <cuda_runtime.h>
+
+#include "m1_device.cuh"   // float_of_bits, bits_of_float, widen
 
 namespace m1 {
 
@@ -58,17 +61,56 @@ __device__ __forceinline__ DW two_prod(float a, float b)
     return DW{ p, fmaf(a, b, -p) };
 }
 
-__device__ __forceinline__ DW dw_from(double x)
+__host__ __device__ __forceinline__ DW dw_from(double x)
 {
     const float h = (float)x;
     return DW{ h, (float)(x - (double)h) };
 }
 
+// dw_from as a call, for the values dw_split's integer form does not cover:
+// kept out of line so that the compiler branches around it instead of
+// evaluating it for every value and selecting.
+static __host__ __device__ __noinline__ DW dw_from_call(double x) { return dw_from(x); }
+
+// The pair dw_from(x) by integer and FP32 operations on the bit pattern of x.
+// GB300 issues FP64 instructions, the conversions between FP64 and FP32 among
+// them, at 1/64 of the FP32 rate, and the three conversions of dw_from bound
+// the kernels that split every cell of a level.  With x = M 2^(e-1075), M the
+// 53-bit significand and e the biased exponent: hi = M rounded to nearest-even
+// at bit 29 (a carry into the exponent field is the correct rounding),
+// rebiased to FP32; lo = (M - hi's significand) 2^(e-1075), an integer of at
+// most 29 bits, formed in FP32 as two exact 15-bit halves joined by one
+// fused multiply-add (a single rounding to nearest) and scaled by the power
+// of two, exact while it stays normal.  That holds for 2^-74 <= |x| < 2^127
+// (e in [949, 1149]); zero is handled here too, and the other values call
+// dw_from, so the result equals dw_from(x) for every x.
+__host__ __device__ __forceinline__ DW dw_split(double x)
+{
+    unsigned long long b;
+    memcpy(&b, &x, sizeof b);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned long long a = b & 0x7fffffffffffffffull;
+    if (a == 0) return DW{ float_of_bits(sign), 0.0f };
+    const unsigned e = (unsigned)(a >> 52);
+    if (e - 949u > 1149u - 949u) return dw_from_call(x);
+    const unsigned long long q = (a + 0x0fffffffull + ((a >> 29) & 1ull)) >> 29;
+    const bool up = q != (a >> 29);
+    const unsigned low = (unsigned)a & 0x1fffffffu;
+    const unsigned m = up ? 0x20000000u - low : low;        // |lo| in units of 2^(e-1075)
+    const float scale = float_of_bits((e - 948u) << 23);     // 2^(e-1075)
+    const float mag = fmaf(small_uint_to_float(m >> 15), 32768.0f * scale,
+                           small_uint_to_float(m & 0x7fffu) * scale);
+    const bool neg = (sign != 0) != up;
+    return DW{ float_of_bits(((unsigned)q - (896u << 23)) | sign),
+               float_of_bits(bits_of_float(mag) | (neg && m != 0 ? 0x80000000u : 0u)) };
+}
+
+
 __device__ __forceinline__ double dw_to_double(DW x) { return (double)x.hi + (double)x.lo; }
 
 __device__ __forceinline__ DW4 dw4_from(double E, double Fx, double Fy, double T)
 {
-    return DW4{ dw_from(E), dw_from(Fx), dw_from(Fy), dw_from(T) };
+    return DW4{ dw_split(E), dw_split(Fx), dw_split(Fy), dw_split(T) };
 }
 
 __device__ __forceinline__ DW operator-(DW x) { return DW{ -x.hi, -x.lo }; }

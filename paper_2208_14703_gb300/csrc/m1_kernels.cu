@@ -1123,8 +1123,8 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
             const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
             const double rT = b.T - (L.c_v * u.T - se);
             nrm += rE * rE + (rFx * rFx + rFy * rFy) * L.ic2 + rT * rT;
-            M.w[k] = Cell4<float>{ (float)u.E, (float)u.Fx, (float)u.Fy, (float)u.T };
-            M.f[k] = Cell4<float>{ (float)rE, (float)rFx, (float)rFy, (float)rT };
+            M.w[k] = Cell4<float>{ narrow(u.E), narrow(u.Fx), narrow(u.Fy), narrow(u.T) };
+            M.f[k] = Cell4<float>{ narrow(rE), narrow(rFx), narrow(rFy), narrow(rT) };
             M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
         });
         const double sum = warp_sum(nrm);
@@ -1314,7 +1314,7 @@ __global__ void __launch_bounds__(kThreads) k_dw_split(const Level<double>* __re
             const Sig2<double> g = L.sig[k];
             D.v[k] = dw4_from(u.E, u.Fx, u.Fy, u.T);
             D.b[k] = dw4_from(b.E, b.Fx, b.Fy, b.T);
-            D.sig[k] = DW2{ dw_from(g.sa), dw_from(g.ss) };
+            D.sig[k] = DW2{ dw_split(g.sa), dw_split(g.ss) };
         }
     }
 }
@@ -1394,7 +1394,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<do
             const Sig2<double> g = L.sig[k];
             DW rE, rFx, rFy, rT;
             residual_dw(D, wv, ev, prev, next, cur, two_d, dw4_from(b.E, b.Fx, b.Fy, b.T),
-                        DW2{ dw_from(g.sa), dw_from(g.ss) }, rE, rFx, rFy, rT);
+                        DW2{ dw_split(g.sa), dw_split(g.ss) }, rE, rFx, rFy, rT);
             const Cell4<double> r = { dw_to_double(rE), dw_to_double(rFx), dw_to_double(rFy),
                                       dw_to_double(rT) };
             L.r[k] = r;
@@ -1442,8 +1442,8 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
         const int k = it.y * kThreads + threadIdx.x;
         if (k < L.n) {
             const Cell4<float> a = M.u[buf][k];
-            Cell4<double> e = { (double)a.E, (double)a.Fx, (double)a.Fy, (double)a.T };
-            if (!(isfinite(e.E) && isfinite(e.Fx) && isfinite(e.Fy) && isfinite(e.T))) {
+            Cell4<double> e = { widen(a.E), widen(a.Fx), widen(a.Fy), widen(a.T) };
+            if (!(isfinite(a.E) && isfinite(a.Fx) && isfinite(a.Fy) && isfinite(a.T))) {
                 // a correction the FP32 cycle could not form is dropped (counted)
                 e.E = e.Fx = e.Fy = e.T = 0.0;
                 atomicAdd(&ctl->newton_fail, 1u);

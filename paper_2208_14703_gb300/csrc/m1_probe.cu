@@ -9,6 +9,11 @@
 // sum, so the compiler cannot drop the work.  A launch is 152 x 8 blocks of 256
 // threads; the count of FMA instructions per launch (summed over lanes) is
 // blocks x threads x kChains x iters.
+//
+// Also here: m1_op_elementwise, which runs the kernels' inline per-element
+// arithmetic (the FP64 reciprocal and square root, the FP32 approximations,
+// the double-word split and the FP32 -> FP64 widening) on caller data, so that
+// tests can hold it against correctly rounded results.
 #include <m1.h>
 
 #include <algorithm>
@@ -16,6 +21,9 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+
+#include "m1_device.cuh"
+#include "m1_dw.cuh"
 
 namespace m1 {
 void set_error_text(const char* msg);   // m1_api.cu: the text m1_last_error returns
@@ -87,6 +95,65 @@ m1_status probe(cudaStream_t s, int reps, double* ops_per_s)
 }
 
 }  // namespace
+
+namespace {
+
+template <int FN>
+__global__ void __launch_bounds__(256) k_elementwise(const void* __restrict__ x, long long n,
+                                                     void* __restrict__ y)
+{
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += step) {
+        if constexpr (FN == M1_FN_RCP64) {
+            ((double*)y)[i] = m1::Fm<double>::rcp(((const double*)x)[i]);
+        } else if constexpr (FN == M1_FN_SQRT64) {
+            ((double*)y)[i] = m1::Fm<double>::sqrt(((const double*)x)[i]);
+        } else if constexpr (FN == M1_FN_RCP32) {
+            ((float*)y)[i] = m1::Fm<float>::rcp(((const float*)x)[i]);
+        } else if constexpr (FN == M1_FN_SQRT32) {
+            ((float*)y)[i] = m1::Fm<float>::sqrt(((const float*)x)[i]);
+        } else if constexpr (FN == M1_FN_DW_SPLIT) {
+            const m1::DW d = m1::dw_split(((const double*)x)[i]);
+            ((float2*)y)[i] = make_float2(d.hi, d.lo);
+        } else {
+            ((double*)y)[i] = m1::widen(((const float*)x)[i]);
+        }
+    }
+}
+
+template <int FN>
+cudaError_t launch_elementwise(const void* x, long long n, void* y, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_elementwise<FN><<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(x, n, y);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" m1_status m1_op_elementwise(int fn, const void* x, long long n, void* y,
+                                       void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y)) || fn < M1_FN_RCP64 || fn > M1_FN_WIDEN)
+        return M1_ERR_INVALID_ARG;
+    if (n == 0) return M1_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSuccess;
+    switch (fn) {
+    case M1_FN_RCP64: e = launch_elementwise<M1_FN_RCP64>(x, n, y, s); break;
+    case M1_FN_SQRT64: e = launch_elementwise<M1_FN_SQRT64>(x, n, y, s); break;
+    case M1_FN_RCP32: e = launch_elementwise<M1_FN_RCP32>(x, n, y, s); break;
+    case M1_FN_SQRT32: e = launch_elementwise<M1_FN_SQRT32>(x, n, y, s); break;
+    case M1_FN_DW_SPLIT: e = launch_elementwise<M1_FN_DW_SPLIT>(x, n, y, s); break;
+    default: e = launch_elementwise<M1_FN_WIDEN>(x, n, y, s); break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        m1::set_error_text(cudaGetErrorString(e));
+        return M1_ERR_CUDA;
+    }
+    return M1_OK;
+}
 
 extern "C" m1_status m1_probe_fma_peak(int precision, void* cuda_stream, int reps,
                                        double* ops_per_s)

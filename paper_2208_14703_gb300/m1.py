@@ -42,6 +42,7 @@ EXPORTS = ["m1_default_params", "m1_create_grid", "m1_destroy_grid", "m1_set_sta
            "m1_batch_implicit_step", "m1_server_create", "m1_serve_submit", "m1_serve_poll",
            "m1_serve_wait", "m1_server_get_stats", "m1_server_destroy", "m1_autotune",
            "m1_set_tuning", "m1_strip_rows", "m1_op_level3", "m1_probe_fma_peak",
+           "m1_op_elementwise", "m1_dw_split", "m1_f32_widen",
            "m1_create_grid3", "m1_destroy_grid3", "m1_grid3_set_state", "m1_grid3_set_inflow",
            "m1_grid3_get_state", "m1_grid3_implicit_step", "m1_grid3_step_history"]
 
@@ -147,6 +148,9 @@ _lib.m1_set_tuning.argtypes = [ctypes.POINTER(TuneEntry), ctypes.c_int]
 _lib.m1_strip_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
 _lib.m1_probe_fma_peak.argtypes = [ctypes.c_int, _vp, ctypes.c_int, _dp]
+_lib.m1_op_elementwise.argtypes = [ctypes.c_int, _vp, ctypes.c_longlong, _vp, _vp]
+_lib.m1_dw_split.argtypes = [_vp, ctypes.c_longlong, _vp, _vp]
+_lib.m1_f32_widen.argtypes = [_vp, ctypes.c_longlong, _vp]
 _lib.m1_op_restrict.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _vp, _vp]
 _lib.m1_op_prolong_correct.argtypes = [ctypes.POINTER(GridDesc), _vp, _vp, _vp, ctypes.c_double,
                                        _vp, ctypes.POINTER(ctypes.c_int)]
@@ -445,6 +449,46 @@ def probe_fma_peak(precision=FP64, stream=None, reps=5):
     out = ctypes.c_double()
     _check(_lib.m1_probe_fma_peak(precision, stream, reps, ctypes.byref(out)), "m1_probe_fma_peak")
     return out.value
+
+
+FN_RCP64, FN_SQRT64, FN_RCP32, FN_SQRT32, FN_DW_SPLIT, FN_WIDEN = range(6)
+
+
+def op_elementwise(fn, x, stream=None):
+    """The kernels' per-element arithmetic applied on the device to a contiguous
+    CUDA tensor x by m1_op_elementwise: float64 in and out for RCP64 / SQRT64,
+    float32 for RCP32 / SQRT32, float64 in and float32 pairs [n, 2] out for
+    DW_SPLIT, float32 in and float64 out for WIDEN."""
+    import torch
+    want = torch.float32 if fn in (FN_RCP32, FN_SQRT32, FN_WIDEN) else torch.float64
+    if x.dtype != want or not x.is_cuda or not x.is_contiguous():
+        raise ValueError(f"m1_op_elementwise fn {fn}: x must be a contiguous {want} CUDA tensor")
+    n = x.numel()
+    if fn == FN_DW_SPLIT:
+        y = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+    elif fn in (FN_RCP32, FN_SQRT32):
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+    else:
+        y = torch.empty(n, dtype=torch.float64, device=x.device)
+    _check(_lib.m1_op_elementwise(fn, x.data_ptr(), n, y.data_ptr(), stream), "m1_op_elementwise")
+    return y
+
+
+def dw_split(x):
+    """(hi, lo) float32 arrays of the double-word split the kernels apply to
+    FP64 values, computed on the host by the same code (m1_dw_split)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    hi, lo = np.empty(x.shape, np.float32), np.empty(x.shape, np.float32)
+    _check(_lib.m1_dw_split(x.ctypes.data, x.size, hi.ctypes.data, lo.ctypes.data), "m1_dw_split")
+    return hi, lo
+
+
+def f32_widen(x):
+    """float64 copy of a float32 array by the kernels' widening (m1_f32_widen)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty(x.shape, np.float64)
+    _check(_lib.m1_f32_widen(x.ctypes.data, x.size, y.ctypes.data), "m1_f32_widen")
+    return y
 
 
 class GridDesc3(ctypes.Structure):

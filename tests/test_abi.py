@@ -158,6 +158,11 @@ def test_probe_rejects_bad_arguments_without_gpu(lib):
     assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 0, ctypes.byref(out)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_probe_fma_peak(7, None, 3, ctypes.byref(out)) == m1.ERR_INVALID_ARG
     assert m1._lib.m1_probe_fma_peak(m1.FP64, None, 3, None) == m1.ERR_INVALID_ARG
+    # the elementwise check entry: argument errors are found before any launch
+    assert m1._lib.m1_op_elementwise(m1.FN_RCP64, None, -1, None, None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_op_elementwise(m1.FN_SQRT64, None, 5, None, None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_op_elementwise(6, None, 0, None, None) == m1.ERR_INVALID_ARG
+    assert m1._lib.m1_op_elementwise(m1.FN_SQRT32, None, 0, None, None) == 0
 
 
 def test_grid3_validation_without_gpu(lib):
