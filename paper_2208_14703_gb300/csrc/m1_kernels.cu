@@ -62,6 +62,15 @@ __device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
     return ctls && (ctls[inst].done || !ctls[inst].active);
 }
 
+// Work-list entry w, or (0, 0) past the allocation (entries up to the capacity
+// are allocated).  The persistent loops read their first entry together with
+// the count instead of after it: a small level's launch is a chain of
+// dependent reads (list, descriptor, rows), and this takes one link out.
+__device__ __forceinline__ int2 item_at(const WorkList& wl, int w)
+{
+    return w < wl.capacity ? wl.items[w] : make_int2(0, 0);
+}
+
 // ---------------------------------------------------------------------------
 // One cell of a warp strip as its neighbours need it: the state (or, in the
 // correction form, the correction e) and its closure P (or P(w + e) - P(w)),
@@ -336,9 +345,11 @@ __global__ void __launch_bounds__(kStripWarps * 32, (sizeof(R) == 8 ? 8 : 10)) k
     __shared__ Level<R> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<R>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<R>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
         const double nrm =
@@ -490,9 +501,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_sweep_ring32(const Level<f
     __shared__ RowSlot32 ring[kStripWarps][kRing];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<float>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const Cell4<float>* __restrict__ src = in_buf < 0 ? L.v : L.u[in_buf];
         if (L.dim == 2) strip_ring32<PSEUDO>(L, ctls + it.x, it, lane, src, out_buf, ring[wib]);
@@ -622,9 +635,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_apply(const Level<R>* __re
     __shared__ Level<R> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<R>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         const double nrm = apply_item<R, MODE, DELTA>(L, it, lane, state_buf, write_r);
         if (MODE == APPLY_RESID && partials) {
@@ -702,9 +717,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_fas_aw32(const Level<float
     __shared__ Level<float> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<float>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (!enter_item(L, lv + it.x, ctls, it.x, lane)) continue;
         fas_aw32_item(L, it, lane);
         __syncwarp();
@@ -721,9 +738,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_norm_state(const Level<R>*
     __shared__ Level<R> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<R>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (ctls && !ctls[it.x].active) continue;
         load_level_warp(L, lv + it.x, lane);
         const int x0 = (it.y % L.sx) * kStripW, y0 = (it.y / L.sx) * L.sh;
@@ -791,10 +810,12 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const Level<R>* __restric
                                                        int fine_buf)
 {
     __shared__ Level<R> Lf, Lc;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (skip(ctls, it.x)) continue;
         if (it.x != inst) {                   // descriptors of a new instance
             __syncthreads();
@@ -813,11 +834,13 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>*
                                WorkList wl)
 {
     __shared__ Level<R> Lf, Lc;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
     const R wgt[3] = { R(0.25), R(0.5), R(0.25) };
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (it.x != inst) {                   // descriptors of a new instance
             __syncthreads();
             load_level(Lf, lvf + it.x);
@@ -892,10 +915,12 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
                                                       int coarse_buf, int fine_buf)
 {
     __shared__ Level<R> Lf, Lc;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (skip(ctls, it.x)) continue;
         if (it.x != inst) {                   // descriptors of a new instance
             __syncthreads();
@@ -916,10 +941,12 @@ __global__ void k_make_rhs(const Level<R>* __restrict__ lv, WorkList wl,
                            const Ctl* __restrict__ ctls, int buf)
 {
     __shared__ Level<R> L;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (ctls && !ctls[it.x].active) continue;
         if (it.x != inst) {                   // descriptor of a new instance
             __syncthreads();
@@ -1092,9 +1119,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<double>& L = Ls[wib];
     Level<float>& M = Ms[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         {
             constexpr int nm = (int)(sizeof(Level<float>) / 8);
             const unsigned long long wm =
@@ -1297,10 +1326,12 @@ __global__ void __launch_bounds__(kThreads) k_dw_split(const Level<double>* __re
                                                        const DwLevel* __restrict__ dwd, WorkList wl)
 {
     __shared__ Level<double> L;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (it.x != inst) {
             __syncthreads();
             load_level(L, lv + it.x);
@@ -1337,9 +1368,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<doub
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<double>& L = Ls[wib];
     Level<float>& M = Ms[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         {
             constexpr int nm = (int)(sizeof(Level<float>) / 8);
             const unsigned long long wm =
@@ -1380,9 +1413,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_residual_dw(const Level<do
     __shared__ Level<double> Ls[kStripWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Level<double>& L = Ls[wib];
+    const int w0 = blockIdx.x * kStripWarps + wib, ws = gridDim.x * kStripWarps;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
-    for (int w = blockIdx.x * kStripWarps + wib; w < nw; w += gridDim.x * kStripWarps) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (!enter_item(L, lv + it.x, nullptr, it.x, lane)) continue;
         const LevelDW D = level_dw(L);
         const bool two_d = L.dim == 2;
@@ -1426,10 +1461,12 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
 {
     __shared__ Level<double> L;
     __shared__ Level<float> M;
+    const int w0 = blockIdx.x, ws = gridDim.x;
+    int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl.items[w];
+    for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
+        const int2 it = nx;
         if (skip(ctls, it.x)) continue;
         Ctl* ctl = ctls + it.x;
         if (it.x != inst) {                   // descriptors of a new instance
