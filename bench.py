@@ -317,6 +317,43 @@ def bench_fp32_sweep_large(m1, stream, flush, hbm_peak, n=4096):
             "kernel": "k_sweep FP32 correction form at the 4096^2 mixed configuration"}
 
 
+def bench_mixed_beam(m1, stream, flush, n=4096):
+    """The mixed-precision configuration: an f = 1 beam entering a thin channel
+    at the west wall of a 4096^2 lognormal medium (L_max = 10, tol 1e-8).  One
+    step through each path, timed after a two-cycle warm-up that builds the
+    captured cycle, and the per-field difference of the two results (the
+    element-wise comparison with the oracle runs on the 1024^2 window of this
+    grid that holds the beam, tests/test_gpu_full_size.py)."""
+    import torch
+    from paper_2208_14703_gb300 import inputs
+    case = inputs.beam_channel_2d(n)
+    s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).to("cuda") for k in range(4)]
+    cells = n * n
+    out = {"workload": f"m1-implicit-step-2d-beam-channel-{n}x{n}-lmax{case['lmax']}-tol1e-8",
+           "l2": "flushed before each timed step"}
+    states = {}
+    for name, prec in (("mixed", m1.MIXED), ("fp64", m1.FP64)):
+        g = m1.grid_from_case(case, precision=prec, stream=stream.cuda_stream)
+        g.set_state(*s0, on_device=True)
+        g.implicit_step(case["dt"], m1.m1_default_params(tol=case["tol"], max_cycles=2),
+                        allow_not_converged=True)
+        g.set_state(*s0, on_device=True)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = g.implicit_step(case["dt"], m1.m1_default_params(tol=case["tol"]))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        states[name] = np.stack(g.get_state())
+        g.close()
+        out[name] = {"ms_per_step": ms, "cycles": st.cycles,
+                     "cell_updates_per_s": cells * st.sweeps / (ms * 1e-3)}
+    out["fp64_over_mixed_time"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["mixed_err_vs_fp64_gpu"] = field_errors(states["mixed"], states["fp64"])
+    return out
+
+
 # FP64 work of one 3D Jacobi update, counted as SWEEP_OPS is: the closure pass
 # (reciprocal 4, F/E 3, 4 - 3 f^2 and its clamp 5, square root 6, E (s - 1)/3 2,
 # 3/(c^2 (2 + s)) 6, q F/E 3, the six tensor entries 6) and the operator pass
@@ -789,6 +826,7 @@ def main():
         mixed = bench_mixed(m1, case, stream, s0, flush, ref64, args.steps, pk["hbm_gbs"])
         mixed["roofline_fp32_sweep_4096"] = bench_fp32_sweep_large(m1, stream, flush,
                                                                    pk["hbm_gbs"])
+        extras["mixed_beam"] = bench_mixed_beam(m1, stream, flush)
         extras["batched"] = bench_batched(m1, args.batch_count, stream)
         if args.serve_full:
             reqs = inputs.serving_stream(64)
@@ -806,7 +844,7 @@ def main():
         extras["mixed"] = mixed
         extras = {k: rounded(v) for k, v in extras.items()}
         # the large blocks last: a reader of the line's tail sees them
-        for k in ("mixed", "batched", "serving"):
+        for k in ("mixed_beam", "mixed", "batched", "serving"):
             extras[k] = extras.pop(k)
 
     launches = sum(s.launches for s in stats) + 2 * args.steps
