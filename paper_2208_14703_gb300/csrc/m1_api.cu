@@ -657,8 +657,8 @@ void Engine<R>::visit(const Params& p, int l, bool fresh, int shape, std::vector
     if (chunks[l + 1].n)
         launch_restrict<R>(dl, dl + cap, chunks[l + 1].view(), ctl, cur[l], s, delta);
     corrections(p, l, shape, cur, s);
-    if (chunks[l].n)
-        launch_prolong<R>(dl + cap, dl, chunks[l].view(), ctl, cur[l + 1], cur[l], s, delta);
+    if (chunks[l + 1].n)
+        launch_prolong<R>(dl + cap, dl, chunks[l + 1].view(), ctl, cur[l + 1], cur[l], s, delta);
     pseudo(l, cur[l], p.m, false, s);
 }
 
@@ -691,8 +691,8 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         if (chunks[1].n)
             launch_restrict<R>(d, d + cap, chunks[1].view(), ctl, cur[0], s, delta);
         corrections(p, 0, p.cycle, cur, s);
-        if (chunks[0].n)
-            launch_prolong<R>(d + cap, d, chunks[0].view(), ctl, cur[1], cur[0], s, delta);
+        if (chunks[1].n)
+            launch_prolong<R>(d + cap, d, chunks[1].view(), ctl, cur[1], cur[0], s, delta);
         sweeps_fine(cur[0], p.nu0, s);
     }
     cur0 = cur[0];
@@ -1017,7 +1017,7 @@ m1_status Engine<R>::op_prolong(const double* uc, const double* vc, const double
     M1_TRY(pack_planar(h[cap].u[0], h[cap].n, uc));
     M1_TRY(pack_planar(h[cap].v, h[cap].n, vc));
     M1_TRY(pack_planar(h[0].u[0], h[0].n, uf));
-    launch_prolong<R>(d + cap, d, chunks[0].view(), ctl, 0, 0, stream);
+    launch_prolong<R>(d + cap, d, chunks[1].view(), ctl, 0, 0, stream);
     M1_CK(cudaGetLastError());
     M1_TRY(unpack_planar(h[0].u[0], h[0].n, out));
     if (damped) {

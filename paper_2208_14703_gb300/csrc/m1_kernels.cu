@@ -868,46 +868,60 @@ __global__ void k_restrict_sig(const Level<R>* __restrict__ lvf, const Level<R>*
 }
 
 // ---------------------------------------------------------------------------
-// u_l += P(u_{l+1} - v_{l+1}) per fine cell (fine 2i <- coarse i, fine 2i+1 <-
-// half of coarse i and i+1; tensor product in 2D); a target outside the
-// admissible set is replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).
+// u_l += P(u_{l+1} - v_{l+1}) (fine 2i <- coarse i, fine 2i+1 <- half of coarse
+// i and i+1; tensor product in 2D); a target outside the admissible set is
+// replaced by u + theta_c min(1, tau*) P(e) (Eq. (34)).  One thread takes the
+// 2 x 2 (1D: 2) fine cells of coarse cell kc: the differences of the coarse
+// cells (ic + a, jc + b), a, b in {0, 1}, are formed once for all of them, and
+// each fine cell (2ic + ox, 2jc + oy) sums its weighted differences (a <= ox,
+// b <= oy) in the order b, then a, as a thread per fine cell would.
 template <typename R, bool DELTA>
-__device__ __forceinline__ void prolong_cell(const Level<R>& Lc, const Level<R>& Lf, int k,
-                                             int coarse_buf, int fine_buf, Ctl* ctl)
+__device__ __forceinline__ void prolong_block(const Level<R>& Lc, const Level<R>& Lf, int kc,
+                                              int coarse_buf, int fine_buf, Ctl* ctl)
 {
-    const int i = k % Lf.nx, j = k / Lf.nx;
-    const int ic = i >> 1, jc = Lf.dim == 2 ? j >> 1 : 0;
-    const int ox = i & 1, oy = Lf.dim == 2 ? (j & 1) : 0;
+    const bool two_d = Lf.dim == 2;
+    const int ic = kc % Lc.nx, jc = two_d ? kc / Lc.nx : 0;
     const Cell4<R>* __restrict__ uc = Lc.u[coarse_buf];
-    const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
-    Cell4<R> pe = { 0, 0, 0, 0 };
     // the coarse cells read lie inside the grid: plain loads
-    const bool inside = ic + 1 < Lc.nx && (Lf.dim != 2 || jc + 1 < Lc.ny);
-    for (int b = 0; b <= oy; ++b)
-        for (int a = 0; a <= ox; ++a) {
-            const size_t kc = (size_t)(jc + b) * Lc.nx + ic + a;
-            const Cell4<R> cu = inside ? uc[kc] : fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
-            const Cell4<R> cv = inside ? Lc.v[kc] : fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
-            pe.E += wt * (cu.E - cv.E); pe.Fx += wt * (cu.Fx - cv.Fx);
-            pe.Fy += wt * (cu.Fy - cv.Fy); pe.T += wt * (cu.T - cv.T);
+    const bool inside = ic + 1 < Lc.nx && (!two_d || jc + 1 < Lc.ny);
+    const int nb = two_d ? 2 : 1;
+    Cell4<R> dc[2][2];
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 2; ++a) {
+            const size_t kk = (size_t)(jc + b) * Lc.nx + ic + a;
+            const Cell4<R> cu = inside ? uc[kk] : fetch(Lc, uc, ic + a, jc + b, KIND_DIFF);
+            const Cell4<R> cv = inside ? Lc.v[kk] : fetch(Lc, Lc.v, ic + a, jc + b, KIND_DIFF);
+            dc[b][a] = Cell4<R>{ cu.E - cv.E, cu.Fx - cv.Fx, cu.Fy - cv.Fy, cu.T - cv.T };
         }
     Cell4<R>* __restrict__ uf = Lf.u[fine_buf];
-    const Cell4<R> e = uf[k];
-    Cell4<R> u = e;
-    if (DELTA) {   // correction form: the admissible set constrains w + e
-        const Cell4<R> wb = Lf.w[k];
-        u.E += wb.E; u.Fx += wb.Fx; u.Fy += wb.Fy; u.T += wb.T;
-    }
-    const Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
-    R th = R(1);
-    if (!admissible(tg, Lf.c)) {
-        th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
-        atomicAdd(&ctl->damped, 1u);
-    }
-    uf[k] = Cell4<R>{ e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy, e.T + th * pe.T };
+    for (int oy = 0; oy < nb; ++oy)
+        for (int ox = 0; ox < 2; ++ox) {
+            const size_t k = (size_t)(2 * jc + oy) * Lf.nx + 2 * ic + ox;
+            const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
+            Cell4<R> pe = { 0, 0, 0, 0 };
+            for (int b = 0; b <= oy; ++b)
+                for (int a = 0; a <= ox; ++a) {
+                    pe.E += wt * dc[b][a].E; pe.Fx += wt * dc[b][a].Fx;
+                    pe.Fy += wt * dc[b][a].Fy; pe.T += wt * dc[b][a].T;
+                }
+            const Cell4<R> e = uf[k];
+            Cell4<R> u = e;
+            if (DELTA) {   // correction form: the admissible set constrains w + e
+                const Cell4<R> wb = Lf.w[k];
+                u.E += wb.E; u.Fx += wb.Fx; u.Fy += wb.Fy; u.T += wb.T;
+            }
+            const Cell4<R> tg = { u.E + pe.E, u.Fx + pe.Fx, u.Fy + pe.Fy, u.T + pe.T };
+            R th = R(1);
+            if (!admissible(tg, Lf.c)) {
+                th = (R)ctl->theta_c * fmin(R(1), max_admissible_step(u, pe, Lf.c));
+                atomicAdd(&ctl->damped, 1u);
+            }
+            uf[k] = Cell4<R>{ e.E + th * pe.E, e.Fx + th * pe.Fx, e.Fy + th * pe.Fy,
+                              e.T + th * pe.T };
+        }
 }
 
-// Items are (instance, 256-cell chunk of the fine level).
+// Items are (instance, 256-cell chunk of the coarse level).
 template <typename R, bool DELTA = false>
 __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict__ lvc,
                                                       const Level<R>* __restrict__ lvf,
@@ -929,8 +943,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const Level<R>* __restrict
             __syncthreads();
             inst = it.x;
         }
-        const int k = it.y * kThreads + threadIdx.x;
-        if (k < Lf.n) prolong_cell<R, DELTA>(Lc, Lf, k, coarse_buf, fine_buf, ctls + it.x);
+        const int kc = it.y * kThreads + threadIdx.x;
+        if (kc < Lc.n) prolong_block<R, DELTA>(Lc, Lf, kc, coarse_buf, fine_buf, ctls + it.x);
     }
 }
 
