@@ -514,6 +514,71 @@ __device__ __forceinline__ Cell4<R> local_solve_delta(R w0, R w1, R diag, R ka, 
 // with T from the mirror cell.  Differences (kind DIFF) hold zero at inflow
 // walls.  A corner resolves the y wall on the cell the x wall points to, then
 // applies the x wall on top (the x wall is the outer rule).
+// The rules of `fetch` (below) split in two, so that a caller can map several
+// ghosts first and issue their loads together: fetch(L, s, i, j, kind) =
+// ghost_apply(L, s[g.k], g, kind) with g = ghost_map(L, i, j) (zero for a
+// difference at an inflow wall, whatever was loaded).
+struct Ghost {
+    size_t k;          // index of the source cell
+    int i, jo;         // mapped column, original row
+    int xrule, yrule;  // BC of the wall crossed (-1: none or periodic)
+    int xwall, ywall;
+};
+
+template <typename R>
+__device__ __forceinline__ Ghost ghost_map(const Level<R>& L, int i, int j)
+{
+    Ghost g;
+    g.jo = j;
+    g.xrule = -1; g.xwall = 0; g.yrule = -1; g.ywall = 0;
+    if (i < 0 || i >= L.nx) {
+        g.xwall = i < 0 ? WALL_W : WALL_E;
+        const int bc = L.bc[g.xwall];
+        if (bc == BC_PERIODIC) {
+            i = i < 0 ? i + L.nx : i - L.nx;
+        } else {
+            i = i < 0 ? -1 - i : 2 * L.nx - 1 - i;
+            g.xrule = bc;
+        }
+    }
+    if (j < 0 || j >= L.ny) {
+        g.ywall = j < 0 ? WALL_S : WALL_N;
+        const int bc = L.bc[g.ywall];
+        if (bc == BC_PERIODIC) {
+            j = j < 0 ? j + L.ny : j - L.ny;
+        } else {
+            j = j < 0 ? -1 - j : 2 * L.ny - 1 - j;
+            g.yrule = bc;
+        }
+    }
+    g.i = i;
+    g.k = (size_t)j * L.nx + i;
+    return g;
+}
+
+template <typename R>
+__device__ __forceinline__ Cell4<R> ghost_apply(const Level<R>& L, Cell4<R> c, const Ghost& g,
+                                                int kind)
+{
+    if (kind == KIND_DIFF && (g.xrule == BC_INFLOW || g.yrule == BC_INFLOW))
+        return Cell4<R>{ R(0), R(0), R(0), R(0) };
+    if (g.yrule == BC_REFLECT) c.Fy = -c.Fy;
+    if (g.yrule == BC_INFLOW) {
+        const R* p = L.inflow + (size_t)(g.ywall * 3) * L.prof_len;
+        c.E = p[g.i]; c.Fx = p[L.prof_len + g.i]; c.Fy = p[2 * L.prof_len + g.i];
+    }
+    if (g.xrule == BC_REFLECT) c.Fx = -c.Fx;
+    if (g.xrule == BC_INFLOW) {
+        const int jj = g.jo < 0 ? 0 : (g.jo >= L.ny ? L.ny - 1 : g.jo);
+        const R* p = L.inflow + (size_t)(g.xwall * 3) * L.prof_len;
+        c.E = p[jj]; c.Fx = p[L.prof_len + jj]; c.Fy = p[2 * L.prof_len + jj];
+    }
+    return c;
+}
+
+// (The same rules as ghost_map + ghost_apply, written as one pass: the sweeps'
+// code generation is tuned on this form, and splitting it cost the fine FP64
+// sweep 3%.)
 template <typename R>
 __device__ __forceinline__ Cell4<R> fetch(const Level<R>& L, const Cell4<R>* __restrict__ s,
                                           int i, int j, int kind)

@@ -765,6 +765,13 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_norm_state(const Level<R>*
 // Full weighting, coarse cell (ic, jc) <- fine cells 2ic-1..2ic+1 (x) and
 // 2jc-1..2jc+1 (y, 2D only), weights 1/4, 1/2, 1/4 per axis: the iterate of
 // buffer fine_buf, the residual and, in the correction form, the base w.
+// FP32: row by row of the stencil, the sources of its three cells are mapped
+// first (ghost rules of `fetch`) and their loads issued together, then the rules
+// applied and the weighted values summed in the order of the stencil; the
+// coarse FP32 levels are small and this takes the loads' latency off the chain.
+// FP64 keeps one stencil point at a time: its restriction is bound by the FP64
+// pipe, and the registers of the batched loads cost it occupancy (measured: the
+// FP64 step 3.7% slower).  Both forms sum the same values in the same order.
 template <typename R, bool DELTA>
 __device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>& Lc, int kc,
                                               int fine_buf)
@@ -774,26 +781,55 @@ __device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>
     const Cell4<R>* __restrict__ us = Lf.u[fine_buf];
     Cell4<R> av = { 0, 0, 0, 0 }, ar = { 0, 0, 0, 0 }, aw = { 0, 0, 0, 0 };
     const int b0 = Lf.dim == 2 ? -1 : 0, b1 = Lf.dim == 2 ? 1 : 0;
-    // the whole 3 x 3 (1D: 3) fine stencil inside the grid: plain loads
-    const bool inside = 2 * ic >= 1 && 2 * ic + 1 < Lf.nx &&
-                        (Lf.dim != 2 || (2 * jc >= 1 && 2 * jc + 1 < Lf.ny));
-    auto get = [&](const Cell4<R>* arr, int i, int j, int kind) {
-        return inside ? arr[(size_t)j * Lf.nx + i] : fetch(Lf, arr, i, j, kind);
-    };
+    if constexpr (sizeof(R) == 8) {
+        // the whole 3 x 3 (1D: 3) fine stencil inside the grid: plain loads
+        const bool inside = 2 * ic >= 1 && 2 * ic + 1 < Lf.nx &&
+                            (Lf.dim != 2 || (2 * jc >= 1 && 2 * jc + 1 < Lf.ny));
+        auto get = [&](const Cell4<R>* arr, int i, int j, int kind) {
+            return inside ? arr[(size_t)j * Lf.nx + i] : fetch(Lf, arr, i, j, kind);
+        };
+        for (int b = b0; b <= b1; ++b) {
+            const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
+            const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
+            for (int a = -1; a <= 1; ++a) {
+                const R wt = wy * wgt[a + 1];
+                const Cell4<R> s = get(us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
+                const Cell4<R> r = get(Lf.r, 2 * ic + a, jf, KIND_DIFF);
+                av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
+                ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+                if (DELTA) {
+                    const Cell4<R> q = get(Lf.w, 2 * ic + a, jf, KIND_STATE);
+                    aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+                }
+            }
+        }
+        Lc.v[kc] = av;
+        Lc.r[kc] = ar;
+        if (DELTA) Lc.w[kc] = aw;
+        return;
+    }
     for (int b = b0; b <= b1; ++b) {
         const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
         const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
-        for (int a = -1; a <= 1; ++a) {
-            const R wt = wy * wgt[a + 1];
+        Ghost g[3];
+        Cell4<R> s[3], r[3], q[3];
+        for (int a = 0; a < 3; ++a) g[a] = ghost_map(Lf, 2 * ic + a - 1, jf);
+        for (int a = 0; a < 3; ++a) {
+            s[a] = us[g[a].k];
+            r[a] = Lf.r[g[a].k];
+            if (DELTA) q[a] = Lf.w[g[a].k];
+        }
+        for (int a = 0; a < 3; ++a) {
+            const R wt = wy * wgt[a];
             // correction form: the correction has zero inflow ghosts, the base
             // carries the prescribed state
-            const Cell4<R> s = get(us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
-            const Cell4<R> r = get(Lf.r, 2 * ic + a, jf, KIND_DIFF);
-            av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
-            ar.E += wt * r.E; ar.Fx += wt * r.Fx; ar.Fy += wt * r.Fy; ar.T += wt * r.T;
+            const Cell4<R> sv = ghost_apply(Lf, s[a], g[a], DELTA ? KIND_DIFF : KIND_STATE);
+            const Cell4<R> rv = ghost_apply(Lf, r[a], g[a], KIND_DIFF);
+            av.E += wt * sv.E; av.Fx += wt * sv.Fx; av.Fy += wt * sv.Fy; av.T += wt * sv.T;
+            ar.E += wt * rv.E; ar.Fx += wt * rv.Fx; ar.Fy += wt * rv.Fy; ar.T += wt * rv.T;
             if (DELTA) {
-                const Cell4<R> q = get(Lf.w, 2 * ic + a, jf, KIND_STATE);
-                aw.E += wt * q.E; aw.Fx += wt * q.Fx; aw.Fy += wt * q.Fy; aw.T += wt * q.T;
+                const Cell4<R> qv = ghost_apply(Lf, q[a], g[a], KIND_STATE);
+                aw.E += wt * qv.E; aw.Fx += wt * qv.Fx; aw.Fy += wt * qv.Fy; aw.T += wt * qv.T;
             }
         }
     }
