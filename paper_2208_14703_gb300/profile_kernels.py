@@ -15,6 +15,12 @@ CFL 100, at n x n cells):
             generated on the device
   step3d    3D: one implicit step of the n^3 hot cube (lognormal opacities,
             reflecting walls, CFL 100) with L_max = --lmax
+  steptime  not a profile: the full step (tol 1e-8) on an FP64 and on a MIXED
+            grid with L_max = --lmax, each timed three times with CUDA events
+            after an L2 flush; prints the faster of the last two and the cycle
+            counts as one JSON line (the before / after timings of kernel
+            changes quoted in the design notes come from this case at
+            --n 1024 --lmax 8)
 The state and opacities are set once; each case runs its launches once after one
 untimed warm-up of the same launches, so `ncu -s` skips the warm-up.
 
@@ -34,7 +40,8 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
-                    choices=["sweep64", "sweep32", "step64", "stepmixed", "sweep3d", "step3d"])
+                    choices=["sweep64", "sweep32", "step64", "stepmixed", "sweep3d", "step3d",
+                             "steptime"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--lmax", type=int, default=6)
     ap.add_argument("--cycles", type=int, default=50, help="max_cycles of the step cases")
@@ -57,6 +64,9 @@ def main():
         else:
             with open(args.tune_file, "w") as fh:
                 json.dump(m1.autotune(), fh)
+    if args.case == "steptime":
+        steptime(m1, inputs, args.n, args.lmax)
+        return
     mixed = args.case in ("sweep32", "stepmixed")
     lmax = 1 if args.case.startswith("sweep") else args.lmax
     case = inputs.hot_square_2d(args.n, lmax=lmax)
@@ -113,6 +123,36 @@ def sweep3d(m1, n):
         _, ms = m1.m1_op_level3(d, 100.0 / n, sig, s, rhs=b, mode=m1.OP3_JACOBI, sweeps=1,
                                 out=out, on_device=True)
     print(f"sweep3d n {n} ms {ms:.3f}")
+
+
+
+def steptime(m1, inputs, n, lmax):
+    """Full-step timings of both precisions (see the module docstring)."""
+    import json
+    import torch
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    case = inputs.hot_square_2d(n, lmax=lmax)
+    s0 = [torch.from_numpy(np.ascontiguousarray(case["state"][k])).cuda() for k in range(4)]
+    out = {"n": n, "lmax": lmax}
+    for name, prec in (("fp64", m1.FP64), ("mixed", m1.MIXED)):
+        g = m1.grid_from_case(case, precision=prec, stream=stream.cuda_stream)
+        params = m1.m1_default_params(tol=case["tol"])
+        ms = []
+        for _ in range(3):
+            g.set_state(*s0, on_device=True)
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = g.implicit_step(case["dt"], params)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        g.close()
+        out[name] = {"ms": round(min(ms[1:]), 2), "cycles": st.cycles}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
