@@ -669,7 +669,8 @@ void Engine<R>::visit(const Params& p, int l, bool fresh, int shape, std::vector
 // cycle k runs in the graph launch of cycle k + 1: the step takes one launch
 // more than it has cycles, and no separate residual pass.
 template <typename R>
-void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail)
+void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail,
+                             bool first_done)
 {
     std::vector<int> cur(L, 0);
     cur[0] = cur0;
@@ -682,6 +683,9 @@ void Engine<R>::record_cycle(const Params& p, int& cur0, cudaStream_t s, bool ta
         launch_sweep<R>(d, strips[0].view(), ctl, false, in, 1 - in, s, delta, ring[0] != 0, part);
         cur[0] = 1 - in;
         launch_finalize<R>(ctl, d, cap, part, nullptr, FIN_DEFER, in, bctl, s);
+        sweeps_fine(cur[0], p.nu0 - 1, s);
+    } else if (first_done) {
+        cur[0] = 1;
         sweeps_fine(cur[0], p.nu0 - 1, s);
     } else {
         sweeps_fine(cur[0], p.nu0, s);
@@ -1235,7 +1239,9 @@ m1_status MixedModel::sv_begin(const std::vector<int>& slots, const std::vector<
     launch_make_rhs<double>(hi.d, hi.init_chunks.view(), hi.ctl, 0, hi.stream);
     launch_dw_split(hi.d, hi.dwd, hi.init_chunks.view(), hi.stream);
     launch_norm_state<double>(hi.d, hi.init_strips.view(), hi.ctl, hi.partb, hi.stream);
-    launch_defect(hi.d, lo.d, hi.init_strips.view(), hi.ctl, hi.part, hi.stream);
+    // the served cycles share the structural parameters (fixed at server creation)
+    launch_defect(hi.d, lo.d, hi.init_strips.view(), hi.ctl, hi.part, hi.stream,
+                  !ps.empty() && ps[0].nu0 > 0);
     launch_finalize<double>(hi.ctl, hi.d, (int)slots.size(), hi.part, hi.partb, FIN_INIT, 0, hi.bctl,
                             hi.stream, hi.init_slots);
     M1_CK(cudaGetLastError());
@@ -1301,13 +1307,16 @@ m1_status MixedModel::set_inflow(int i, int side, const double* E, const double*
 // defect of the new iterate with the FP32 source of the next cycle, stop test.
 void MixedModel::record_cycle(const Params& p, cudaStream_t s)
 {
+    // the defect that ends a cycle (or starts the step) also forms the next
+    // cycle's first fine sweep (from e = 0 the sweep needs no neighbour)
+    const bool fused = p.nu0 > 0;
     int cur0 = 0;
-    lo.record_cycle(p, cur0, s, false);
+    lo.record_cycle(p, cur0, s, false, fused);
     launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur0, s, hi.dwd);
     // each instance's defect comes from one of the two: FP64, or double-word FP32
     // where its tolerance lies far above the double-word noise floor (FIN_INIT)
-    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
-    launch_defect_dw(hi.d, lo.d, hi.dwd, hi.strips[0].view(), hi.ctl, hi.part, s);
+    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s, fused);
+    launch_defect_dw(hi.d, lo.d, hi.dwd, hi.strips[0].view(), hi.ctl, hi.part, s, fused);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, nullptr, FIN_CYCLE, 0, hi.bctl, s);
 }
 
@@ -1344,7 +1353,7 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
     launch_make_rhs<double>(hi.d, c0, hi.ctl, 0, s);
     launch_dw_split(hi.d, hi.dwd, c0, s);
     launch_norm_state<double>(hi.d, t0, hi.ctl, hi.partb, s);
-    launch_defect(hi.d, lo.d, t0, hi.ctl, hi.part, s);
+    launch_defect(hi.d, lo.d, t0, hi.ctl, hi.part, s, p.nu0 > 0);
     launch_finalize<double>(hi.ctl, hi.d, hi.cap, hi.part, hi.partb, FIN_INIT, 0, hi.bctl, s);
     M1_CK(cudaGetLastError());
     for (int i = 0; i < hi.cap; ++i)
@@ -1374,7 +1383,8 @@ m1_status MixedModel::step(const double* dts, const m1_solve_params& sp, m1_step
             o.status = c.status;
             o.newton_fail = c.newton_fail;
             o.damped = c.damped;
-            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 4);   // accumulate, defects, finalize
+            // accumulate, defects, finalize; the first fine sweep is the defects'
+            o.launches = 4 + launched * (lo.kernels_per_cycle(p) + 4 - (p.nu0 > 0 ? 1 : 0));
         }
         ++k;
     }
@@ -1392,7 +1402,7 @@ m1_status MixedModel::jacobi(int i, double dt, int sweeps)
     M1_TRY(hi.set_ctl_simple(0, 0.0, 0.5, 0.5));
     cudaStream_t s = hi.stream;
     launch_make_rhs<double>(hi.d, hi.chunks[0].view(), hi.ctl, 0, s);
-    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s);
+    launch_defect(hi.d, lo.d, hi.strips[0].view(), hi.ctl, hi.part, s, false);
     int cur = 0;
     lo.sweeps_fine(cur, sweeps, s);
     launch_accumulate(hi.d, lo.d, hi.chunks[0].view(), hi.ctl, cur, s);

@@ -140,7 +140,10 @@ struct Engine {
     void sweeps_fine(int& cur, int count, cudaStream_t s);
     void fas_rhs(int l, cudaStream_t s);
     void pseudo(int l, int& cur, int m, bool from_v, cudaStream_t s, bool fas = false);
-    void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true);
+    // first_done (the FP32 engine of the mixed model): the defect kernels have
+    // already formed the first fine sweep into buffer 1, so the cycle starts there
+    void record_cycle(const Params& p, int& cur0, cudaStream_t s, bool tail = true,
+                      bool first_done = false);
     void visit(const Params& p, int l, bool fresh, int shape, std::vector<int>& cur, cudaStream_t s);
     void corrections(const Params& p, int l, int shape, std::vector<int>& cur, cudaStream_t s);
     long long kernels_per_cycle(const Params& p) const;

@@ -1151,6 +1151,25 @@ __global__ void k_check_state(const Cell4<R>* __restrict__ s, const Sig2<R>* __r
     if (!ok) atomicAdd(bad, 1u);
 }
 
+// The first fine Jacobi sweep of the next FP32 cycle (Algorithm 1 in the
+// correction form), formed by the defect kernels beside the cycle's FP32
+// problem when `first_sweep` is set: from e = 0 every neighbour term vanishes
+// exactly (each closure difference P(w + 0) - P(w) is zero), so the sweep is
+// the cell's own local solve with right-hand side g, and its result goes to
+// buffer 1, where the cycle's second sweep reads it.  The cycle then launches
+// one fine sweep fewer.
+__device__ __forceinline__ Cell4<float> first_sweep32(const Level<float>& M, const Cell4<float>& w,
+                                                      const Cell4<float>& g, float sa, float ss,
+                                                      Ctl* ctl)
+{
+    const float ka = M.cdt * sa, kt = M.cdt * (sa + ss);
+    bool ok;
+    const Cell4<float> e = local_solve_delta<float>(0.f, 1.f, M.diag, ka, kt, M.c_v, M.a_r, w.T,
+                                                    g.E, g.Fx, g.Fy, g.T, ok);
+    if (!ok) atomicAdd(&ctl->newton_fail, 1u);
+    return e;
+}
+
 // ---------------------------------------------------------------------------
 // Mixed precision: FP32 V-cycles in correction form inside FP64 defect
 // correction.
@@ -1162,7 +1181,8 @@ __global__ void k_check_state(const Cell4<R>* __restrict__ s, const Sig2<R>* __r
 __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>* __restrict__ lv64,
                                                              const Level<float>* __restrict__ lv32,
                                                              WorkList wl, Ctl* __restrict__ ctls,
-                                                             double* __restrict__ partials)
+                                                             double* __restrict__ partials,
+                                                             int first_sweep)
 {
     __shared__ Level<double> Ls[kStripWarps];
     __shared__ Level<float> Ms[kStripWarps];
@@ -1202,9 +1222,14 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
             const double rFy = b.Fy - ((L.diag + kt) * u.Fy - NFy);
             const double rT = b.T - (L.c_v * u.T - se);
             nrm += rE * rE + (rFx * rFx + rFy * rFy) * L.ic2 + rT * rT;
-            M.w[k] = Cell4<float>{ narrow(u.E), narrow(u.Fx), narrow(u.Fy), narrow(u.T) };
-            M.f[k] = Cell4<float>{ narrow(rE), narrow(rFx), narrow(rFy), narrow(rT) };
-            M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
+            const Cell4<float> w32 = { narrow(u.E), narrow(u.Fx), narrow(u.Fy), narrow(u.T) };
+            const Cell4<float> g32 = { narrow(rE), narrow(rFx), narrow(rFy), narrow(rT) };
+            M.w[k] = w32;
+            M.f[k] = g32;
+            if (first_sweep)
+                M.u[1][k] = first_sweep32(M, w32, g32, narrow(sg.sa), narrow(sg.ss), ctls + it.x);
+            else
+                M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
         });
         const double sum = warp_sum(nrm);
         if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
@@ -1411,7 +1436,8 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<doub
                                                                 const Level<float>* __restrict__ lv32,
                                                                 const DwLevel* __restrict__ dwd,
                                                                 WorkList wl, Ctl* __restrict__ ctls,
-                                                                double* __restrict__ partials)
+                                                                double* __restrict__ partials,
+                                                                int first_sweep)
 {
     __shared__ Level<double> Ls[kStripWarps];
     __shared__ Level<float> Ms[kStripWarps];
@@ -1441,11 +1467,17 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<doub
                                                  const StagedDW& prev, const StagedDW& next,
                                                  const StagedDW& cur) {
             DW rE, rFx, rFy, rT;
-            residual_dw(D, wv, ev, prev, next, cur, two_d, S.b[k], S.sig[k], rE, rFx, rFy, rT);
+            const DW2 sg = S.sig[k];
+            residual_dw(D, wv, ev, prev, next, cur, two_d, S.b[k], sg, rE, rFx, rFy, rT);
             nrm += rE.hi * rE.hi + (rFx.hi * rFx.hi + rFy.hi * rFy.hi) * ic2 + rT.hi * rT.hi;
-            M.w[k] = Cell4<float>{ cur.E.hi, cur.Fx.hi, cur.Fy.hi, cur.T.hi };
-            M.f[k] = Cell4<float>{ rE.hi, rFx.hi, rFy.hi, rT.hi };
-            M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
+            const Cell4<float> w32 = { cur.E.hi, cur.Fx.hi, cur.Fy.hi, cur.T.hi };
+            const Cell4<float> g32 = { rE.hi, rFx.hi, rFy.hi, rT.hi };
+            M.w[k] = w32;
+            M.f[k] = g32;
+            if (first_sweep)
+                M.u[1][k] = first_sweep32(M, w32, g32, sg.sa.hi, sg.ss.hi, ctls + it.x);
+            else
+                M.u[0][k] = Cell4<float>{ 0.f, 0.f, 0.f, 0.f };
         });
         const double sum = warp_sum((double)nrm);
         if (lane == 0) partials[L.part_off + it.y] = sum * L.vol;
@@ -1696,15 +1728,17 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 }
 
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
-                   double* partials, cudaStream_t s)
+                   double* partials, cudaStream_t s, bool first_sweep)
 {
-    k_defect<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials);
+    k_defect<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, wl, ctls, partials,
+                                                          first_sweep ? 1 : 0);
 }
 
 void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, const DwLevel* dwd,
-                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s)
+                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s, bool first_sweep)
 {
-    k_defect_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, dwd, wl, ctls, partials);
+    k_defect_dw<<<pgrid_warps(wl), kStripWarps * 32, 0, s>>>(lv64, lv32, dwd, wl, ctls, partials,
+                                                             first_sweep ? 1 : 0);
 }
 
 void launch_dw_split(const Level<double>* lv, const DwLevel* dwd, WorkList wl, cudaStream_t s)

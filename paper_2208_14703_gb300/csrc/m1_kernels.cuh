@@ -52,11 +52,14 @@ void launch_check_state(const Cell4<R>* st, const Sig2<R>* sig, int n, double c,
 
 // FP32 correction form, coarse level: A(w) -> aw and f = [A(w + v) - A(w)] + r.
 void launch_fas_aw32(const Level<float>* lv, WorkList wl, Ctl* ctls, cudaStream_t s);
+// The FP64 defect and the next FP32 cycle's problem (w = fl32(v), g = fl32(r));
+// first_sweep: also that cycle's first fine sweep from e = 0, into buffer 1
+// (else e = 0 in buffer 0).
 void launch_defect(const Level<double>* lv64, const Level<float>* lv32, WorkList wl, Ctl* ctls,
-                   double* partials, cudaStream_t s);
+                   double* partials, cudaStream_t s, bool first_sweep);
 // the defect in double-word FP32, for the instances whose control block chose it
 void launch_defect_dw(const Level<double>* lv64, const Level<float>* lv32, const DwLevel* dwd,
-                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s);
+                      WorkList wl, Ctl* ctls, double* partials, cudaStream_t s, bool first_sweep);
 // double-word copies of the fine level's iterate, right-hand side and opacities
 void launch_dw_split(const Level<double>* lv, const DwLevel* dwd, WorkList wl, cudaStream_t s);
 // the double-word residual r = b - A(u) of level-0 state u alone (written in FP64),
