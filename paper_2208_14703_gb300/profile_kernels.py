@@ -10,6 +10,8 @@ CFL 100, at n x n cells):
             (k_sweep<float> in correction form), FP64 accumulation
   step64    one implicit step on an FP64 grid with L_max = --lmax
   stepmixed one implicit step on a MIXED grid with L_max = --lmax
+            (step64 and stepmixed: --workload beam takes the beam-in-a-channel
+            grid of the mixed-precision configuration instead of the hot square)
   sweep3d   3D: one Jacobi sweep (closure pass + operator pass) of an n^3 grid with
             reflecting walls, admissible random states and lognormal opacities
             generated on the device
@@ -46,6 +48,9 @@ def main():
     ap.add_argument("--lmax", type=int, default=6)
     ap.add_argument("--cycles", type=int, default=50, help="max_cycles of the step cases")
     ap.add_argument("--tune-file", default=None)
+    ap.add_argument("--workload", choices=["hot", "beam"], default="hot",
+                    help="2D step cases: the hot square, or the beam entering a channel "
+                         "(the mixed-precision configuration's generator)")
     args = ap.parse_args()
 
     from paper_2208_14703_gb300 import inputs, m1
@@ -69,7 +74,10 @@ def main():
         return
     mixed = args.case in ("sweep32", "stepmixed")
     lmax = 1 if args.case.startswith("sweep") else args.lmax
-    case = inputs.hot_square_2d(args.n, lmax=lmax)
+    if args.workload == "beam" and not args.case.startswith("sweep"):
+        case = inputs.beam_channel_2d(args.n, lmax=lmax)
+    else:
+        case = inputs.hot_square_2d(args.n, lmax=lmax)
     g = m1.grid_from_case(case, precision=m1.MIXED if mixed else m1.FP64)
     state = [np.ascontiguousarray(case["state"][k]) for k in range(4)]
     dt = case["dt"]

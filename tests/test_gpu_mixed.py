@@ -148,3 +148,35 @@ def test_mixed_step_with_double_word_defect_matches_oracle(name, make, lmax):
     err = field_errors(out, ref, case["desc"]["c"])
     print(name, st.cycles, "cycles", err)
     assert max(err.values()) <= BOUND, err
+
+
+# The mixed path forms the cycles' defect in double words when
+# tol ||r_0|| > 5e-12 diag ||b|| (m1_api.cu, make_ctl).  The difference between
+# the double-word and the FP64 defect is largest at converged states (general
+# values in every term of A); pin it there, on the hot square and the beam, at
+# least 50 times below that threshold.
+DW_FLOOR_CASES = [
+    ("hot-square-256", lambda: inputs.hot_square_2d(256, lmax=6)),
+    ("beam-window-256", lambda: inputs.beam_channel_crop(256, full=1024, lmax=6)),
+]
+
+
+@pytest.mark.parametrize("name,make", DW_FLOOR_CASES, ids=[c[0] for c in DW_FLOOR_CASES])
+def test_double_word_defect_floor_at_converged_state(name, make):
+    case = make()
+    og = O.Grid.from_case(case)
+    b = O.rhs_of(og, case["state"])
+    g = m1.grid_from_case(case, precision=m1.FP64)
+    g.implicit_step(case["dt"], m1.m1_default_params(tol=case["tol"]))
+    v = np.stack(g.get_state())
+    g.close()
+    desc = m1.desc_from_case(case)
+    sig = np.stack([case["sa"], case["ss"]])
+    r64, _ = m1.m1_op_level(desc, case["dt"], sig, v, b, mode=m1.OP_RESIDUAL, inflow=case["inflow"])
+    rdw, _ = m1.m1_op_level(desc, case["dt"], sig, v, b, mode=m1.OP_RESIDUAL_DW,
+                            inflow=case["inflow"])
+    d = case["desc"]
+    diag = 1 + d["c"] * case["dt"] * d["nx"] / d["lx"] + d["c"] * case["dt"] * d["ny"] / d["ly"]
+    floor = O.norm(og, rdw - r64) / (diag * O.norm(og, b))
+    print(name, "double-word defect floor", floor, "x diag ||b||")
+    assert floor <= 5e-12 / 50
