@@ -280,11 +280,32 @@ __device__ __forceinline__ R max_admissible_step(const Cell4<R>& u, const Cell4<
     return fmin(tau, t);
 }
 
+// x > 0 for an FP64 x from its bit pattern (sign clear, not zero, not NaN):
+// the FP64 comparison would take an FP64-pipe slot.
+__device__ __forceinline__ bool positive_f64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
+// The admissible set: E > 0, T > 0, |F| <= c E (with the slack of Slack<R>).
+// c2 = c * c, which a caller may form once for many cells.
+template <typename R>
+__device__ __forceinline__ bool admissible_c2(const Cell4<R>& s, R c2)
+{
+    if constexpr (sizeof(R) == 8) {
+        return positive_f64(s.E) && positive_f64(s.T) &&
+               s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+    } else {
+        return s.E > R(0) && s.T > R(0) &&
+               s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ bool admissible(const Cell4<R>& s, R c)
 {
-    return s.E > R(0) && s.T > R(0) &&
-           s.Fx * s.Fx + s.Fy * s.Fy <= c * c * s.E * s.E * (R(1) + Slack<R>::v);
+    return admissible_c2(s, c * c);
 }
 
 // Newton on g(T) = C T + K T^4 - R (increasing, convex for T > 0) started at

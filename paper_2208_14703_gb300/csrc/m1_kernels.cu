@@ -1194,12 +1194,13 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect(const Level<double>
     const int nw = *wl.count;
     for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
         const int2 it = nx;
+        // k_defect_dw forms this instance's defect: skip before reading any descriptor
+        if (ctls[it.x].defect_dw) continue;
         {
             constexpr int nm = (int)(sizeof(Level<float>) / 8);
             const unsigned long long wm =
                 lane < nm ? reinterpret_cast<const unsigned long long*>(lv32 + it.x)[lane] : 0ull;
             if (!enter_item(L, lv64 + it.x, ctls, it.x, lane)) continue;
-            if (ctls[it.x].defect_dw) continue;   // k_defect_dw forms this instance's defect
             if (lane < nm) reinterpret_cast<unsigned long long*>(&M)[lane] = wm;
             __syncwarp();
         }
@@ -1449,12 +1450,13 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_defect_dw(const Level<doub
     const int nw = *wl.count;
     for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
         const int2 it = nx;
+        // k_defect forms this instance's defect: skip before reading any descriptor
+        if (!ctls[it.x].defect_dw) continue;
         {
             constexpr int nm = (int)(sizeof(Level<float>) / 8);
             const unsigned long long wm =
                 lane < nm ? reinterpret_cast<const unsigned long long*>(lv32 + it.x)[lane] : 0ull;
             if (!enter_item(L, lv64 + it.x, ctls, it.x, lane)) continue;
-            if (!ctls[it.x].defect_dw) continue;   // k_defect forms this instance's defect
             if (lane < nm) reinterpret_cast<unsigned long long*>(&M)[lane] = wm;
             __syncwarp();
         }
@@ -1547,6 +1549,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
     int2 nx = item_at(wl, w0);
     const int nw = *wl.count;
     int inst = -1;
+    double c2 = 0.0;
     for (int w = w0; w < nw; w += ws, nx = item_at(wl, w)) {
         const int2 it = nx;
         if (skip(ctls, it.x)) continue;
@@ -1557,6 +1560,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
             load_level(M, lv32 + it.x);
             __syncthreads();
             inst = it.x;
+            c2 = L.c * L.c;
         }
         const int k = it.y * kThreads + threadIdx.x;
         if (k < L.n) {
@@ -1569,7 +1573,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const Level<double>* __
             }
             const Cell4<double> u = L.u[0][k];
             Cell4<double> tg = { u.E + e.E, u.Fx + e.Fx, u.Fy + e.Fy, u.T + e.T };
-            if (!admissible(tg, L.c)) {
+            if (!admissible_c2(tg, c2)) {
                 const double th = ctl->theta_c * fmin(1.0, max_admissible_step(u, e, L.c));
                 tg.E = u.E + th * e.E; tg.Fx = u.Fx + th * e.Fx;
                 tg.Fy = u.Fy + th * e.Fy; tg.T = u.T + th * e.T;
