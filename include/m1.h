@@ -55,6 +55,15 @@ typedef enum {
  *   m1_set_inflow (T copied from the boundary cell). */
 typedef enum { M1_BC_PERIODIC = 0, M1_BC_REFLECT = 1, M1_BC_NEUMANN = 2, M1_BC_INFLOW = 3 } m1_bc;
 
+/* M1_FP64: every level in FP64.  M1_MIXED: the iterate, the right-hand side,
+ * the opacities and the solution stay in FP64 at the fine level; each cycle
+ * forms the fine defect r = b - A(v), runs one FP32 V-cycle for the correction
+ * e of A(w + e) - A(w) = r around the base w = fl32(v) (correction form), and
+ * adds v += e in FP64 with the damping of Eq. (34).  The defect of the cycles is
+ * formed in double-word FP32 (about 48 bits) when tol ||r_0|| > 5e-12 diag ||b||,
+ * where its noise (measured at most ~3e-14 diag ||b||) stays below 1% of the stop
+ * test's threshold, and in FP64 otherwise; the defect of the step's start is
+ * FP64.  The stop test, the dtau control and the result are FP64 quantities. */
 typedef enum { M1_FP64 = 0, M1_MIXED = 1 } m1_precision;
 
 /* Grid description.  lx, ly: domain lengths (cells hx = lx/nx, hy = ly/ny);
