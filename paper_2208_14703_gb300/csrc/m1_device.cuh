@@ -290,12 +290,25 @@ __device__ __forceinline__ bool positive_f64(double x)
 
 // The admissible set: E > 0, T > 0, |F| <= c E (with the slack of Slack<R>).
 // c2 = c * c, which a caller may form once for many cells.
+//
+// FP64: |F|^2 <= c^2 E^2 (1 + slack) is first decided in FP32, from the values
+// rounded to FP32, wherever those settle it with a relative margin of 1e-5: the
+// FP32 sides carry a relative error below 4e-7 (inputs rounded once, three or
+// four roundings after), so such a decision is the FP64 test's own.  Cells near
+// the boundary (and values outside FP32's normal range) take the FP64 test.
 template <typename R>
 __device__ __forceinline__ bool admissible_c2(const Cell4<R>& s, R c2)
 {
     if constexpr (sizeof(R) == 8) {
-        return positive_f64(s.E) && positive_f64(s.T) &&
-               s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+        if (!(positive_f64(s.E) && positive_f64(s.T))) return false;
+        const float e32 = narrow(s.E), x32 = narrow(s.Fx), y32 = narrow(s.Fy);
+        const float a32 = fmaf(y32, y32, x32 * x32);
+        const float b32 = narrow(c2) * e32 * e32;
+        if (b32 >= FLT_MIN && b32 <= FLT_MAX && a32 <= FLT_MAX) {
+            if (a32 <= b32 * 0.99999f) return true;
+            if (a32 >= b32 * 1.00001f) return false;
+        }
+        return s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
     } else {
         return s.E > R(0) && s.T > R(0) &&
                s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
