@@ -296,7 +296,9 @@ __device__ __forceinline__ bool positive_f64(double x)
 // FP32 sides carry a relative error below 4e-7 (inputs rounded once, three or
 // four roundings after), so such a decision is the FP64 test's own.  Cells near
 // the boundary (and values outside FP32's normal range) take the FP64 test.
-template <typename R>
+// SLACK: with the factor (1 + Slack<R>) of the prolongation's damping test;
+// without it, the plain cone of the explicit pseudo-time step's limiter.
+template <typename R, bool SLACK = true>
 __device__ __forceinline__ bool admissible_c2(const Cell4<R>& s, R c2)
 {
     if constexpr (sizeof(R) == 8) {
@@ -308,10 +310,13 @@ __device__ __forceinline__ bool admissible_c2(const Cell4<R>& s, R c2)
             if (a32 <= b32 * 0.99999f) return true;
             if (a32 >= b32 * 1.00001f) return false;
         }
-        return s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+        if (SLACK) return s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+        return s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E;
     } else {
-        return s.E > R(0) && s.T > R(0) &&
-               s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+        if (SLACK)
+            return s.E > R(0) && s.T > R(0) &&
+                   s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E * (R(1) + Slack<R>::v);
+        return s.E > R(0) && s.T > R(0) && s.Fx * s.Fx + s.Fy * s.Fy <= c2 * s.E * s.E;
     }
 }
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ R limited_step(const Cell4<R>& u, const Cell4<R>& f, 
                                           R s, R c)
 {
     const Cell4<R> p = { u.E + s * f.E, u.Fx + s * f.Fx, u.Fy + s * f.Fy, u.T + s * f.T };
-    if (p.E > R(0) && p.T > R(0) && p.Fx * p.Fx + p.Fy * p.Fy <= c * c * p.E * p.E) return dtau;
+    if (admissible_c2<R, false>(p, c * c)) return dtau;
     return fmin(dtau, theta * max_admissible_step(u, f, c));
 }
 
