@@ -228,6 +228,29 @@ template <> struct Fm<float> {
 };
 
 // ---------------------------------------------------------------------------
+// FP64 comparisons from bit patterns: exact, off the FP64 pipe.
+// x > 0 for an FP64 x from its bit pattern (sign clear, not zero, not NaN):
+// the FP64 comparison would take an FP64-pipe slot.
+__device__ __forceinline__ bool positive_f64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
+// x > 1 and x == 0 for an FP64 x from its bit pattern (NaN compares false, as in
+// the FP64 comparisons these replace).
+__device__ __forceinline__ bool gt_one_f64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0x3ff0000000000000LL && b <= 0x7ff0000000000000LL;
+}
+
+__device__ __forceinline__ bool is_zero_f64(double x)
+{
+    return (__double_as_longlong(x) << 1) == 0;
+}
+
+// ---------------------------------------------------------------------------
 // Per-cell arithmetic.
 
 // M1 closure (Section 2.1, Eq. (5)) in the algebraically equivalent form
@@ -241,7 +264,8 @@ __device__ __forceinline__ void closure(R E, R Fx, R Fy, R inv_c2, R& Pxx, R& Px
     const R fx = Fx * iE, fy = Fy * iE;
     // 4 - 3 f^2 with f^2 = |F/E|^2 / c^2 clamped to 1
     R a = fma(fma(fy, fy, fx * fx), R(-3) * inv_c2, R(4));
-    a = a > R(1) ? a : R(1);
+    if constexpr (sizeof(R) == 8) a = gt_one_f64(a) ? a : R(1);   // off the FP64 pipe
+    else a = a > R(1) ? a : R(1);
     const R s = Fm<R>::sqrt(a);
     const R Eiso = E * fma(s, R(1) / R(3), R(-1) / R(3));
     const R q = Fm<R>::rcp(R(2) + s) * (R(3) * inv_c2);
@@ -278,14 +302,6 @@ __device__ __forceinline__ R max_admissible_step(const Cell4<R>& u, const Cell4<
         t = -c0 / (R(2) * b);
     }
     return fmin(tau, t);
-}
-
-// x > 0 for an FP64 x from its bit pattern (sign clear, not zero, not NaN):
-// the FP64 comparison would take an FP64-pipe slot.
-__device__ __forceinline__ bool positive_f64(double x)
-{
-    const long long b = __double_as_longlong(x);
-    return b > 0 && b <= 0x7ff0000000000000LL;
 }
 
 // The admissible set: E > 0, T > 0, |F| <= c E (with the slack of Slack<R>).
@@ -431,7 +447,10 @@ __device__ __forceinline__ Cell4<R> local_solve(R w0, R w1, R diag, R ka, R kt, 
     R k = w1 * ka;
     R C = w0 + w1 * c_v;
     ok = true;
-    if (k == R(0)) {
+    bool k0;
+    if constexpr (sizeof(R) == 8) k0 = is_zero_f64(k);
+    else k0 = k == R(0);
+    if (k0) {
         const R iF = Fm<R>::rcp(w0 + w1 * (diag + kt));
         o.Fx = bFx * iF;
         o.Fy = bFy * iF;
