@@ -62,6 +62,15 @@ __device__ __forceinline__ bool skip(const Ctl* ctls, int inst)
     return ctls && (ctls[inst].done || !ctls[inst].active);
 }
 
+// 2^-k (0 <= k <= 4) built from its exponent: the transfer weights are products
+// of 1/2 and 1/4, exact either way, and this keeps them off the FP64 pipe.
+template <typename R>
+__device__ __forceinline__ R pow2_neg(int k)
+{
+    if constexpr (sizeof(R) == 8) return __longlong_as_double((long long)(1023 - k) << 52);
+    else return __int_as_float((127 - k) << 23);
+}
+
 // Work-list entry w, or (0, 0) past the allocation (entries up to the capacity
 // are allocated).  The persistent loops read their first entry together with
 // the count instead of after it: a small level's launch is a chain of
@@ -789,10 +798,11 @@ __device__ __forceinline__ void restrict_cell(const Level<R>& Lf, const Level<R>
             return inside ? arr[(size_t)j * Lf.nx + i] : fetch(Lf, arr, i, j, kind);
         };
         for (int b = b0; b <= b1; ++b) {
-            const R wy = Lf.dim == 2 ? wgt[b + 1] : R(1);
+            // weights 2^-(eb + ea): 1/4, 1/2, 1/4 per axis (1D: no y factor)
+            const int eb = Lf.dim == 2 ? (b == 0 ? 1 : 2) : 0;
             const int jf = Lf.dim == 2 ? 2 * jc + b : 0;
             for (int a = -1; a <= 1; ++a) {
-                const R wt = wy * wgt[a + 1];
+                const R wt = pow2_neg<R>(eb + (a == 0 ? 1 : 2));
                 const Cell4<R> s = get(us, 2 * ic + a, jf, DELTA ? KIND_DIFF : KIND_STATE);
                 const Cell4<R> r = get(Lf.r, 2 * ic + a, jf, KIND_DIFF);
                 av.E += wt * s.E; av.Fx += wt * s.Fx; av.Fy += wt * s.Fy; av.T += wt * s.T;
@@ -933,7 +943,7 @@ __device__ __forceinline__ void prolong_block(const Level<R>& Lc, const Level<R>
     for (int oy = 0; oy < nb; ++oy)
         for (int ox = 0; ox < 2; ++ox) {
             const size_t k = (size_t)(2 * jc + oy) * Lf.nx + 2 * ic + ox;
-            const R wt = (ox ? R(0.5) : R(1)) * (oy ? R(0.5) : R(1));
+            const R wt = pow2_neg<R>(ox + oy);   // 1, 1/2 or 1/4
             Cell4<R> pe = { 0, 0, 0, 0 };
             for (int b = 0; b <= oy; ++b)
                 for (int a = 0; a <= ox; ++a) {
